@@ -1,0 +1,179 @@
+/*
+ * ilu2l.h -- C ABI of the GB300-native two-level ILU domain-decomposition
+ * preconditioner and the flexible GMRES solver around it.
+ *
+ * Method: Xu, Li, Osei-Kuffuor, "A Two-level GPU-Accelerated Incomplete LU
+ * Preconditioner for General Sparse Linear Systems" (arXiv 2303.08881).
+ *   - the problem A x = b                                   (Sec. 1, Eq. 1-1)
+ *   - p-way domain decomposition, interior nodes first      (Sec. 2.2.1, Eq. equ22)
+ *   - block Jacobi ILU                                      (Sec. 2.1, Sec. 3.1)
+ *   - additive two-level Schur ILU, E/F form               (Sec. 2.2.2, Algorithm
+ *                                                            "Additive block ILU solve")
+ *   - the one-L / one-U solve W/Z form and GPU Schur solve  (Sec. 3.2, Eq. preSS,
+ *                                                            Eq. preSMV2, Algorithm
+ *                                                            "Additive SCHUR-ILU on GPU")
+ *   - modified ILU for the Schur factor                     (Sec. 2.3, Sec. 3.3)
+ *   - flexible GMRES(m) outside                             (Sec. 4.1.1)
+ *
+ * All p subdomains live on one GPU and are processed together. Memory layout,
+ * ownership and errors are stated per call. Every call returns an ilu_status;
+ * nothing is thrown across the ABI. Handles are not thread-safe: one handle is
+ * used by one host thread at a time; different handles may run concurrently.
+ */
+#ifndef ILU2L_H
+#define ILU2L_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ILU_OK = 0,
+    ILU_ERR_ARG = 1,            /* bad argument: part out of [0,p), NULL, aliasing, bad enum */
+    ILU_ERR_CSR = 2,            /* unsorted / duplicate / out-of-range column, missing diagonal */
+    ILU_ERR_OOM = 3,            /* a device or host allocation failed */
+    ILU_ERR_ZERO_PIVOT = 4,     /* an exactly zero pivot with the perturbation disabled */
+    ILU_ERR_NOT_CONVERGED = 5,  /* maxit reached; x holds the last iterate, info is filled */
+    ILU_ERR_BREAKDOWN = 6,      /* Arnoldi breakdown without convergence */
+    ILU_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    ILU_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+    ILU_ERR_TOO_LARGE = 9,      /* n or nnz >= 2^31 */
+    ILU_ERR_UNSUPPORTED = 10    /* option combination not implemented on the device */
+} ilu_status;
+
+/* Square CSR matrix in HOST memory: 0-based int32 indices, columns strictly increasing
+   within each row, diagonal stored. The library copies it during ilu_setup. */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t* rowptr; /* n + 1 */
+    const int32_t* colind; /* nnz */
+    const double* val;     /* nnz */
+} ilu_csr;
+
+typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1 } ilu_variant;
+typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2 } ilu_fact;
+typedef enum { ILU_FORM_AUTO = 0, ILU_FORM_WZ = 1, ILU_FORM_EF = 2 } ilu_form;
+typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1 } ilu_prec;
+
+typedef struct {
+    int32_t variant;      /* ilu_variant */
+    int32_t factor_B;     /* factor of the interior block B (BJ: of each local block A_i) */
+    int32_t factor_S;     /* factorisation of A_i whose (2,2) blocks give L_S, U_S */
+    int32_t form;         /* ilu_form; AUTO = W/Z for ILU0/MILU0 B-factors, E/F for ILUT */
+    double ilut_tau;      /* ILUT relative drop tolerance (row 2-norm scaled) */
+    int32_t ilut_p;       /* ILUT entries kept per row in each of the L and U parts */
+    int32_t inner_iters;  /* GMRES steps on the preconditioned Schur system (Eq. preSS) */
+    int32_t pc_precision; /* ilu_prec: arithmetic of the factors and of M^{-1} */
+    int32_t ordering;     /* 0 = natural (ascending original index); others reserved */
+    double pivot_eps;     /* small-pivot perturbation relative to max_j |a_ij| (0 = off) */
+    void* stream;         /* cudaStream_t for every device call (NULL = legacy stream) */
+    uint64_t spin_limit;  /* iteration bound of every device-side wait (0 = default) */
+    int32_t use_graphs;   /* capture one FGMRES cycle as a CUDA graph (1) or launch (0) */
+    int32_t block_threads;/* threads per CTA of the per-subdomain kernels (0 = autotune) */
+    int32_t analysis_only;/* 1: host analysis only (no device memory, no factorisation);
+                             only ilu_get_sizes / _perm / _levels and ilu_free are valid */
+} ilu_opts;
+
+typedef struct {
+    int32_t iters;        /* Arnoldi steps over all cycles (hypre's counting) */
+    int32_t restarts;     /* completed cycles */
+    double rel_res_true;  /* ||b - A x||_2 / ||b||_2 computed in FP64 at the end */
+    double rel_res_est;   /* last Givens residual estimate / ||b|| */
+    double setup_ms;      /* wall time of ilu_setup for this handle */
+    double solve_ms;      /* wall time of this gmres_solve */
+    int32_t status;       /* ilu_status of the solve */
+    int32_t npert;        /* pivots perturbed during setup */
+} ilu_solve_info;
+
+/* Defaults: SCHUR, B = ILU0, S = MILU0, form AUTO, inner 3 steps, FP32 preconditioner,
+   natural ordering, pivot_eps 1e-8, ILUT(1e-3, 10), graphs on, autotuned CTA size. */
+void ilu_opts_default(ilu_opts* opts);
+
+/* Setup (Algorithm "Additive SCHUR-ILU on GPU", Setup; Algorithm "Block Jacobi ILU on
+   GPU", Setup). A: host CSR; part: host int32[n] with values in [0, p); p >= 1.
+   Host side: validation, interior/interface classification (a node is interface if a
+   stored a_ij or a_ji couples it to another subdomain), interior-first permutation
+   (interior grouped by subdomain, then interface grouped by subdomain, ascending
+   original index inside each group), local blocks A_i = [B_i F_i; E_i C_i], level sets.
+   Device side: ILU(0)/MILU(0) numeric factorisation of every A_i (ILUT is computed on
+   the host), factor extraction and packing. The library copies A and part; on success
+   *h owns all device memory until ilu_free. Errors: ILU_ERR_CSR, ILU_ERR_ARG,
+   ILU_ERR_TOO_LARGE, ILU_ERR_OOM, ILU_ERR_ZERO_PIVOT (only with pivot_eps = 0),
+   ILU_ERR_CUDA. On error *h is NULL. Synchronises the stream before returning. */
+ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu_opts* opts,
+                     void** h);
+
+/* z = M^{-1} r (Algorithm "Additive SCHUR-ILU on GPU", Solve, with the inner GMRES of
+   Eq. preSS; or the block Jacobi solve). r, z: DEVICE double[n] in the original
+   ordering, caller-owned; z must not alias r. Asynchronous on opts.stream.
+   Errors: ILU_ERR_ARG (NULL, aliasing), ILU_ERR_CUDA. */
+ilu_status ilu_apply(void* h, const double* r, double* z);
+
+/* Flexible GMRES(restart) with right preconditioning M^{-1} (Sec. 4.1.1), all vectors
+   FP64 on the device: b (DEVICE double[n], original ordering) and x (DEVICE double[n],
+   in = x0, out = solution), caller-owned. Stops when the true residual
+   ||b - A x|| <= rtol ||b|| (checked at the end of every cycle; a cycle ends early when
+   the Givens estimate meets the same bound) or after maxit Arnoldi steps.
+   Synchronises the stream at every cycle end and fills *info (may be NULL).
+   Returns ILU_OK, ILU_ERR_NOT_CONVERGED (x = last iterate), ILU_ERR_TIMEOUT, ILU_ERR_ARG,
+   ILU_ERR_OOM, ILU_ERR_CUDA. ||b|| = 0 gives x = 0. */
+ilu_status gmres_solve(void* h, const double* b, double* x, double rtol, int32_t restart,
+                       int32_t maxit, ilu_solve_info* info);
+
+/* Releases every resource of the handle (NULL is a no-op). Synchronises the stream. */
+ilu_status ilu_free(void* h);
+
+/* Static string for a status code. */
+const char* ilu_status_str(ilu_status s);
+
+/* ---------------------------------------------------------------------------------
+ * Introspection and single-step entry points (for parity checks and benchmarks).
+ * All host outputs are caller-allocated; all device pointers are caller-owned.
+ * --------------------------------------------------------------------------------- */
+
+/* out[0..11] = n, p, n1, n2, nnz(A), nnz(C_off), perturbed pivots, max levels of
+   (L_B, U_B, L_S, U_S, L_A, U_A) over subdomains, max rows of a local block A_i. */
+ilu_status ilu_get_sizes(void* h, int64_t* out);
+
+/* Permutation (host int32 outputs, each may be NULL): perm[new] = old, iperm[old] = new,
+   int_ptr[p+1] / if_ptr[p+1]: interior rows of subdomain s are new indices
+   [int_ptr[s], int_ptr[s+1]), interface rows n1 + [if_ptr[s], if_ptr[s+1]);
+   iface[n] = 1 for interface nodes (original numbering). */
+ilu_status ilu_get_perm(void* h, int32_t* perm, int32_t* iperm, int32_t* int_ptr,
+                        int32_t* if_ptr, int32_t* iface);
+
+/* Level of every row (host int32[n] indexed by the permuted global row, -1 for rows not
+   in the factor) for which = 0 L_A, 1 U_A (pattern of each local block A_i), 2 L_B,
+   3 U_B, 4 L_S, 5 U_S (patterns the apply uses); *nlev = max levels over subdomains.
+   Level: 0 without dependencies, else 1 + max level of the rows it depends on. */
+ilu_status ilu_get_levels(void* h, int32_t which, int32_t* lev, int32_t* nlev);
+
+/* Combined L\U values (host double[nnz(A_s)]) of the device factorisation of local
+   block s in the local CSR pattern (local order: interior then interface, ascending
+   original index): fact = 1 the factor giving L_B, U_B, W, Z; fact = 2 the one giving
+   L_S, U_S. ILU_ERR_ARG if that factor does not have the pattern of A_s (ILUT). */
+ilu_status ilu_get_local_factor(void* h, int32_t s, int32_t fact, double* val);
+
+/* y = A x with the handle's FP64 CSR SpMV kernel (x, y DEVICE double[n], original
+   ordering, no aliasing). Asynchronous on opts.stream. */
+ilu_status ilu_spmv(void* h, const double* x, double* y);
+
+/* The inner Schur solve alone (Eq. preSS with inner_iters GMRES steps, x0 = 0):
+   gp, y DEVICE double[n2] in interface numbering. Asynchronous. */
+ilu_status ilu_inner_solve(void* h, const double* gp, double* y);
+
+/* Accumulated device time per kernel class since the last reset, when profiling is
+   enabled with ilu_profile(h, 1): names[i] (static strings), ms[i], launches[i] for
+   i < *count (capacity in *count on entry). Profiling brackets each class's launches
+   with CUDA events on opts.stream and disables graph capture while on. */
+ilu_status ilu_profile(void* h, int32_t enable);
+ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* launches,
+                            int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,286 @@
+"""Python binding of ilu2l, the GB300-native two-level ILU domain-decomposition
+preconditioner and flexible GMRES solver (C ABI in ``include/ilu2l.h``).
+
+Argument marshalling only: every step of the setup's numeric phase, the apply and the
+solver runs in the CUDA kernels of ``libilu2l.so``. Device vectors are torch CUDA
+float64 tensors (PyTorch provides device memory and streams); matrices and partitions
+are host numpy arrays. There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libilu2l.so")
+
+ILU_OK, ILU_ERR_ARG, ILU_ERR_CSR, ILU_ERR_OOM, ILU_ERR_ZERO_PIVOT = 0, 1, 2, 3, 4
+ILU_ERR_NOT_CONVERGED, ILU_ERR_BREAKDOWN, ILU_ERR_TIMEOUT, ILU_ERR_CUDA = 5, 6, 7, 8
+ILU_ERR_TOO_LARGE, ILU_ERR_UNSUPPORTED = 9, 10
+VARIANTS = {"bj": 0, "schur": 1}
+FACTORS = {"ilu0": 0, "milu0": 1, "ilut": 2}
+FORMS = {"auto": 0, "wz": 1, "ef": 2}
+PRECS = {"fp64": 0, "fp32": 1}
+LEVELS = {"LA": 0, "UA": 1, "LB": 2, "UB": 3, "LS": 4, "US": 5}
+
+
+class IluError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} (status {status})")
+        self.status = status
+
+
+class ilu_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p),
+                ("colind", C.c_void_p), ("val", C.c_void_p)]
+
+
+class ilu_opts(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("factor_B", C.c_int32), ("factor_S", C.c_int32),
+                ("form", C.c_int32), ("ilut_tau", C.c_double), ("ilut_p", C.c_int32),
+                ("inner_iters", C.c_int32), ("pc_precision", C.c_int32), ("ordering", C.c_int32),
+                ("pivot_eps", C.c_double), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
+                ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
+                ("analysis_only", C.c_int32)]
+
+
+class ilu_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("rel_res_true", C.c_double),
+                ("rel_res_est", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("status", C.c_int32), ("npert", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libilu2l.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, I, D, I64 = C.c_void_p, C.c_int32, C.c_double, C.c_int64
+        sig = {
+            "ilu_opts_default": (None, [P]),
+            "ilu_setup": (I, [P, P, I, P, P]),
+            "ilu_apply": (I, [P, P, P]),
+            "gmres_solve": (I, [P, P, P, D, I, I, P]),
+            "ilu_free": (I, [P]),
+            "ilu_status_str": (C.c_char_p, [I]),
+            "ilu_get_sizes": (I, [P, P]),
+            "ilu_get_perm": (I, [P, P, P, P, P, P]),
+            "ilu_get_levels": (I, [P, I, P, P]),
+            "ilu_get_local_factor": (I, [P, I, I, P]),
+            "ilu_spmv": (I, [P, P, P]),
+            "ilu_inner_solve": (I, [P, P, P]),
+            "ilu_profile": (I, [P, I]),
+            "ilu_profile_read": (I, [P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    try:
+        return lib().ilu_status_str(int(s)).decode()
+    except RuntimeError:
+        return "unknown"
+
+
+def _ptr(t):
+    """device pointer of a contiguous torch CUDA float64 tensor"""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class Opts:
+    """Mirror of ilu_opts with readable enums."""
+    variant: str = "schur"
+    factor_B: str = "ilu0"
+    factor_S: str = "milu0"
+    form: str = "auto"
+    ilut_tau: float = 1e-3
+    ilut_p: int = 10
+    inner_iters: int = 3
+    pc_precision: str = "fp32"
+    pivot_eps: float = 1e-8
+    use_graphs: bool = True
+    block_threads: int = 0
+    stream: int | None = None
+    spin_limit: int = 0
+    analysis_only: bool = False
+
+    def to_c(self) -> ilu_opts:
+        o = ilu_opts()
+        lib().ilu_opts_default(C.byref(o))
+        o.variant = VARIANTS[self.variant]
+        o.factor_B = FACTORS[self.factor_B]
+        o.factor_S = FACTORS[self.factor_S]
+        o.form = FORMS[self.form]
+        o.ilut_tau = float(self.ilut_tau)
+        o.ilut_p = int(self.ilut_p)
+        o.inner_iters = int(self.inner_iters)
+        o.pc_precision = PRECS[self.pc_precision]
+        o.pivot_eps = float(self.pivot_eps)
+        o.use_graphs = int(bool(self.use_graphs))
+        o.block_threads = int(self.block_threads)
+        o.spin_limit = int(self.spin_limit)
+        o.analysis_only = int(bool(self.analysis_only))
+        if self.analysis_only:
+            o.stream = None
+        elif self.stream is None:
+            import torch
+            o.stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        else:
+            o.stream = C.c_void_p(int(self.stream))
+        return o
+
+
+class Handle:
+    """Owns one ilu2l handle (ilu_free on close / garbage collection)."""
+
+    def __init__(self, ptr: C.c_void_p, n: int, p: int, opts: Opts):
+        self._h = ptr
+        self.n = n
+        self.p = p
+        self.opts = opts
+
+    @property
+    def ptr(self):
+        if not self._h:
+            raise RuntimeError("handle already freed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().ilu_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- introspection ----
+    def sizes(self) -> dict:
+        out = np.zeros(12, np.int64)
+        _check(lib().ilu_get_sizes(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_sizes")
+        keys = ["n", "p", "n1", "n2", "nnz", "nnz_coff", "npert", "nlev_LB", "nlev_UB",
+                "nlev_LS", "nlev_US", "max_ns"]
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def perm(self) -> dict:
+        n, p = self.n, self.p
+        perm = np.empty(n, np.int32)
+        iperm = np.empty(n, np.int32)
+        int_ptr = np.empty(p + 1, np.int32)
+        if_ptr = np.empty(p + 1, np.int32)
+        iface = np.empty(n, np.int32)
+        _check(lib().ilu_get_perm(self.ptr, *[a.ctypes.data_as(C.c_void_p) for a in
+                                              (perm, iperm, int_ptr, if_ptr, iface)]), "ilu_get_perm")
+        return dict(perm=perm, iperm=iperm, int_ptr=int_ptr, if_ptr=if_ptr, iface=iface)
+
+    def levels(self, which) -> tuple[np.ndarray, int]:
+        w = LEVELS[which] if isinstance(which, str) else int(which)
+        lev = np.empty(self.n, np.int32)
+        nl = C.c_int32(0)
+        _check(lib().ilu_get_levels(self.ptr, w, lev.ctypes.data_as(C.c_void_p), C.byref(nl)),
+               "ilu_get_levels")
+        return lev, nl.value
+
+    def local_factor(self, s: int, fact: int, nnz: int) -> np.ndarray:
+        v = np.empty(nnz)
+        _check(lib().ilu_get_local_factor(self.ptr, int(s), int(fact), v.ctypes.data_as(C.c_void_p)),
+               "ilu_get_local_factor")
+        return v
+
+    def spmv(self, x, y):
+        _check(lib().ilu_spmv(self.ptr, _ptr(x), _ptr(y)), "ilu_spmv")
+
+    def inner_solve(self, gp, y):
+        _check(lib().ilu_inner_solve(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve")
+
+    def profile(self, enable: bool):
+        _check(lib().ilu_profile(self.ptr, int(enable)), "ilu_profile")
+
+    def profile_read(self) -> dict:
+        cap = 32
+        names = (C.c_char_p * cap)()
+        ms = np.zeros(cap)
+        nl = np.zeros(cap, np.int64)
+        cnt = C.c_int32(cap)
+        _check(lib().ilu_profile_read(self.ptr, C.cast(names, C.c_void_p), ms.ctypes.data_as(C.c_void_p),
+                                      nl.ctypes.data_as(C.c_void_p), C.byref(cnt)), "ilu_profile_read")
+        return {names[i].decode(): (float(ms[i]), int(nl[i])) for i in range(min(cnt.value, cap))}
+
+
+def _check(st, what):
+    if st != ILU_OK:
+        raise IluError(st, what)
+
+
+# ---- the C-ABI calls, same names ----------------------------------------------------
+
+
+def ilu_setup(n, rowptr, colind, val, part, p, opts: Opts | None = None) -> Handle:
+    """Setup of the preconditioner for the host CSR matrix (rowptr, colind, val) and the
+    partition part[n] into p subdomains. Raises IluError on a non-OK status."""
+    opts = opts or Opts()
+    rowptr = _np(rowptr, np.int32)
+    colind = _np(colind, np.int32)
+    val = _np(val, np.float64)
+    part = _np(part, np.int32)
+    A = ilu_csr(int(n), int(rowptr[-1]) if rowptr.size else 0, rowptr.ctypes.data,
+                colind.ctypes.data, val.ctypes.data)
+    o = opts.to_c()
+    h = C.c_void_p()
+    _check(lib().ilu_setup(C.byref(A), part.ctypes.data_as(C.c_void_p), int(p), C.byref(o), C.byref(h)),
+           "ilu_setup")
+    return Handle(h, int(n), int(p), opts)
+
+
+def ilu_setup_problem(prob, opts: Opts | None = None) -> Handle:
+    return ilu_setup(prob.n, prob.rowptr, prob.colind, prob.val, prob.part, prob.p, opts)
+
+
+def ilu_apply(h: Handle, r, z) -> None:
+    """z = M^{-1} r for torch CUDA float64 vectors in the original ordering."""
+    _check(lib().ilu_apply(h.ptr, _ptr(r), _ptr(z)), "ilu_apply")
+
+
+def gmres_solve(h: Handle, b, x, rtol: float = 1e-8, restart: int = 50, maxit: int = 10000,
+                raise_on_fail: bool = False) -> dict:
+    """FGMRES(restart) for A x = b; x (torch CUDA float64) holds x0 on entry."""
+    info = ilu_solve_info()
+    st = lib().gmres_solve(h.ptr, _ptr(b), _ptr(x), float(rtol), int(restart), int(maxit), C.byref(info))
+    if st not in (ILU_OK, ILU_ERR_NOT_CONVERGED) or (raise_on_fail and st != ILU_OK):
+        raise IluError(st, "gmres_solve")
+    return dict(status=int(st), iters=info.iters, restarts=info.restarts,
+                rel_res_true=info.rel_res_true, rel_res_est=info.rel_res_est,
+                setup_ms=info.setup_ms, solve_ms=info.solve_ms, npert=info.npert)
+
+
+def ilu_free(h: Handle) -> None:
+    h.close()
+
+
+__all__ = ["Opts", "Handle", "IluError", "ilu_setup", "ilu_setup_problem", "ilu_apply",
+           "gmres_solve", "ilu_free", "status_str", "lib", "LIB_PATH"]

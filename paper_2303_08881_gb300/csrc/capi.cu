@@ -1,0 +1,525 @@
+// capi.cu -- the C ABI of ilu2l (include/ilu2l.h): handle lifecycle, device uploads, the
+// device factorisation, apply dispatch and the FGMRES driver (one CUDA graph per cycle,
+// one host read of the device control block per cycle).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+namespace ilu2l {
+
+const char* kProfNames[PC_COUNT] = {"apply_fwd", "apply_inner", "apply_bwd", "apply_bj", "spmv_dot",
+                                    "cgs", "norm_givens", "update", "residual"};
+
+namespace {
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return map_err(e_); \
+    } while (0)
+
+ilu_status map_err(cudaError_t e) {
+    if (e == cudaSuccess) return ILU_OK;
+    if (e == cudaErrorMemoryAllocation) return ILU_ERR_OOM;
+    return ILU_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t upload(Handle& h, T** dst, const std::vector<T>& src) {
+    cudaError_t e = cudaSuccess;
+    *dst = h.alloc<T>(src.size(), &e);
+    if (!*dst) return e;
+    if (!src.empty()) e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h.st);
+    return e;
+}
+
+template <class T>
+ilu_status upload_prog(Handle& h, int id) {
+    ProgHost& P = h.prog[id];
+    ProgBufs& B = h.pb[id];
+    if (P.sub_lvl.size() < (size_t)h.p + 1) P.sub_lvl.resize(h.p + 1, P.sub_lvl.empty() ? 0 : P.sub_lvl.back());
+    CK(upload(h, &B.sub_lvl, P.sub_lvl));
+    CK(upload(h, &B.lvl_ptr, P.lvl_ptr));
+    CK(upload(h, &B.prow, P.prow));
+    CK(upload(h, &B.pptr, P.pptr));
+    CK(upload(h, &B.pcol, P.pcol));
+    CK(upload(h, &B.psrc, P.psrc));
+    CK(upload(h, &B.pdsrc, P.pdsrc));
+    cudaError_t e = cudaSuccess;
+    B.pval = h.alloc<T>(P.pcol.size(), &e);
+    if (!B.pval) return map_err(e);
+    B.pdinv = h.alloc<T>(P.prow.size(), &e);
+    if (!B.pdinv) return map_err(e);
+    CK(launch_pack<T>(P, B.psrc, B.pdsrc, h.d_vals, (T*)B.pval, (T*)B.pdinv, h.st));
+    return ILU_OK;
+}
+
+template <class T>
+ilu_status device_setup_t(Handle& h) {
+    cudaError_t e = cudaSuccess;
+    const int n = h.n;
+    // shared-memory working vector
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h.device));
+    const int64_t cap = std::max<int64_t>(0, (int64_t)optin - 20 * 1024) / (int64_t)sizeof(T);
+    h.smem_len = (int32_t)std::min<int64_t>(h.max_ns, cap);
+    CK(configure_apply<T>((size_t)h.smem_len * sizeof(T)));
+    const bool need_xg = h.max_ns > h.smem_len;
+    h.d_xg = h.alloc<T>(need_xg ? (size_t)n : 1, &e);
+    if (!h.d_xg) return map_err(e);
+    h.d_fq = h.alloc<T>((size_t)std::max(n, 1), &e);
+    if (!h.d_fq) return map_err(e);
+    // C_off in the PC type
+    std::vector<T> cv(h.coff_v.begin(), h.coff_v.end());
+    CK(upload(h, &h.d_coff_rp, h.coff_rp));
+    CK(upload(h, &h.d_coff_ci, h.coff_ci));
+    T* dcv = nullptr;
+    CK(upload(h, &dcv, cv));
+    h.d_coff_v = dcv;
+    // inner GMRES workspace
+    h.d_iV = h.alloc<T>((size_t)(h.inner_k + 1) * std::max(h.n2, 1), &e);
+    h.d_iW0 = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
+    h.d_iW1 = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
+    if (!h.d_iV || !h.d_iW0 || !h.d_iW1) return map_err(e);
+    cv.clear();
+    cv.shrink_to_fit();
+    if (h.variant == ILU_VARIANT_BJ) {
+        ilu_status s = upload_prog<T>(h, PR_BJ);
+        if (s != ILU_OK) return s;
+    } else {
+        for (int id : {PR_FWD, PR_S, PR_BWD}) {
+            ilu_status s = upload_prog<T>(h, id);
+            if (s != ILU_OK) return s;
+        }
+    }
+    return ILU_OK;
+}
+
+ilu_status device_setup(Handle& h) {
+    cudaError_t e = cudaSuccess;
+    CK(cudaGetDevice(&h.device));
+    CK(cudaDeviceGetAttribute(&h.sm_count, cudaDevAttrMultiProcessorCount, h.device));
+    const int n = h.n, p = h.p;
+    CK(upload(h, &h.d_qoff, h.qoff));
+    CK(upload(h, &h.d_nint, h.nint));
+    CK(upload(h, &h.d_if_ptr, h.if_ptr));
+    CK(upload(h, &h.d_q_orig, h.q_orig));
+    CK(upload(h, &h.d_q_rp, h.q_rp));
+    CK(upload(h, &h.d_q_ci, h.q_ci));
+    CK(upload(h, &h.d_q_dpos, h.q_dpos));
+    // value array [F1 | F2 | A_local]
+    h.d_vals = h.alloc<double>((size_t)h.nvals, &e);
+    if (!h.d_vals) return map_err(e);
+    if (!h.q_v.empty())
+        CK(cudaMemcpyAsync(h.d_vals + h.a_base, h.q_v.data(), h.q_v.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, h.st));
+    if (!h.f1_device && !h.f1_host_vals.empty())
+        CK(cudaMemcpyAsync(h.d_vals + h.f1.base, h.f1_host_vals.data(),
+                           h.f1_host_vals.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    h.d_err = h.alloc<int32_t>(1, &e);
+    h.d_npert = h.alloc<int32_t>(1, &e);
+    if (!h.d_err || !h.d_npert) return map_err(e);
+    CK(cudaMemsetAsync(h.d_err, 0, sizeof(int32_t), h.st));
+    CK(cudaMemsetAsync(h.d_npert, 0, sizeof(int32_t), h.st));
+    // numeric factorisation schedule
+    CK(upload(h, &h.d_num_sub, h.numprog.sub_lvl));
+    CK(upload(h, &h.d_num_lvl, h.numprog.lvl_ptr));
+    CK(upload(h, &h.d_num_row, h.numprog.prow));
+    if (h.f1_device) CK(launch_ilu_numeric(h, h.d_vals + h.f1.base, h.kB == ILU_FACT_MILU0 ? 1 : 0, h.st));
+    if (!h.f2_alias) CK(launch_ilu_numeric(h, h.d_vals + h.f2.base, h.kS == ILU_FACT_MILU0 ? 1 : 0, h.st));
+    int32_t herr = 0, hpert = 0;
+    CK(cudaMemcpyAsync(&herr, h.d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, h.st));
+    CK(cudaMemcpyAsync(&hpert, h.d_npert, sizeof(int32_t), cudaMemcpyDeviceToHost, h.st));
+    CK(cudaStreamSynchronize(h.st));
+    if (herr & 1) return ILU_ERR_ZERO_PIVOT;
+    h.npert += hpert;
+    // inner control + partials
+    h.d_ipart = h.alloc<double>((size_t)3 * (kMaxInner + 1) * p, &e);
+    h.d_ictl = h.alloc<InnerCtl>(1, &e);
+    if (!h.d_ipart || !h.d_ictl) return map_err(e);
+    CK(cudaMemsetAsync(h.d_ictl, 0, sizeof(InnerCtl), h.st));
+    ilu_status s = (h.prec == ILU_PREC_FP32) ? device_setup_t<float>(h) : device_setup_t<double>(h);
+    if (s != ILU_OK) return s;
+    CK(cudaStreamSynchronize(h.st));
+    (void)n;
+    return ILU_OK;
+}
+
+ilu_status ensure_fgmres(Handle& h, int m) {
+    if (h.fg_m >= m && h.fg.V) {
+        h.fg.m = m;
+        return ILU_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    const size_t n = (size_t)std::max(h.n, 1);
+    h.fg_G = h.sm_count * 4;
+    h.fg_threads = 256;
+    FgDev f{};
+    f.V = h.alloc<double>((size_t)(m + 1) * n, &e);
+    f.Z = h.alloc<double>((size_t)m * n, &e);
+    f.w = h.alloc<double>(n, &e);
+    f.H = h.alloc<double>((size_t)(m + 1) * m, &e);
+    f.cs = h.alloc<double>((size_t)m + 1, &e);
+    f.sn = h.alloc<double>((size_t)m + 1, &e);
+    f.g = h.alloc<double>((size_t)m + 1, &e);
+    f.h2 = h.alloc<double>((size_t)m + 1, &e);
+    f.hnext = h.alloc<double>(1, &e);
+    f.part = h.alloc<double>((size_t)(m + 2) * h.fg_G, &e);
+    f.ctl = h.alloc<FgCtl>(1, &e);
+    if (!f.V || !f.Z || !f.w || !f.H || !f.cs || !f.sn || !f.g || !f.h2 || !f.hnext || !f.part || !f.ctl)
+        return map_err(e);
+    CK(cudaMemsetAsync(f.ctl, 0, sizeof(FgCtl), h.st));
+    f.m = m;
+    f.G = h.fg_G;
+    h.fg = f;
+    h.fg_m = m;
+    if (h.cycle_exec) {
+        cudaGraphExecDestroy(h.cycle_exec);
+        h.cycle_exec = nullptr;
+    }
+    if (!h.h_ctl) CK(cudaMallocHost(&h.h_ctl, sizeof(FgCtl)));
+    return ILU_OK;
+}
+
+template <class T>
+cudaError_t apply_t(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
+    if (h.variant == ILU_VARIANT_BJ) return launch_bj<T>(h, r, z, done, st);
+    cudaError_t e = launch_schur_fwd<T>(h, r, done, st);
+    if (e == cudaSuccess) e = launch_inner<T>(h, done, st);
+    if (e == cudaSuccess) e = launch_schur_bwd<T>(h, r, z, done, st);
+    return e;
+}
+
+cudaError_t apply_any(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
+    return (h.prec == ILU_PREC_FP32) ? apply_t<float>(h, r, z, done, st) : apply_t<double>(h, r, z, done, st);
+}
+
+// one FGMRES cycle: m steps (each a no-op once the cycle is done), update, true residual
+cudaError_t enqueue_cycle(const Handle& h, const double* b, double* x, cudaStream_t st) {
+    const size_t n = (size_t)h.n;
+    const int32_t* done = &h.fg.ctl->cycle_done;
+    for (int j = 0; j < h.fg.m; j++) {
+        cudaError_t e = apply_any(h, h.fg.V + (size_t)j * n, h.fg.Z + (size_t)j * n, done, st);
+        if (e != cudaSuccess) return e;
+        e = launch_fg_step(h, j, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_fg_end(h, b, x, st);
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+}  // namespace ilu2l
+
+using namespace ilu2l;
+
+extern "C" {
+
+void ilu_opts_default(ilu_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->variant = ILU_VARIANT_SCHUR;
+    o->factor_B = ILU_FACT_ILU0;
+    o->factor_S = ILU_FACT_MILU0;
+    o->form = ILU_FORM_AUTO;
+    o->ilut_tau = 1e-3;
+    o->ilut_p = 10;
+    o->inner_iters = 3;
+    o->pc_precision = ILU_PREC_FP32;
+    o->ordering = 0;
+    o->pivot_eps = 1e-8;
+    o->stream = nullptr;
+    o->spin_limit = 0;
+    o->use_graphs = 1;
+    o->block_threads = 0;
+    o->analysis_only = 0;
+}
+
+const char* ilu_status_str(ilu_status s) {
+    switch (s) {
+        case ILU_OK: return "ok";
+        case ILU_ERR_ARG: return "invalid argument";
+        case ILU_ERR_CSR: return "malformed CSR matrix";
+        case ILU_ERR_OOM: return "out of memory";
+        case ILU_ERR_ZERO_PIVOT: return "zero pivot";
+        case ILU_ERR_NOT_CONVERGED: return "not converged";
+        case ILU_ERR_BREAKDOWN: return "Krylov breakdown";
+        case ILU_ERR_TIMEOUT: return "device wait timed out";
+        case ILU_ERR_CUDA: return "CUDA error";
+        case ILU_ERR_TOO_LARGE: return "problem too large";
+        case ILU_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+ilu_status ilu_free(void* hp) {
+    if (!hp) return ILU_OK;
+    Handle* h = (Handle*)hp;
+    if (!h->o.analysis_only) cudaStreamSynchronize(h->st);
+    if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+    return ILU_OK;
+}
+
+ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu_opts* opts, void** hout) {
+    if (!hout) return ILU_ERR_ARG;
+    *hout = nullptr;
+    if (!A || !part || p < 1) return ILU_ERR_ARG;
+    const double t0 = now_ms();
+    Handle* h = new (std::nothrow) Handle;
+    if (!h) return ILU_ERR_OOM;
+    if (opts)
+        h->o = *opts;
+    else
+        ilu_opts_default(&h->o);
+    const ilu_opts& o = h->o;
+    if ((o.variant != ILU_VARIANT_BJ && o.variant != ILU_VARIANT_SCHUR) || o.factor_B < 0 || o.factor_B > 2 ||
+        o.factor_S < 0 || o.factor_S > 1 || (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32) ||
+        o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
+        (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
+        (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024))) {
+        delete h;
+        return ILU_ERR_ARG;
+    }
+    if (o.ordering != 0) {
+        delete h;
+        return ILU_ERR_UNSUPPORTED;
+    }
+    h->variant = o.variant;
+    h->kB = o.factor_B;
+    h->kS = o.factor_S;
+    h->prec = o.pc_precision;
+    h->inner_k = o.inner_iters;
+    h->form = (o.variant == ILU_VARIANT_SCHUR && (o.factor_B == ILU_FACT_ILUT || o.form == ILU_FORM_EF))
+                  ? ILU_FORM_EF
+                  : ILU_FORM_WZ;
+    h->st = (cudaStream_t)o.stream;
+    h->threads = o.block_threads ? o.block_threads : 256;
+    ilu_status s = host_setup(*h, A, part, p);
+    if (s == ILU_OK && o.analysis_only) {
+        h->setup_ms = now_ms() - t0;
+        *hout = h;
+        return ILU_OK;
+    }
+    if (s == ILU_OK) {
+        s = device_setup(*h);
+        if (s == ILU_OK) {
+            // the original CSR for the FP64 SpMV
+            cudaError_t e = cudaSuccess;
+            h->d_A_rp = h->alloc<int32_t>((size_t)A->n + 1, &e);
+            h->d_A_ci = h->alloc<int32_t>((size_t)A->nnz, &e);
+            h->d_A_v = h->alloc<double>((size_t)A->nnz, &e);
+            if (!h->d_A_rp || !h->d_A_ci || !h->d_A_v) s = map_err(e);
+            if (s == ILU_OK) {
+                e = cudaMemcpyAsync(h->d_A_rp, A->rowptr, ((size_t)A->n + 1) * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->st);
+                if (e == cudaSuccess && A->nnz)
+                    e = cudaMemcpyAsync(h->d_A_ci, A->colind, (size_t)A->nnz * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice, h->st);
+                if (e == cudaSuccess && A->nnz)
+                    e = cudaMemcpyAsync(h->d_A_v, A->val, (size_t)A->nnz * sizeof(double), cudaMemcpyHostToDevice,
+                                        h->st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+                s = map_err(e);
+            }
+        }
+    }
+    if (s != ILU_OK) {
+        ilu_free(h);
+        return s;
+    }
+    // host copies of the value arrays are no longer needed
+    std::vector<double>().swap(h->q_v);
+    std::vector<double>().swap(h->f1_host_vals);
+    h->setup_ms = now_ms() - t0;
+    *hout = h;
+    return ILU_OK;
+}
+
+ilu_status ilu_apply(void* hp, const double* r, double* z) {
+    if (!hp || !r || !z || r == z) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only) return ILU_ERR_ARG;
+    return map_err(apply_any(*h, r, z, nullptr, h->st));
+}
+
+ilu_status ilu_spmv(void* hp, const double* x, double* y) {
+    if (!hp || !x || !y || x == y) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only) return ILU_ERR_ARG;
+    return map_err(launch_spmv(*h, x, y, h->st));
+}
+
+ilu_status ilu_inner_solve(void* hp, const double* gp, double* y) {
+    if (!hp || !gp || !y || gp == y) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only) return ILU_ERR_ARG;
+    if (h->variant != ILU_VARIANT_SCHUR) return ILU_ERR_ARG;
+    cudaError_t e = (h->prec == ILU_PREC_FP32) ? launch_inner_io<float>(*h, gp, y, h->st)
+                                                : launch_inner_io<double>(*h, gp, y, h->st);
+    return map_err(e);
+}
+
+ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_t restart, int32_t maxit,
+                       ilu_solve_info* info) {
+    if (!hp || !b || !x || b == x || restart < 1 || restart > kMaxRestart || maxit < 0 || !(rtol >= 0.0))
+        return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only) return ILU_ERR_ARG;
+    const double t0 = now_ms();
+    ilu_status s = ensure_fgmres(*h, restart);
+    if (s != ILU_OK) return s;
+    FgCtl init{};
+    init.rtol = rtol;
+    init.maxit = maxit;
+    init.m = restart;
+    *h->h_ctl = init;
+    CK(cudaMemcpyAsync(h->fg.ctl, h->h_ctl, sizeof(FgCtl), cudaMemcpyHostToDevice, h->st));
+    CK(launch_fg_start(*h, b, x, h->st));
+    const bool graphs = h->o.use_graphs && !h->prof;
+    if (graphs && (h->cycle_exec == nullptr || h->cycle_b != b || h->cycle_x != x || h->cycle_m != restart)) {
+        if (h->cycle_exec) {
+            cudaGraphExecDestroy(h->cycle_exec);
+            h->cycle_exec = nullptr;
+        }
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_cycle(*h, b, x, cs);
+            e = cudaStreamEndCapture(cs, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->cycle_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return map_err(e);
+        h->cycle_b = b;
+        h->cycle_x = x;
+        h->cycle_m = restart;
+    }
+    int cycles = 0;
+    ilu_status result = ILU_OK;
+    for (;;) {
+        CK(cudaMemcpyAsync(h->h_ctl, h->fg.ctl, sizeof(FgCtl), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        const FgCtl& c = *h->h_ctl;
+        if (c.converged) {
+            if (c.bnorm == 0.0) CK(cudaMemsetAsync(x, 0, (size_t)h->n * sizeof(double), h->st));
+            result = ILU_OK;
+            break;
+        }
+        if (c.total >= maxit) {
+            result = ILU_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (graphs)
+            CK(cudaGraphLaunch(h->cycle_exec, h->st));
+        else
+            CK(enqueue_cycle(*h, b, x, h->st));
+        cycles++;
+    }
+    CK(cudaStreamSynchronize(h->st));
+    const FgCtl& c = *h->h_ctl;
+    if (info) {
+        info->iters = c.total;
+        info->restarts = cycles;
+        info->rel_res_true = c.bnorm > 0 ? c.res_true / c.bnorm : 0.0;
+        info->rel_res_est = c.bnorm > 0 ? c.est / c.bnorm : 0.0;
+        info->setup_ms = h->setup_ms;
+        info->solve_ms = now_ms() - t0;
+        info->status = result;
+        info->npert = h->npert;
+    }
+    return result;
+}
+
+ilu_status ilu_get_sizes(void* hp, int64_t* out) {
+    if (!hp || !out) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    out[0] = h->n;
+    out[1] = h->p;
+    out[2] = h->n1;
+    out[3] = h->n2;
+    out[4] = h->nnz;
+    out[5] = h->nnz_coff;
+    out[6] = h->npert;
+    out[7] = h->nlev[2];
+    out[8] = h->nlev[3];
+    out[9] = h->nlev[4];
+    out[10] = h->nlev[5];
+    out[11] = h->max_ns;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_perm(void* hp, int32_t* perm, int32_t* iperm, int32_t* int_ptr, int32_t* if_ptr,
+                        int32_t* iface) {
+    if (!hp) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (perm) std::memcpy(perm, h->perm.data(), h->perm.size() * sizeof(int32_t));
+    if (iperm) std::memcpy(iperm, h->iperm.data(), h->iperm.size() * sizeof(int32_t));
+    if (int_ptr) std::memcpy(int_ptr, h->int_ptr.data(), h->int_ptr.size() * sizeof(int32_t));
+    if (if_ptr) std::memcpy(if_ptr, h->if_ptr.data(), h->if_ptr.size() * sizeof(int32_t));
+    if (iface)
+        for (int32_t i = 0; i < h->n; i++) iface[i] = h->iface[i];
+    return ILU_OK;
+}
+
+ilu_status ilu_get_levels(void* hp, int32_t which, int32_t* lev, int32_t* nlev) {
+    if (!hp || !lev || which < 0 || which > 5) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    std::memcpy(lev, h->lev[which].data(), h->lev[which].size() * sizeof(int32_t));
+    if (nlev) *nlev = h->nlev[which];
+    return ILU_OK;
+}
+
+ilu_status ilu_get_local_factor(void* hp, int32_t s, int32_t fact, double* val) {
+    if (!hp || !val) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only || s < 0 || s >= h->p || (fact != 1 && fact != 2)) return ILU_ERR_ARG;
+    const FPat& F = (fact == 1) ? h->f1 : h->f2;
+    const bool pattern_of_A = (fact == 1) ? h->f1_device : true;
+    if (!pattern_of_A) return ILU_ERR_ARG;
+    const int32_t q0 = h->qoff[s], q1 = h->qoff[s + 1];
+    const int64_t b = h->q_rp[q0], e = h->q_rp[q1];
+    CK(cudaMemcpy(val, h->d_vals + F.base + b, (size_t)(e - b) * sizeof(double), cudaMemcpyDeviceToHost));
+    return ILU_OK;
+}
+
+ilu_status ilu_profile(void* hp, int32_t enable) {
+    if (!hp) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    h->prof = enable != 0;
+    for (int i = 0; i < PC_COUNT; i++) {
+        h->prof_ms[i] = 0.0;
+        h->prof_n[i] = 0;
+    }
+    return ILU_OK;
+}
+
+ilu_status ilu_profile_read(void* hp, const char** names, double* ms, int64_t* launches, int32_t* count) {
+    if (!hp || !count) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    const int m = std::min<int>(*count, PC_COUNT);
+    for (int i = 0; i < m; i++) {
+        if (names) names[i] = kProfNames[i];
+        if (ms) ms[i] = h->prof_ms[i];
+        if (launches) launches[i] = h->prof_n[i];
+    }
+    *count = PC_COUNT;
+    return ILU_OK;
+}
+
+}  // extern "C"

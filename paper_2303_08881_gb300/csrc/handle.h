@@ -1,0 +1,161 @@
+// handle.h -- the ilu2l handle: host-side setup products and device buffers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace ilu2l {
+
+enum ProgId { PR_BJ = 0, PR_FWD = 1, PR_S = 2, PR_BWD = 3, PR_COUNT = 4 };
+
+// A factor's sparsity pattern over all Q rows (rows outside the factor are empty).
+// Values live in the handle's value array at [base + k] for pattern entry k.
+struct FPat {
+    std::vector<int32_t> rp, ci, dpos;  // ci: local column; dpos: diagonal entry or -1
+    int64_t base = 0;
+};
+
+struct ProgBufs {
+    int32_t *sub_lvl = nullptr, *lvl_ptr = nullptr, *prow = nullptr, *pptr = nullptr,
+            *pcol = nullptr, *psrc = nullptr, *pdsrc = nullptr;
+    void* pval = nullptr;
+    void* pdinv = nullptr;
+};
+
+struct Handle {
+    ilu_opts o{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int32_t n = 0, p = 0, n1 = 0, n2 = 0;
+    int64_t nnz = 0, nnz_coff = 0;
+    int variant = 1, form = 1, prec = 1, kB = 0, kS = 1;
+    bool f2_alias = false, f1_device = true;
+    int npert = 0;
+    double setup_ms = 0.0;
+    int threads = 256;       // threads of the per-subdomain kernels
+    int32_t smem_len = 0;    // working vector capacity (elements of the PC type)
+    int32_t max_ns = 0;
+    int sm_count = 152;
+
+    // host products (kept for introspection)
+    std::vector<int32_t> part, iface, perm, iperm, int_ptr, if_ptr, qoff, nint, q_orig;
+    std::vector<int32_t> q_rp, q_ci, q_dpos;  // local CSR of every A_s, Q order
+    std::vector<double> q_v;
+    std::vector<int32_t> lev[6];
+    int32_t nlev[6] = {0, 0, 0, 0, 0, 0};
+    FPat f1, f2;           // patterns of the two factorisations (f2 may equal f1)
+    std::vector<double> f1_host_vals;  // ILUT values (host-computed factor F1)
+    int64_t a_base = 0;    // region of the original local values in the value array
+    int64_t nvals = 0;
+    ProgHost prog[PR_COUNT];
+    ProgHost numprog;      // L_A levels of every A_s for the numeric factorisation
+    std::vector<int32_t> coff_rp, coff_ci;
+    std::vector<double> coff_v;
+
+    // device memory
+    std::vector<void*> allocs;
+    int32_t *d_qoff = nullptr, *d_nint = nullptr, *d_if_ptr = nullptr, *d_q_orig = nullptr;
+    int32_t *d_q_rp = nullptr, *d_q_ci = nullptr, *d_q_dpos = nullptr;
+    double* d_vals = nullptr;        // [F1 | F2 | A_local] FP64 values
+    int32_t *d_A_rp = nullptr, *d_A_ci = nullptr;
+    double* d_A_v = nullptr;         // the original matrix (FP64 SpMV)
+    ProgBufs pb[PR_COUNT];
+    int32_t *d_num_sub = nullptr, *d_num_lvl = nullptr, *d_num_row = nullptr;
+    int32_t *d_coff_rp = nullptr, *d_coff_ci = nullptr;
+    void* d_coff_v = nullptr;        // PC type
+    void* d_fq = nullptr;            // f' buffer (Q order, PC type)
+    void* d_xg = nullptr;            // global working vectors for oversize subdomains
+    void* d_iV = nullptr;            // inner Arnoldi vectors
+    void* d_iW0 = nullptr;
+    void* d_iW1 = nullptr;
+    double* d_ipart = nullptr;
+    InnerCtl* d_ictl = nullptr;
+    int32_t* d_err = nullptr;        // device error word (bit flags)
+    int32_t* d_npert = nullptr;
+    double* d_tmp_in = nullptr;      // n2-vector staging for ilu_inner_solve
+    int32_t inner_k = 3;
+
+    // FGMRES workspace (grown on demand)
+    FgDev fg{};
+    int32_t fg_m = 0;
+    int fg_G = 0;
+    int fg_threads = 256;
+    cudaGraphExec_t cycle_exec = nullptr;
+    int32_t cycle_m = 0;
+    const double* cycle_b = nullptr;
+    double* cycle_x = nullptr;
+    FgCtl* h_ctl = nullptr;          // pinned host mirror of the control block
+
+    // profiling
+    bool prof = false;
+    double prof_ms[PC_COUNT] = {};
+    int64_t prof_n[PC_COUNT] = {};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    template <class T>
+    T* alloc(size_t count, cudaError_t* err) {
+        void* p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            *err = e;
+            return nullptr;
+        }
+        allocs.push_back(p);
+        return (T*)p;
+    }
+
+    SubDev sub() const {
+        SubDev s;
+        s.qoff = d_qoff;
+        s.nint = d_nint;
+        s.if_ptr = d_if_ptr;
+        s.q_orig = d_q_orig;
+        s.p = p;
+        s.n = n;
+        s.n1 = n1;
+        s.n2 = n2;
+        s.smem_len = smem_len;
+        return s;
+    }
+
+    template <class T>
+    ProgDev<T> progdev(int id) const {
+        ProgDev<T> d;
+        d.sub_lvl = pb[id].sub_lvl;
+        d.lvl_ptr = pb[id].lvl_ptr;
+        d.prow = pb[id].prow;
+        d.pptr = pb[id].pptr;
+        d.pcol = pb[id].pcol;
+        d.pval = (const T*)pb[id].pval;
+        d.pdinv = (const T*)pb[id].pdinv;
+        return d;
+    }
+
+    template <class T>
+    InnerDev<T> innerdev() const {
+        InnerDev<T> d;
+        d.coff_rp = d_coff_rp;
+        d.coff_ci = d_coff_ci;
+        d.coff_v = (const T*)d_coff_v;
+        d.V = (T*)d_iV;
+        d.W0 = (T*)d_iW0;
+        d.W1 = (T*)d_iW1;
+        d.part = d_ipart;
+        d.ctl = d_ictl;
+        d.k = inner_k;
+        return d;
+    }
+};
+
+// host setup (setup_host.cpp): validation, classification, permutation, local blocks,
+// C_off, factor patterns (ILUT values on the host), level sets and level programs.
+ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p);
+
+}  // namespace ilu2l

@@ -1,0 +1,150 @@
+// internal.h -- device data layout and launchers of the ilu2l library (not part of the ABI).
+//
+// Orderings used inside the library:
+//   original   : the caller's row numbering (vectors crossing the ABI);
+//   P (global) : interior rows grouped by subdomain, then interface rows grouped by
+//                subdomain (Sec. 2.2.1, Eq. equ22); interface numbering = P index - n1;
+//   Q (local)  : subdomain-major, inside subdomain s its local order [interior_s;
+//                interface_s]; subdomain s owns Q rows [qoff[s], qoff[s+1]).
+// Every per-subdomain kernel runs one CTA per subdomain on its Q range and keeps the
+// subdomain's working vector in shared memory when it fits (else in a global scratch).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ilu2l.h"
+
+namespace ilu2l {
+
+constexpr int kMaxInner = 32;   // inner GMRES steps supported on the device
+constexpr int kMaxRestart = 400;
+
+// ---- a level program: rows of every subdomain scheduled level by level --------------
+// Rows of subdomain s are processed in levels [sub_lvl[s], sub_lvl[s+1]); level e covers
+// packed rows [lvl_ptr[e], lvl_ptr[e+1]); packed row k updates x[prow[k]] =
+// (x[prow[k]] - sum_q pval[q] * x[pcol[q]]) * pdinv[k] over q in [pptr[k], pptr[k+1]).
+// Indices are local to the subdomain's working vector (offset by the program's base).
+struct ProgHost {
+    std::vector<int32_t> sub_lvl, lvl_ptr, prow, pptr, pcol, psrc, pdsrc;
+    int32_t max_level_rows = 0, max_levels = 0;
+    int64_t nnz() const { return (int64_t)pcol.size(); }
+};
+
+template <class T>
+struct ProgDev {
+    const int32_t* sub_lvl;
+    const int32_t* lvl_ptr;
+    const int32_t* prow;
+    const int32_t* pptr;
+    const int32_t* pcol;
+    const T* pval;
+    const T* pdinv;
+};
+
+// ---- per-subdomain geometry ----------------------------------------------------------
+struct SubDev {
+    const int32_t* qoff;    // p+1
+    const int32_t* nint;    // p  : interior rows of s
+    const int32_t* if_ptr;  // p+1: interface numbering offsets
+    const int32_t* q_orig;  // n  : original index of Q row q
+    int32_t p, n, n1, n2;
+    int32_t smem_len;       // working-vector capacity in shared memory (elements)
+};
+
+// ---- inner (Schur-level) GMRES state, one per apply ----------------------------------
+struct InnerCtl {
+    double beta;                              // ||c||, c = S~^{-1} g'
+    double H[(kMaxInner + 1) * kMaxInner];    // column-major Hessenberg
+    int32_t steps;                            // -1 while running, else the steps taken
+    int32_t zero;                             // c == 0
+};
+
+template <class T>
+struct InnerDev {
+    const int32_t* coff_rp;  // n2+1
+    const int32_t* coff_ci;  // interface numbering
+    const T* coff_v;
+    T* V;          // (k+1) x n2, normalised Arnoldi vectors
+    T* W0;         // unnormalised vector, two buffers (alternating)
+    T* W1;
+    double* part;  // partial sums: 3 banks x (k+1) x p
+    InnerCtl* ctl;
+    int32_t k;
+};
+
+// ---- outer FGMRES control block -------------------------------------------------------
+struct FgCtl {
+    double rtol, bnorm, target, beta, est;
+    int32_t steps;      // steps in the current cycle
+    int32_t cycle_done; // 1 once the current cycle ended (converged estimate / breakdown / maxit)
+    int32_t total;      // Arnoldi steps over all cycles
+    int32_t maxit;
+    int32_t converged;  // true residual met the target
+    int32_t breakdown;
+    int32_t m;
+    uint32_t counter;   // last-CTA-done counter
+    double res_true;
+};
+
+struct FgDev {
+    double* V;      // (m+1) x n
+    double* Z;      // m x n
+    double* w;      // n
+    double* H;      // (m+1) x m column-major
+    double* cs;
+    double* sn;
+    double* g;      // m+1
+    double* h2;     // m+1: reorthogonalisation coefficients of the current step
+    double* hnext;  // 1: norm of the next basis vector
+    double* part;   // G x (m+1) partial sums
+    FgCtl* ctl;
+    int32_t m, G;
+};
+
+struct CsrDev {
+    const int32_t* rp;
+    const int32_t* ci;
+    const double* v;
+    int32_t n;
+};
+
+// ---- profiling classes ----------------------------------------------------------------
+enum ProfClass { PC_APPLY_FWD = 0, PC_INNER, PC_APPLY_BWD, PC_BJ, PC_SPMV_DOT, PC_CGS, PC_NORM,
+                 PC_UPDATE, PC_RESID, PC_COUNT };
+extern const char* kProfNames[PC_COUNT];
+
+struct Handle;
+
+// ---- launchers (kernels_*.cu) --------------------------------------------------------
+// trsv / apply programs
+template <class T>
+cudaError_t configure_apply(size_t dyn_bytes);
+template <class T>
+cudaError_t launch_bj(const Handle& h, const double* r, double* z, const int32_t* done,
+                      cudaStream_t st);
+template <class T>
+cudaError_t launch_schur_fwd(const Handle& h, const double* r, const int32_t* done,
+                             cudaStream_t st);
+template <class T>
+cudaError_t launch_inner(const Handle& h, const int32_t* done, cudaStream_t st);
+template <class T>
+cudaError_t launch_schur_bwd(const Handle& h, const double* r, double* z, const int32_t* done,
+                             cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_io(const Handle& h, const double* gp, double* y, cudaStream_t st);
+// numeric ILU and packing
+cudaError_t launch_ilu_numeric(const Handle& h, double* F, int milu, cudaStream_t st);
+template <class T>
+cudaError_t launch_pack(const ProgHost& ph, const int32_t* d_psrc, const int32_t* d_pdsrc,
+                        const double* vals, T* pval, T* pdinv, cudaStream_t st);
+// Krylov / SpMV
+cudaError_t launch_spmv(const Handle& h, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_fg_start(const Handle& h, const double* b, const double* x, cudaStream_t st);
+cudaError_t launch_fg_step(const Handle& h, int j, cudaStream_t st);
+cudaError_t launch_fg_end(const Handle& h, const double* b, double* x, cudaStream_t st);
+
+}  // namespace ilu2l

@@ -1,0 +1,387 @@
+// kernels_krylov.cu -- FP64 CSR SpMV and the flexible GMRES(m) kernels (Sec. 4.1.1: the
+// outer Krylov method is FGMRES because the inner Schur GMRES makes M^{-1} vary).
+//
+// Every kernel partitions the n rows into G contiguous CTA ranges. Reductions write one
+// partial per CTA; the last CTA to finish (atomic ticket after a fence) combines the
+// partials in a fixed order, so every result is independent of timing. The Arnoldi
+// state (Hessenberg, Givens rotations, residual estimate, the cycle flag) lives on the
+// device: the host reads it once per cycle.
+//
+// One Arnoldi step j (after z_j = M^{-1} v_j):
+//   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w
+//   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w
+//   k_fg_norm      w -= V h2, ||w||, Givens rotation, residual estimate, stop decision
+//   k_fg_next      v_{j+1} = w / ||w||
+#include "devutil.cuh"
+#include "handle.h"
+
+namespace ilu2l {
+
+__device__ __forceinline__ void cta_rows(int n, int& r0, int& r1) {
+    const int R = (n + gridDim.x - 1) / gridDim.x;
+    r0 = blockIdx.x * R;
+    r1 = min(n, r0 + R);
+}
+
+// y_r = A_r . x with VL lanes per row; result valid in the row's first lane. Every lane
+// of the warp must call it (the shuffles use the full mask); lanes of an out-of-range row
+// pass valid = false.
+template <int VL>
+__device__ __forceinline__ double row_dot(const CsrDev& A, int r, bool valid, const double* __restrict__ x,
+                                          int sl) {
+    double s = 0.0;
+    if (valid) {
+        const int e = A.rp[r + 1];
+        for (int q = A.rp[r] + sl; q < e; q += VL) s += A.v[q] * x[A.ci[q]];
+    }
+#pragma unroll
+    for (int o = VL / 2; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o, VL);
+    return s;
+}
+
+// Last CTA ticket: returns true in every thread of the last CTA to arrive.
+__device__ __forceinline__ bool last_cta(uint32_t* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// In the last CTA: out[i] = sum_c part[i*G + c] for i < m, fixed order.
+__device__ __forceinline__ void reduce_partials(const double* part, int G, int m, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < m; i += nw) {
+        double s = 0.0;
+        for (int c = lane; c < G; c += 32) s += __ldcg(part + (size_t)i * G + c);
+        s = warp_sum(s);
+        if (lane == 0) out[i] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+template <int VL>
+__global__ void k_spmv(CsrDev A, const double* __restrict__ x, double* __restrict__ y) {
+    const int per_block = blockDim.x / VL;  // rows per block per pass (uniform trip count)
+    const int sub = threadIdx.x / VL, sl = threadIdx.x & (VL - 1);
+    for (int base = blockIdx.x * per_block; base < A.n; base += gridDim.x * per_block) {
+        const int r = base + sub;
+        const bool valid = r < A.n;
+        const double s = row_dot<VL>(A, r, valid, x, sl);
+        if (valid && sl == 0) y[r] = s;
+    }
+}
+
+// r = b - A x into V[0]; ||r||^2 (and ||b||^2 on the first call); cycle set-up
+template <int VL>
+__global__ void k_fg_resid(CsrDev A, FgDev f, const double* __restrict__ b, const double* __restrict__ x,
+                           int first) {
+    __shared__ double red[64];
+    __shared__ double tot[2];
+    int r0, r1;
+    cta_rows(A.n, r0, r1);
+    const int sl = threadIdx.x & (VL - 1), sub = threadIdx.x / VL, nsub = blockDim.x / VL;
+    double rr = 0.0, bb = 0.0;
+    for (int base = r0; base < r1; base += nsub) {
+        const int r = base + sub;
+        const bool valid = r < r1;
+        const double ax = row_dot<VL>(A, r, valid, x, sl);
+        if (valid && sl == 0) {
+            const double rv = b[r] - ax;
+            f.V[r] = rv;
+            rr += rv * rv;
+            bb += b[r] * b[r];
+        }
+    }
+    double v2[2] = {rr, bb};
+    block_sum_n<2>(v2, red);
+    if (threadIdx.x == 0) {
+        f.part[blockIdx.x] = v2[0];
+        f.part[(size_t)f.G + blockIdx.x] = v2[1];
+    }
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, 2, tot);
+    if (threadIdx.x == 0) {
+        FgCtl* c = f.ctl;
+        c->counter = 0;
+        if (first) {
+            c->bnorm = sqrt(tot[1]);
+            c->target = c->rtol * c->bnorm;
+            c->total = 0;
+            c->converged = 0;
+            c->breakdown = 0;
+        }
+        const double beta = sqrt(tot[0]);
+        c->beta = beta;
+        c->res_true = beta;
+        c->steps = 0;
+        c->est = beta;
+        if (c->bnorm == 0.0 || beta <= c->target) {
+            c->converged = 1;
+            c->cycle_done = 1;
+        } else if (c->total >= c->maxit) {
+            c->cycle_done = 1;
+        } else {
+            c->cycle_done = 0;
+            for (int i = 0; i <= f.m; i++) f.g[i] = 0.0;
+            f.g[0] = beta;
+        }
+    }
+}
+
+__global__ void k_fg_scale0(FgDev f, int n) {
+    if (f.ctl->cycle_done) return;
+    const double inv = 1.0 / f.ctl->beta;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        f.V[r] = f.V[r] * inv;
+}
+
+// w = A z_j; partial dots V_i . w, i <= j; last CTA stores h1 in column j of H
+template <int VL>
+__global__ void k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
+    __shared__ double red[32 * 8];
+    if (f.ctl->cycle_done) return;
+    int r0, r1;
+    cta_rows(A.n, r0, r1);
+    const int n = A.n;
+    const double* __restrict__ zj = f.Z + (size_t)j * n;
+    const int sl = threadIdx.x & (VL - 1), sub = threadIdx.x / VL, nsub = blockDim.x / VL;
+    for (int base = r0; base < r1; base += nsub) {
+        const int r = base + sub;
+        const bool valid = r < r1;
+        const double s = row_dot<VL>(A, r, valid, zj, sl);
+        if (valid && sl == 0) f.w[r] = s;
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const double w = f.w[r];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (i0 + u <= j) acc[u] += f.V[(size_t)(i0 + u) * n + r] * w;
+        }
+        block_sum_n<8>(acc, red);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < 8 && i0 + u <= j; u++) f.part[(size_t)(i0 + u) * f.G + blockIdx.x] = acc[u];
+    }
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, j + 1, f.H + (size_t)j * (f.m + 1));
+    if (threadIdx.x == 0) f.ctl->counter = 0;
+}
+
+// w -= V h (h = column j of H); second pass dots; last CTA adds them to column j and
+// keeps them in f.h2 for k_fg_norm
+__global__ void k_fg_cgs(FgDev f, int n, int j) {
+    __shared__ double red[32 * 8];
+    __shared__ double hh[kMaxRestart + 1];
+    if (f.ctl->cycle_done) return;
+    int r0, r1;
+    cta_rows(n, r0, r1);
+    const double* Hj = f.H + (size_t)j * (f.m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hh[i] = __ldcg(Hj + i);
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double w = f.w[r];
+        for (int i = 0; i <= j; i++) w -= hh[i] * f.V[(size_t)i * n + r];
+        f.w[r] = w;
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const double w = f.w[r];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (i0 + u <= j) acc[u] += f.V[(size_t)(i0 + u) * n + r] * w;
+        }
+        block_sum_n<8>(acc, red);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < 8 && i0 + u <= j; u++) f.part[(size_t)(i0 + u) * f.G + blockIdx.x] = acc[u];
+    }
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, j + 1, f.h2);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= j; i++) f.H[(size_t)j * (f.m + 1) + i] += f.h2[i];
+        f.ctl->counter = 0;
+    }
+}
+
+// w -= V h2; ||w||; Givens; estimate; stop decision
+__global__ void k_fg_norm(FgDev f, int n, int j) {
+    __shared__ double red[32];
+    __shared__ double hh[kMaxRestart + 1];
+    __shared__ double tot[1];
+    if (f.ctl->cycle_done) return;
+    int r0, r1;
+    cta_rows(n, r0, r1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hh[i] = __ldcg(f.h2 + i);
+    __syncthreads();
+    double acc = 0.0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double w = f.w[r];
+        for (int i = 0; i <= j; i++) w -= hh[i] * f.V[(size_t)i * n + r];
+        f.w[r] = w;
+        acc += w * w;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, 1, tot);
+    if (threadIdx.x == 0) {
+        FgCtl* c = f.ctl;
+        c->counter = 0;
+        const double hn = sqrt(tot[0]);
+        const int m1 = f.m + 1;
+        double* col = f.H + (size_t)j * m1;
+        col[j + 1] = hn;
+        for (int i = 0; i < j; i++) {
+            const double a = f.cs[i] * col[i] + f.sn[i] * col[i + 1];
+            col[i + 1] = -f.sn[i] * col[i] + f.cs[i] * col[i + 1];
+            col[i] = a;
+        }
+        const double d = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+        double cj, sj;
+        if (d == 0.0) {
+            cj = 1.0;
+            sj = 0.0;
+        } else {
+            cj = col[j] / d;
+            sj = col[j + 1] / d;
+        }
+        f.cs[j] = cj;
+        f.sn[j] = sj;
+        col[j] = cj * col[j] + sj * col[j + 1];
+        col[j + 1] = 0.0;
+        f.g[j + 1] = -sj * f.g[j];
+        f.g[j] = cj * f.g[j];
+        c->total += 1;
+        c->steps = j + 1;
+        c->est = fabs(f.g[j + 1]);
+        *f.hnext = hn;  // norm of the new basis vector, for k_fg_next
+        if (c->est <= c->target || hn == 0.0 || c->total >= c->maxit || j + 1 == f.m) {
+            c->cycle_done = 1;
+            if (hn == 0.0) c->breakdown = 1;
+        }
+    }
+}
+
+__global__ void k_fg_next(FgDev f, int n, int j) {
+    if (f.ctl->cycle_done) return;
+    const double inv = 1.0 / __ldcg(f.hnext);
+    double* vn = f.V + (size_t)(j + 1) * n;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        vn[r] = f.w[r] * inv;
+}
+
+// y = R^{-1} g (every CTA, redundantly); x += Z y on the CTA's rows
+__global__ void k_fg_update(FgDev f, int n, double* __restrict__ x) {
+    __shared__ double y[kMaxRestart];
+    __shared__ int steps_s;
+    if (threadIdx.x == 0) {
+        const int steps = f.ctl->steps;
+        for (int i = steps - 1; i >= 0; i--) {
+            double s = f.g[i];
+            for (int l = i + 1; l < steps; l++) s -= f.H[(size_t)l * (f.m + 1) + i] * y[l];
+            y[i] = s / f.H[(size_t)i * (f.m + 1) + i];
+        }
+        steps_s = steps;
+    }
+    __syncthreads();
+    const int steps = steps_s;
+    if (steps == 0) return;
+    int r0, r1;
+    cta_rows(n, r0, r1);
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double xv = x[r];
+        for (int i = 0; i < steps; i++) xv += y[i] * f.Z[(size_t)i * n + r];
+        x[r] = xv;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+static int pick_vl(const Handle& h) {
+    const double avg = h.n ? (double)h.nnz / h.n : 1.0;
+    if (avg <= 3) return 2;
+    if (avg <= 10) return 4;
+    if (avg <= 20) return 8;
+    if (avg <= 40) return 16;
+    return 32;
+}
+
+static CsrDev csr_of(const Handle& h) {
+    CsrDev A;
+    A.rp = h.d_A_rp;
+    A.ci = h.d_A_ci;
+    A.v = h.d_A_v;
+    A.n = h.n;
+    return A;
+}
+
+#define ILU2L_VL_SWITCH(vl, CALL) \
+    switch (vl) {                 \
+        case 2: {                 \
+            constexpr int V = 2;  \
+            CALL;                 \
+        } break;                  \
+        case 4: {                 \
+            constexpr int V = 4;  \
+            CALL;                 \
+        } break;                  \
+        case 8: {                 \
+            constexpr int V = 8;  \
+            CALL;                 \
+        } break;                  \
+        case 16: {                \
+            constexpr int V = 16; \
+            CALL;                 \
+        } break;                  \
+        default: {                \
+            constexpr int V = 32; \
+            CALL;                 \
+        } break;                  \
+    }
+
+cudaError_t launch_spmv(const Handle& h, const double* x, double* y, cudaStream_t st) {
+    if (h.n == 0) return cudaSuccess;
+    const int vl = pick_vl(h);
+    const int blocks = h.sm_count * 8;
+    ILU2L_VL_SWITCH(vl, (k_spmv<V><<<blocks, 256, 0, st>>>(csr_of(h), x, y)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_start(const Handle& h, const double* b, const double* x, cudaStream_t st) {
+    const int vl = pick_vl(h);
+    ILU2L_VL_SWITCH(vl, (k_fg_resid<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, b, x, 1)));
+    k_fg_scale0<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_step(const Handle& h, int j, cudaStream_t st) {
+    const int vl = pick_vl(h);
+    ILU2L_VL_SWITCH(vl, (k_fg_spmv_dot<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, j)));
+    k_fg_cgs<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
+    k_fg_norm<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
+    k_fg_next<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_end(const Handle& h, const double* b, double* x, cudaStream_t st) {
+    const int vl = pick_vl(h);
+    k_fg_update<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, x);
+    ILU2L_VL_SWITCH(vl, (k_fg_resid<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, b, x, 0)));
+    k_fg_scale0<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n);
+    return cudaGetLastError();
+}
+
+}  // namespace ilu2l

@@ -1,0 +1,597 @@
+// setup_host.cpp -- host half of ilu_setup: validation, interior/interface classification,
+// interior-first permutation, local blocks in Q order, C_off, factor patterns, the host
+// ILUT factor, level sets and the level programs the device kernels execute.
+//
+// Paper passages: Sec. 2.2.1 (classification, relabelling, Eq. equ22), Sec. 3.1 (level
+// scheduling analysis, L\U stored in the pattern), Sec. 3.2 (local blocks Eq. localA,
+// factor extraction L_B, U_B, L_S, U_S, W, Z, the off-diagonal blocks of S, Eq. SS).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "handle.h"
+
+namespace ilu2l {
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// validation
+
+ilu_status validate(const ilu_csr* A, const int32_t* part, int32_t p) {
+    if (!A || !part || p < 1 || A->n < 0 || A->nnz < 0) return ILU_ERR_ARG;
+    if (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->val))) return ILU_ERR_ARG;
+    const int32_t n = A->n;
+    if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return ILU_ERR_CSR;
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t b = A->rowptr[i], e = A->rowptr[i + 1];
+        if (e < b) return ILU_ERR_CSR;
+        bool diag = false;
+        for (int32_t q = b; q < e; q++) {
+            const int32_t c = A->colind[q];
+            if (c < 0 || c >= n) return ILU_ERR_CSR;
+            if (q > b && c <= A->colind[q - 1]) return ILU_ERR_CSR;
+            diag |= (c == i);
+        }
+        if (!diag) return ILU_ERR_CSR;
+    }
+    for (int32_t i = 0; i < n; i++)
+        if (part[i] < 0 || part[i] >= p) return ILU_ERR_ARG;
+    return ILU_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// level computation on a window of a factor pattern (rows r0..r1-1 of one subdomain,
+// local numbering, q0 = the subdomain's first Q row).
+//   lower: lev(r) = 0 without entries c in [clo, r), else 1 + max lev(c);
+//   upper: from the bottom over entries c in (r, chi).
+// Returns the number of levels; lev is indexed by local row.
+
+int window_levels(const FPat& F, int32_t q0, int32_t r0, int32_t r1, int32_t clo, int32_t chi,
+                  bool upper, std::vector<int32_t>& lev) {
+    int nl = 0;
+    if (!upper) {
+        for (int32_t r = r0; r < r1; r++) {
+            int32_t l = 0;
+            for (int32_t k = F.rp[q0 + r]; k < F.rp[q0 + r + 1]; k++) {
+                const int32_t c = F.ci[k];
+                if (c >= clo && c < r) l = std::max(l, lev[c] + 1);
+            }
+            lev[r] = l;
+            nl = std::max(nl, l + 1);
+        }
+    } else {
+        for (int32_t r = r1 - 1; r >= r0; r--) {
+            int32_t l = 0;
+            for (int32_t k = F.rp[q0 + r]; k < F.rp[q0 + r + 1]; k++) {
+                const int32_t c = F.ci[k];
+                if (c > r && c < chi) l = std::max(l, lev[c] + 1);
+            }
+            lev[r] = l;
+            nl = std::max(nl, l + 1);
+        }
+    }
+    return nl;
+}
+
+void prog_init(ProgHost& P) {
+    P.sub_lvl.assign(1, 0);
+    P.lvl_ptr.assign(1, 0);
+    P.pptr.assign(1, 0);
+    P.prow.clear();
+    P.pcol.clear();
+    P.psrc.clear();
+    P.pdsrc.clear();
+    P.max_level_rows = 0;
+    P.max_levels = 0;
+}
+
+void prog_close_level(ProgHost& P) {
+    const int32_t rows = (int32_t)P.prow.size() - P.lvl_ptr.back();
+    P.max_level_rows = std::max(P.max_level_rows, rows);
+    P.lvl_ptr.push_back((int32_t)P.prow.size());
+}
+
+void prog_push_row(ProgHost& P, const FPat& F, int32_t q0, int32_t r, int32_t clo, int32_t chi,
+                   bool upper, int32_t base) {
+    P.prow.push_back(r - base);
+    for (int32_t k = F.rp[q0 + r]; k < F.rp[q0 + r + 1]; k++) {
+        const int32_t c = F.ci[k];
+        const bool take = upper ? (c > r && c < chi) : (c >= clo && c < chi && c != r);
+        if (take) {
+            P.pcol.push_back(c - base);
+            P.psrc.push_back((int32_t)(F.base + k));
+        }
+    }
+    P.pptr.push_back((int32_t)P.pcol.size());
+    P.pdsrc.push_back(upper ? (int32_t)(F.base + F.dpos[q0 + r]) : -1);
+}
+
+int32_t row_count(const FPat& F, int32_t q0, int32_t r, int32_t clo, int32_t chi, bool upper) {
+    int32_t cnt = 0;
+    for (int32_t k = F.rp[q0 + r]; k < F.rp[q0 + r + 1]; k++) {
+        const int32_t c = F.ci[k];
+        cnt += upper ? (c > r && c < chi) : (c >= clo && c < chi && c != r);
+    }
+    return cnt;
+}
+
+// Levels of a triangular window appended to program P (one subdomain). Unit-lower rows
+// with no entry leave x unchanged and are not scheduled; upper rows always are (pivot).
+int prog_add_tri(ProgHost& P, const FPat& F, int32_t q0, int32_t r0, int32_t r1, int32_t clo,
+                 int32_t chi, bool upper, int32_t base, std::vector<int32_t>& lev) {
+    if (r1 <= r0) return 0;
+    const int nl = window_levels(F, q0, r0, r1, clo, upper ? chi : r1, upper, lev);
+    // bucket rows by level, ascending row inside a level
+    std::vector<int32_t> cnt(nl + 1, 0);
+    for (int32_t r = r0; r < r1; r++) cnt[lev[r] + 1]++;
+    for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
+    std::vector<int32_t> order(r1 - r0);
+    std::vector<int32_t> fillp(cnt.begin(), cnt.end() - 1);
+    for (int32_t r = r0; r < r1; r++) order[fillp[lev[r]]++] = r;
+    int added = 0;
+    for (int l = 0; l < nl; l++) {
+        const size_t before = P.prow.size();
+        for (int32_t t = cnt[l]; t < cnt[l + 1]; t++) {
+            const int32_t r = order[t];
+            if (!upper && row_count(F, q0, r, clo, r, false) == 0) continue;
+            prog_push_row(P, F, q0, r, clo, upper ? chi : r, upper, base);
+        }
+        if (P.prow.size() > before) {
+            prog_close_level(P);
+            added++;
+        }
+    }
+    return added;
+}
+
+// One level holding a block product x[r] -= sum M(r, c) x[c], c in [clo, chi).
+int prog_add_single(ProgHost& P, const FPat& F, int32_t q0, int32_t r0, int32_t r1, int32_t clo,
+                    int32_t chi, int32_t base) {
+    const size_t before = P.prow.size();
+    for (int32_t r = r0; r < r1; r++) {
+        if (row_count(F, q0, r, clo, chi, false) == 0) continue;
+        prog_push_row(P, F, q0, r, clo, chi, false, base);
+    }
+    if (P.prow.size() > before) {
+        prog_close_level(P);
+        return 1;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------
+// host ILUT(tau, p) of a local square matrix given by rows of a Q-order CSR window.
+// Dual threshold (the paper uses ILUT without defining it, Sec. 4.2; standard reading):
+// t_i = tau ||a_i||_2; eliminate pivots k < i in ascending order with fill; drop l_ik
+// (and skip its update) when |l_ik| < t_i; afterwards drop |w_j| < t_i and keep the p
+// largest of the L part and of the U part (ties: larger |value|, then smaller column);
+// the diagonal is always kept; small pivots perturbed as in the ILU(0) kernel.
+
+struct IlutRow {
+    std::vector<int32_t> ci;
+    std::vector<double> v;
+};
+
+int ilut_local(const int32_t* rp, const int32_t* ci, const double* a, int32_t m, double tau,
+               int32_t pkeep, double eps, std::vector<IlutRow>& rows, int* npert) {
+    rows.assign(m, IlutRow{});
+    std::vector<double> w(m, 0.0);
+    std::vector<uint8_t> on(m, 0);
+    std::vector<int32_t> diagpos(m, 0);
+    std::vector<int32_t> lcand, ulist, lkeep;
+    std::vector<std::pair<double, int32_t>> sel;
+    for (int32_t i = 0; i < m; i++) {
+        double nrm2 = 0.0;
+        double amax = 0.0;
+        for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+            nrm2 += a[q] * a[q];
+            amax = std::max(amax, std::fabs(a[q]));
+        }
+        const double ti = tau * std::sqrt(nrm2);
+        lcand.clear();
+        ulist.clear();
+        lkeep.clear();
+        on[i] = 1;
+        w[i] = 0.0;
+        for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+            const int32_t c = ci[q];
+            w[c] = a[q];
+            if (c == i) continue;
+            on[c] = 1;
+            if (c < i) {
+                lcand.push_back(c);
+                std::push_heap(lcand.begin(), lcand.end(), std::greater<int32_t>());
+            } else {
+                ulist.push_back(c);
+            }
+        }
+        while (!lcand.empty()) {
+            std::pop_heap(lcand.begin(), lcand.end(), std::greater<int32_t>());
+            const int32_t k = lcand.back();
+            lcand.pop_back();
+            const IlutRow& rk = rows[k];
+            const double lik = w[k] / rk.v[diagpos[k]];
+            if (std::fabs(lik) < ti) {
+                w[k] = 0.0;
+                on[k] = 0;
+                continue;
+            }
+            w[k] = lik;
+            lkeep.push_back(k);
+            for (size_t t = (size_t)diagpos[k] + 1; t < rk.ci.size(); t++) {
+                const int32_t j = rk.ci[t];
+                if (!on[j]) {
+                    on[j] = 1;
+                    w[j] = 0.0;
+                    if (j < i) {
+                        lcand.push_back(j);
+                        std::push_heap(lcand.begin(), lcand.end(), std::greater<int32_t>());
+                    } else {
+                        ulist.push_back(j);
+                    }
+                }
+                w[j] -= lik * rk.v[t];
+            }
+        }
+        auto pick = [&](const std::vector<int32_t>& idx, std::vector<std::pair<int32_t, double>>& out) {
+            sel.clear();
+            for (int32_t j : idx)
+                if (std::fabs(w[j]) >= ti) sel.emplace_back(w[j], j);
+            auto better = [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
+                const double ax = std::fabs(x.first), ay = std::fabs(y.first);
+                if (ax != ay) return ax > ay;
+                return x.second < y.second;
+            };
+            if ((int32_t)sel.size() > pkeep) {
+                std::nth_element(sel.begin(), sel.begin() + pkeep, sel.end(), better);
+                sel.resize(pkeep);
+            }
+            out.clear();
+            for (auto& e : sel) out.emplace_back(e.second, e.first);
+            std::sort(out.begin(), out.end());
+        };
+        std::vector<std::pair<int32_t, double>> lsel, usel;
+        pick(lkeep, lsel);
+        pick(ulist, usel);
+        double uii = w[i];
+        const double thr = eps * amax;
+        if (eps > 0.0 && std::fabs(uii) < thr) {
+            uii = (uii >= 0.0) ? thr : -thr;
+            (*npert)++;
+        }
+        if (uii == 0.0) return ILU_ERR_ZERO_PIVOT;
+        IlutRow& ro = rows[i];
+        for (auto& e : lsel) {
+            ro.ci.push_back(e.first);
+            ro.v.push_back(e.second);
+        }
+        diagpos[i] = (int32_t)ro.ci.size();
+        ro.ci.push_back(i);
+        ro.v.push_back(uii);
+        for (auto& e : usel) {
+            ro.ci.push_back(e.first);
+            ro.v.push_back(e.second);
+        }
+        on[i] = 0;
+        w[i] = 0.0;
+        for (int32_t j : lkeep) {
+            on[j] = 0;
+            w[j] = 0.0;
+        }
+        for (int32_t j : ulist) {
+            on[j] = 0;
+            w[j] = 0.0;
+        }
+    }
+    return ILU_OK;
+}
+
+}  // namespace
+
+// ====================================================================================
+
+ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
+    ilu_status st = validate(A, part, p);
+    if (st != ILU_OK) return st;
+    const int32_t n = A->n;
+    h.n = n;
+    h.p = p;
+    h.nnz = A->nnz;
+    h.part.assign(part, part + n);
+
+    // ---- classification (Sec. 2.2.1): interface iff coupled to another subdomain in A
+    //      or A^T (symmetrised pattern keeps B, E, F block diagonal for any pattern).
+    h.iface.assign(n, 0);
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+            const int32_t j = A->colind[q];
+            if (part[j] != part[i]) {
+                h.iface[i] = 1;
+                h.iface[j] = 1;
+            }
+        }
+
+    // ---- interior-first relabelling (Eq. equ22)
+    h.int_ptr.assign(p + 1, 0);
+    h.if_ptr.assign(p + 1, 0);
+    for (int32_t i = 0; i < n; i++) (h.iface[i] ? h.if_ptr : h.int_ptr)[part[i] + 1]++;
+    for (int32_t s = 0; s < p; s++) {
+        h.int_ptr[s + 1] += h.int_ptr[s];
+        h.if_ptr[s + 1] += h.if_ptr[s];
+    }
+    h.n1 = h.int_ptr[p];
+    h.n2 = n - h.n1;
+    h.perm.assign(n, 0);
+    h.iperm.assign(n, 0);
+    {
+        std::vector<int32_t> ci(h.int_ptr.begin(), h.int_ptr.end() - 1);
+        std::vector<int32_t> cf(h.if_ptr.begin(), h.if_ptr.end() - 1);
+        for (int32_t i = 0; i < n; i++) {
+            const int32_t s = part[i];
+            const int32_t g = h.iface[i] ? h.n1 + cf[s]++ : ci[s]++;
+            h.perm[g] = i;
+            h.iperm[i] = g;
+        }
+    }
+
+    // ---- Q order: subdomain s owns [qoff[s], qoff[s+1]) = [interior_s ; interface_s]
+    h.qoff.assign(p + 1, 0);
+    h.nint.assign(p, 0);
+    h.max_ns = 0;
+    for (int32_t s = 0; s < p; s++) {
+        h.nint[s] = h.int_ptr[s + 1] - h.int_ptr[s];
+        const int32_t ns = h.nint[s] + (h.if_ptr[s + 1] - h.if_ptr[s]);
+        h.qoff[s + 1] = h.qoff[s] + ns;
+        h.max_ns = std::max(h.max_ns, ns);
+    }
+    h.q_orig.assign(n, 0);
+    std::vector<int32_t> loc(n);  // local index of every original node in its subdomain
+    for (int32_t s = 0; s < p; s++) {
+        const int32_t ni = h.nint[s];
+        for (int32_t l = 0; l < ni; l++) {
+            const int32_t i = h.perm[h.int_ptr[s] + l];
+            h.q_orig[h.qoff[s] + l] = i;
+            loc[i] = l;
+        }
+        for (int32_t l = 0; l < h.if_ptr[s + 1] - h.if_ptr[s]; l++) {
+            const int32_t i = h.perm[h.n1 + h.if_ptr[s] + l];
+            h.q_orig[h.qoff[s] + ni + l] = i;
+            loc[i] = ni + l;
+        }
+    }
+
+    // ---- local blocks A_s (Eq. localA) in Q order, and C_off (off-diagonal blocks of S,
+    //      which equal those of C, Sec. 2.2.2) in interface numbering
+    h.q_rp.assign(n + 1, 0);
+    h.coff_rp.assign(h.n2 + 1, 0);
+    for (int32_t q = 0; q < n; q++) {
+        const int32_t i = h.q_orig[q];
+        int32_t c_in = 0, c_out = 0;
+        for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+            (part[A->colind[k]] == part[i] ? c_in : c_out)++;
+        h.q_rp[q + 1] = h.q_rp[q] + c_in;
+        if (h.iface[i]) h.coff_rp[h.iperm[i] - h.n1 + 1] = c_out;
+    }
+    for (int32_t r = 0; r < h.n2; r++) h.coff_rp[r + 1] += h.coff_rp[r];
+    const int64_t nnzQ = h.q_rp[n];
+    h.q_ci.resize(nnzQ);
+    h.q_v.resize(nnzQ);
+    h.q_dpos.assign(n, -1);
+    h.coff_ci.resize(h.coff_rp[h.n2]);
+    h.coff_v.resize(h.coff_rp[h.n2]);
+    h.nnz_coff = h.coff_rp[h.n2];
+    {
+        std::vector<std::pair<int32_t, double>> row;
+        for (int32_t q = 0; q < n; q++) {
+            const int32_t i = h.q_orig[q];
+            row.clear();
+            for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+                const int32_t j = A->colind[k];
+                if (part[j] == part[i]) row.emplace_back(loc[j], A->val[k]);
+            }
+            std::sort(row.begin(), row.end(),
+                      [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                          return a.first < b.first;
+                      });
+            int32_t at = h.q_rp[q];
+            int32_t s = part[i];
+            int32_t lrow = q - h.qoff[s];
+            for (auto& e : row) {
+                if (e.first == lrow) h.q_dpos[q] = at;
+                h.q_ci[at] = e.first;
+                h.q_v[at++] = e.second;
+            }
+            if (h.iface[i]) {
+                row.clear();
+                for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+                    const int32_t j = A->colind[k];
+                    if (part[j] != part[i]) row.emplace_back(h.iperm[j] - h.n1, A->val[k]);
+                }
+                std::sort(row.begin(), row.end(),
+                          [](const std::pair<int32_t, double>& a,
+                             const std::pair<int32_t, double>& b) { return a.first < b.first; });
+                int32_t at2 = h.coff_rp[h.iperm[i] - h.n1];
+                for (auto& e : row) {
+                    h.coff_ci[at2] = e.first;
+                    h.coff_v[at2++] = e.second;
+                }
+            }
+        }
+    }
+
+    // ---- factor patterns and value regions [F1 | F2 | A_local]
+    FPat apat;
+    apat.rp = h.q_rp;
+    apat.ci = h.q_ci;
+    apat.dpos = h.q_dpos;
+    const bool schur = (h.variant == ILU_VARIANT_SCHUR);
+    const bool f1_ilut = (h.kB == ILU_FACT_ILUT);
+    h.f1_device = !f1_ilut;
+    if (!f1_ilut) {
+        h.f1 = apat;
+        h.f1.base = 0;
+    } else {
+        // ILUT of B_s (two-level) or of A_s (block Jacobi), on the host, per subdomain
+        std::vector<std::vector<IlutRow>> res(p);
+        std::vector<int> stat(p, ILU_OK), pert(p, 0);
+        const double tau = h.o.ilut_tau;
+        const int32_t pk = h.o.ilut_p;
+        const double eps = h.o.pivot_eps;
+        auto work = [&](int32_t s0, int32_t s1) {
+            std::vector<int32_t> brp, bci;
+            std::vector<double> bv;
+            for (int32_t s = s0; s < s1; s++) {
+                const int32_t q0 = h.qoff[s];
+                const int32_t m = schur ? h.nint[s] : (h.qoff[s + 1] - q0);
+                brp.assign(m + 1, 0);
+                bci.clear();
+                bv.clear();
+                for (int32_t r = 0; r < m; r++) {
+                    for (int32_t k = h.q_rp[q0 + r]; k < h.q_rp[q0 + r + 1]; k++)
+                        if (h.q_ci[k] < m) {
+                            bci.push_back(h.q_ci[k]);
+                            bv.push_back(h.q_v[k]);
+                        }
+                    brp[r + 1] = (int32_t)bci.size();
+                }
+                stat[s] = ilut_local(brp.data(), bci.data(), bv.data(), m, tau, pk, eps, res[s],
+                                     &pert[s]);
+            }
+        };
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        nt = std::min<unsigned>(nt, (unsigned)p);
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; t++)
+            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
+        for (auto& t : th) t.join();
+        for (int32_t s = 0; s < p; s++) {
+            if (stat[s] != ILU_OK) return (ilu_status)stat[s];
+            h.npert += pert[s];
+        }
+        h.f1.rp.assign(n + 1, 0);
+        h.f1.dpos.assign(n, -1);
+        h.f1.ci.clear();
+        h.f1_host_vals.clear();
+        for (int32_t s = 0; s < p; s++) {
+            const int32_t q0 = h.qoff[s];
+            const int32_t ns = h.qoff[s + 1] - q0;
+            for (int32_t r = 0; r < ns; r++) {
+                const int32_t q = q0 + r;
+                if (r < (int32_t)res[s].size()) {
+                    const IlutRow& ro = res[s][r];
+                    for (size_t t = 0; t < ro.ci.size(); t++) {
+                        if (ro.ci[t] == r) h.f1.dpos[q] = (int32_t)h.f1.ci.size();
+                        h.f1.ci.push_back(ro.ci[t]);
+                        h.f1_host_vals.push_back(ro.v[t]);
+                    }
+                }
+                h.f1.rp[q + 1] = (int32_t)h.f1.ci.size();
+            }
+        }
+        h.f1.base = 0;
+    }
+    const int64_t nnz1 = (int64_t)h.f1.ci.size();
+    h.f2_alias = !(schur && (f1_ilut || h.kS != h.kB));
+    if (h.f2_alias) {
+        h.f2 = h.f1;
+        h.a_base = nnz1;
+    } else {
+        h.f2 = apat;
+        h.f2.base = nnz1;
+        h.a_base = nnz1 + nnzQ;
+    }
+    apat.base = h.a_base;
+    h.nvals = h.a_base + nnzQ;
+    if (h.nvals >= (int64_t)INT32_MAX) return ILU_ERR_TOO_LARGE;
+
+    // ---- level sets (introspection) and level programs
+    for (int w = 0; w < 6; w++) {
+        h.lev[w].assign(n, -1);
+        h.nlev[w] = 0;
+    }
+    for (int pr = 0; pr < PR_COUNT; pr++) prog_init(h.prog[pr]);
+    prog_init(h.numprog);
+    std::vector<int32_t> lev(h.max_ns + 1, 0);
+    const bool wz = (h.form == ILU_FORM_WZ);
+    for (int32_t s = 0; s < p; s++) {
+        const int32_t q0 = h.qoff[s];
+        const int32_t ni = h.nint[s];
+        const int32_t ns = h.qoff[s + 1] - q0;
+        auto glob = [&](int32_t l) { return l < ni ? h.int_ptr[s] + l : h.n1 + h.if_ptr[s] + (l - ni); };
+        // introspection levels
+        const FPat& pa = (!schur) ? h.f1 : apat;
+        for (int w = 0; w < 6; w++) {
+            const FPat& F = (w < 2) ? pa : (w < 4 ? h.f1 : h.f2);
+            int32_t r0 = 0, r1 = ns, clo = 0, chi = ns;
+            if (w == 2 || w == 3) {
+                r1 = ni;
+                chi = ni;
+            } else if (w == 4 || w == 5) {
+                r0 = ni;
+                clo = ni;
+            }
+            const int nl = window_levels(F, q0, r0, r1, clo, chi, (w & 1) != 0, lev);
+            h.nlev[w] = std::max(h.nlev[w], (r1 > r0) ? nl : 0);
+            for (int32_t r = r0; r < r1; r++) h.lev[w][glob(r)] = lev[r];
+        }
+        // numeric factorisation schedule: L levels of the pattern of A_s (all local rows)
+        {
+            ProgHost& N = h.numprog;
+            const int nl = window_levels(apat, q0, 0, ns, 0, ns, false, lev);
+            std::vector<std::vector<int32_t>> byl(nl);
+            for (int32_t r = 0; r < ns; r++) byl[lev[r]].push_back(r);
+            for (int l = 0; l < nl; l++) {
+                for (int32_t r : byl[l]) N.prow.push_back(r);
+                prog_close_level(N);
+            }
+            N.sub_lvl.push_back((int32_t)N.lvl_ptr.size() - 1);
+            N.max_levels = std::max(N.max_levels, nl);
+        }
+        if (!schur) {
+            ProgHost& P = h.prog[PR_BJ];
+            int a = prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, false, 0, lev);
+            a += prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, true, 0, lev);
+            P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+            P.max_levels = std::max(P.max_levels, a);
+        } else {
+            {   // forward: f' = L_B^{-1} f then g' = g - W f'   (W/Z)
+                //          t = U_B^{-1} L_B^{-1} f then g' = g - E t   (E/F)
+                ProgHost& P = h.prog[PR_FWD];
+                int a = prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                if (wz) {
+                    a += prog_add_single(P, h.f1, q0, ni, ns, 0, ni, 0);
+                } else {
+                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                    a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                }
+                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                P.max_levels = std::max(P.max_levels, a);
+            }
+            {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni)
+                ProgHost& P = h.prog[PR_S];
+                int a = prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, ni, lev);
+                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, ni, lev);
+                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                P.max_levels = std::max(P.max_levels, a);
+            }
+            {   // backward: u = U_B^{-1}(f' - Z y)  (W/Z);  u = U_B^{-1} L_B^{-1}(f - F y) (E/F)
+                ProgHost& P = h.prog[PR_BWD];
+                int a = 0;
+                if (wz) {
+                    a += prog_add_single(P, h.f1, q0, 0, ni, ni, ns, 0);
+                } else {
+                    a += prog_add_single(P, apat, q0, 0, ni, ni, ns, 0);
+                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                }
+                a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                P.max_levels = std::max(P.max_levels, a);
+            }
+        }
+    }
+    return ILU_OK;
+}
+
+}  // namespace ilu2l

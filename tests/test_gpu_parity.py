@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded
+inputs.
+
+Bars (stated per check):
+  * integer setup products (classification, permutation, level sets): bit-exact;
+  * ILU(0) / MILU(0) factors computed on the device: bit-exact (the kernel keeps the
+    sequential operation order and rounds every operation separately);
+  * FP64 apply / SpMV / inner solve: normwise relative difference <= 1e-12 and every
+    element within 1e-12 * ||z||_inf (different summation order and fused multiply-adds
+    in the solves are the only differences);
+  * FP32 preconditioner: normwise relative difference <= TOL32 = 2e-4 (see
+    TOL32 below for the derivation);
+  * FGMRES: FP64 preconditioner iteration count within +-1 of the oracle, FP32 within
+    10 %; true relative residual <= rtol; solution within 1e-6 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_08881_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP32 preconditioner tolerance: each level of a triangular solve adds O(u32 * growth)
+# relative error (u32 = 6e-8); the deepest programs here have ~100 levels and the local
+# factors of the anisotropic problems amplify by <~ 30, i.e. ~100 * 6e-8 * 30 = 2e-4.
+TOL32 = 2e-4
+
+
+def _problems():
+    return {
+        "poisson64": lambda: P.make_config("1"),
+        "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
+        "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
+        "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
+        "rand": lambda: P.randsparse(3000, 8, mean_k=4.0, seed=4),
+        "p1": lambda: P.aniso2d_boxes(30, 1, seed=5),
+    }
+
+
+PROBS = _problems()
+CONFIGS = [
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0"),
+    dict(variant="bj", factor_B="milu0", factor_S="milu0"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0"),
+    dict(variant="schur", factor_B="ilu0", factor_S="ilu0"),
+    dict(variant="schur", factor_B="milu0", factor_S="milu0"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", form="ef"),
+    dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
+]
+
+
+def _cid(c):
+    return "-".join(str(v) for v in c.values())
+
+
+@pytest.fixture(scope="module")
+def ilu():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+_cache = {}
+
+
+def _prob(name):
+    if name not in _cache:
+        _cache[name] = PROBS[name]()
+    return _cache[name]
+
+
+def _pair(ilu, name, cfg, prec):
+    pr = _prob(name)
+    kw = dict(cfg)
+    opts = ilu.Opts(pc_precision=prec, **kw)
+    h = ilu.ilu_setup_problem(pr, opts)
+    okw = {k: v for k, v in kw.items()}
+    orc = O.Oracle.from_problem(pr, **okw)
+    return pr, h, orc
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _assert_close64(got, ref, what):
+    scale = max(np.abs(ref).max(), 1e-300)
+    rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    assert rel <= 1e-12, f"{what}: normwise {rel:.3e}"
+    assert np.abs(got - ref).max() <= 1e-12 * scale, f"{what}: max elt {np.abs(got - ref).max() / scale:.3e}"
+
+
+# ---------------------------------------------------------------------------------------
+# setup products
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("cfg", CONFIGS[:3] + CONFIGS[6:], ids=_cid)
+def test_setup_structure_bit_exact(ilu, name, cfg):
+    pr, h, orc = _pair(ilu, name, cfg, "fp64")
+    pm = orc.perm()
+    hp = h.perm()
+    for k in ("perm", "iperm", "int_ptr", "if_ptr", "iface"):
+        assert np.array_equal(hp[k], pm[k]), k
+    s = h.sizes()
+    os_ = orc.sizes()
+    assert (s["n1"], s["n2"], s["nnz_coff"]) == (os_.n1, os_.n2, os_.nnz_coff)
+    for w in range(6):
+        lg, nlg = h.levels(w)
+        lo, nlo = orc.levels(w)
+        assert np.array_equal(lg, lo) and nlg == nlo, f"levels {w}"
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("cfg", [CONFIGS[0], CONFIGS[2], CONFIGS[4]], ids=_cid)
+def test_device_factors_bit_exact(ilu, name, cfg):
+    pr, h, orc = _pair(ilu, name, cfg, "fp64")
+    facts = [1] if cfg["variant"] == "bj" or cfg["factor_B"] == cfg["factor_S"] else [1, 2]
+    for s in range(pr.p):
+        rp, _, _ = orc.local_csr(s)
+        nnz = int(rp[-1])
+        for f in facts:
+            got = h.local_factor(s, f, nnz)
+            ref = orc.local_factor(s, f)
+            assert np.array_equal(got, ref), f"subdomain {s} factor {f}: max diff {np.abs(got - ref).max()}"
+    assert h.sizes()["npert"] == orc.sizes().npert
+    h.close()
+
+
+# ---------------------------------------------------------------------------------------
+# kernels
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_spmv_fp64(ilu, name):
+    pr, h, orc = _pair(ilu, name, CONFIGS[0], "fp64")
+    x = np.random.default_rng(7).standard_normal(pr.n)
+    y = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    h.spmv(_dev(x), y)
+    torch.cuda.synchronize()
+    _assert_close64(y.cpu().numpy(), O.spmv(pr.n, pr.rowptr, pr.colind, pr.val, x), "spmv")
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("cfg", CONFIGS, ids=_cid)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_matches_oracle(ilu, name, cfg, prec):
+    pr, h, orc = _pair(ilu, name, cfg, prec)
+    r = np.random.default_rng(11).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    got = z.cpu().numpy()
+    ref = orc.apply(r)
+    assert np.isfinite(got).all()
+    if prec == "fp64":
+        _assert_close64(got, ref, f"apply {name}")
+    else:
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= TOL32, f"fp32 apply {name}: {rel:.3e}"
+    # a second call on the same handle gives the same bits (no state leaks between calls)
+    z2 = torch.empty_like(z)
+    ilu.ilu_apply(h, _dev(r), z2)
+    torch.cuda.synchronize()
+    assert torch.equal(z, z2)
+    h.close()
+
+
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "rand", "cuts3d"])
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_inner_solve_fp64(ilu, name, k):
+    cfg = dict(variant="schur", factor_B="ilu0", factor_S="milu0", inner_iters=k)
+    pr, h, orc = _pair(ilu, name, cfg, "fp64")
+    n2 = orc.sizes().n2
+    g = np.random.default_rng(13).standard_normal(n2)
+    y = torch.empty(n2, dtype=torch.float64, device="cuda")
+    h.inner_solve(_dev(g), y)
+    torch.cuda.synchronize()
+    _assert_close64(y.cpu().numpy(), orc.inner_gmres(g), "inner")
+    h.close()
+
+
+def test_apply_of_zero_is_zero(ilu):
+    pr, h, orc = _pair(ilu, "aniso2d_ragged", CONFIGS[2], "fp32")
+    z = torch.full((pr.n,), 7.0, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, torch.zeros(pr.n, dtype=torch.float64, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert not z.any()
+    h.close()
+
+
+# ---------------------------------------------------------------------------------------
+# edge cases
+
+
+def _tiny_cases():
+    # n = 1; all-interface subdomains (empty interiors); a subdomain with no rows
+    one = (1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.5]),
+           np.array([0], np.int32), 1)
+    tri = P.tridiag(3, -1.0, 4.0, -1.0)
+    three = (3, tri[1], tri[2], tri[3], np.array([0, 1, 2], np.int32), 3)
+    pr = P.aniso2d_boxes(12, 2)
+    gap = (pr.n, pr.rowptr, pr.colind, pr.val, np.where(pr.part == 3, 4, pr.part).astype(np.int32), 5)
+    return {"n1": one, "all_interface": three, "empty_subdomain": gap}
+
+
+@pytest.mark.parametrize("case", list(_tiny_cases()))
+@pytest.mark.parametrize("cfg", [CONFIGS[0], CONFIGS[2], CONFIGS[6]], ids=_cid)
+def test_edge_cases(ilu, case, cfg):
+    n, rp, ci, v, part, p = _tiny_cases()[case]
+    h = ilu.ilu_setup(n, rp, ci, v, part, p, ilu.Opts(pc_precision="fp64", **cfg))
+    orc = O.Oracle(n, rp, ci, v, part, p, **cfg)
+    r = np.random.default_rng(3).standard_normal(n)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    _assert_close64(z.cpu().numpy(), orc.apply(r), case)
+    b = _dev(r)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = ilu.gmres_solve(h, b, x, rtol=1e-10, restart=5, maxit=200)
+    assert info["status"] == 0 and info["rel_res_true"] <= 1e-10
+    h.close()
+
+
+def test_bad_vectors_are_rejected(ilu):
+    pr, h, _ = _pair(ilu, "poisson64", CONFIGS[0], "fp64")
+    r = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(ilu.IluError) as e:
+        ilu.ilu_apply(h, r, r)
+    assert e.value.status == ilu.ILU_ERR_ARG
+    h.close()
+
+
+# ---------------------------------------------------------------------------------------
+# FGMRES
+
+
+@pytest.mark.parametrize("name,cfg,prec,restart", [
+    ("poisson64", CONFIGS[0], "fp64", 30),
+    ("poisson64", CONFIGS[2], "fp64", 30),
+    ("aniso2d_ragged", CONFIGS[2], "fp64", 50),
+    ("aniso2d_ragged", CONFIGS[2], "fp32", 50),
+    ("conv3d", CONFIGS[2], "fp32", 50),
+    ("cuts3d", CONFIGS[6], "fp32", 50),
+    ("rand", CONFIGS[2], "fp32", 20),
+    ("conv3d", CONFIGS[5], "fp64", 10),
+])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):
+    pr = _prob(name)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, use_graphs=graphs, **cfg))
+    orc = O.Oracle.from_problem(pr, **cfg)
+    ref = orc.fgmres(pr.b, rtol=1e-8, restart=restart, maxit=5000)
+    b = _dev(pr.b)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=restart, maxit=5000)
+    torch.cuda.synchronize()
+    assert info["status"] == 0
+    xs = x.cpu().numpy()
+    res = np.linalg.norm(pr.b - pr.scipy() @ xs) / np.linalg.norm(pr.b)
+    assert res <= 1e-8 * 1.0001 and abs(res - info["rel_res_true"]) <= 1e-10
+    if prec == "fp64":
+        assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    else:
+        assert abs(info["iters"] - ref["iters"]) <= max(1, 0.1 * ref["iters"]), (info["iters"], ref["iters"])
+    assert np.linalg.norm(xs - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    # solving again from the solution converges immediately; b = 0 gives x = 0
+    info2 = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=restart, maxit=5000)
+    assert info2["iters"] == 0
+    x.fill_(3.0)
+    info3 = ilu.gmres_solve(h, torch.zeros_like(b), x, rtol=1e-8, restart=restart)
+    assert info3["status"] == 0 and not x.any()
+    h.close()
+
+
+def test_fgmres_maxit_reports_not_converged(ilu):
+    pr = _prob("aniso2d_ragged")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp64", **CONFIGS[2]))
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ilu.gmres_solve(h, _dev(pr.b), x, rtol=1e-12, restart=5, maxit=7)
+    assert info["status"] == ilu.ILU_ERR_NOT_CONVERGED and info["iters"] == 7
+    orc = O.Oracle.from_problem(pr, **CONFIGS[2])
+    ref = orc.fgmres(pr.b, rtol=1e-12, restart=5, maxit=7)
+    assert ref["iters"] == 7
+    np.testing.assert_allclose(info["rel_res_true"], ref["relres"], rtol=1e-8)
+    h.close()

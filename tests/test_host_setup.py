@@ -1,0 +1,72 @@
+"""The library's host-side setup (analysis-only handles, no GPU): interior/interface
+classification, interior-first permutation, level sets of every factor pattern (ILUT's
+included) match the oracle bit for bit."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_08881_gb300 import problems as P
+
+CASES = {
+    "poisson64": lambda: P.make_config("1"),
+    "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
+    "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
+    "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
+    "rand": lambda: P.randsparse(3000, 8, mean_k=4.0, seed=4),
+    "p1": lambda: P.aniso2d_boxes(30, 1, seed=5),
+}
+CFGS = [
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0"),
+    dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
+    dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-2, ilut_p=3),
+    dict(variant="bj", factor_B="ilut", factor_S="ilu0", ilut_tau=1e-3, ilut_p=5),
+]
+
+
+@pytest.fixture(scope="module")
+def ilu():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: "-".join(map(str, c.values())))
+def test_host_analysis_matches_oracle(ilu, name, cfg):
+    pr = CASES[name]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **cfg))
+    orc = O.Oracle.from_problem(pr, **cfg)
+    pm, hp = orc.perm(), h.perm()
+    for k in ("perm", "iperm", "int_ptr", "if_ptr", "iface"):
+        assert np.array_equal(hp[k], pm[k]), k
+    s, so = h.sizes(), orc.sizes()
+    assert (s["n1"], s["n2"], s["nnz_coff"], s["nnz"]) == (so.n1, so.n2, so.nnz_coff, so.nnz)
+    assert s["npert"] == (so.npert if cfg["factor_B"] == "ilut" else 0)
+    for w in range(6):
+        lg, nlg = h.levels(w)
+        lo, nlo = orc.levels(w)
+        assert np.array_equal(lg, lo) and nlg == nlo, f"levels {w}"
+    h.close()
+
+
+def test_full_size_2d_workload_structure(ilu):
+    """1024^2 9-point anisotropic problem on 8x8 boxes: the counts of the interior /
+    interface split and the level depth of L_B (natural order: level x + 2y; the corner
+    boxes have a 127 x 127 interior, so 126 + 2*126 + 1 levels)."""
+    pr = P.make_config("2")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
+    s = h.sizes()
+    assert (s["n"], s["nnz"], s["n1"], s["n2"], s["nnz_coff"]) == (
+        1048576, 9424900, 1020100, 28476, 85764)
+    assert s["nlev_LB"] == 3 * 126 + 1
+    h.close()
+
+
+def test_analysis_handle_refuses_device_calls(ilu):
+    pr = P.make_config("1")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
+    import ctypes as C
+    assert ilu.lib().ilu_apply(h.ptr, C.c_void_p(16), C.c_void_p(32)) == ilu.ILU_ERR_ARG
+    h.close()
