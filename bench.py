@@ -1,0 +1,416 @@
+"""Benchmark: FGMRES(50) time-to-rtol 1e-8 with the two-level ILU preconditioner on one
+GB300 (or N replicas), plus the preconditioner-apply bandwidth, mixed vs FP64, the
+roofline of the dominant kernel, an end-to-end number through the C ABI with host
+buffers, and the FP64 CPU oracle as the baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl ilu2l|reference]
+
+A step is one complete solve: FGMRES from x0 = 0 to ||b - Ax|| <= 1e-8 ||b|| on the
+workload's synthetic right-hand side with the factors resident (the setup is timed
+separately and inside the end-to-end number). value = solves per second over all
+ranks (each rank solves its own replica; no data-path collective exists).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2303_08881_gb300 import problems as P  # noqa: E402
+
+METRIC = "GMRES time-to-rtol 1e-8, PC-apply HBM GB/s, mixed vs FP64, p50/p99 latency"
+UNIT = "solves/s"
+RTOL = 1e-8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic bytes (each array read or written once per pass; gathers counted once)
+
+
+def prog_bytes(prog, sv):
+    return prog["entries"] * (4 + sv) + prog["rows"] * (8 + sv) + prog["levels"] * 4
+
+
+def class_bytes(sz, prec, iters, m, k):
+    """Algorithmic bytes summed over the working launches of every kernel class of one
+    solve with `iters` Arnoldi steps in cycles of m, inner GMRES of k steps."""
+    n, nnz, n1, n2, ncoff = sz["n"], sz["nnz"], sz["n1"], sz["n2"], sz["nnz_coff"]
+    sv = 4 if prec == "fp32" else 8
+    full, rem = divmod(iters, m)
+    steps = [m] * full + ([rem] if rem else [])
+    js = [j for s in steps for j in range(s)]
+    cycles = len(steps)
+    b = {}
+    spmv = 12 * nnz + 4 * (n + 1)
+    b["fg_spmv_dot"] = sum(spmv + 16 * n + 8 * (j + 1) * n for j in js)
+    b["fg_cgs"] = sum(8 * (j + 1) * n + 16 * n for j in js)
+    b["fg_norm"] = sum(8 * (j + 1) * n + 16 * n for j in js)
+    b["fg_next"] = sum(16 * n for j in js if j + 1 < m)
+    b["fg_update"] = sum(8 * s * n + 16 * n for s in steps)
+    b["fg_resid"] = (cycles + 1) * (spmv + 24 * n)
+    b["fg_scale0"] = (cycles + 1) * 16 * n
+    if sz["prog_bj"]["rows"]:
+        b["apply_bj"] = iters * (prog_bytes(sz["prog_bj"], sv) + 20 * n)
+    else:
+        fwd = prog_bytes(sz["prog_fwd"], sv) + prog_bytes(sz["prog_s"], sv) + 12 * n + sv * n
+        inner = 0
+        for j in range(k):
+            inner += (ncoff * (4 + sv) + 4 * (n2 + 1) + prog_bytes(sz["prog_s"], sv)
+                      + 3 * sv * n2 + (j + 1) * sv * n2)                      # part A
+            inner += 2 * ((j + 1) * sv * n2 + 2 * sv * n2)                     # parts B, C
+        bwd = prog_bytes(sz["prog_bwd"], sv) + sv * n1 + k * sv * n2 + 12 * n
+        b["apply_fwd"] = iters * fwd
+        b["apply_inner"] = iters * inner
+        b["apply_bwd"] = iters * bwd
+        b["_apply_one"] = fwd + inner + bwd
+    return b
+
+
+# ---------------------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/ilu2l_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+
+
+def solver_opts(cfg, prec):
+    sol = dict(P.CONFIG_SOLVER[cfg])
+    restart = sol.pop("restart")
+    sol.pop("prec")
+    sol["pc_precision"] = prec
+    return sol, restart
+
+
+def cpu_baseline(cfg, sample_cycles=1):
+    """The FP64 oracle, single-threaded: setup + `sample_cycles` FGMRES cycles, scaled to
+    the oracle's own iteration count on this workload (tests/golden)."""
+    import oracle as O
+    sol, restart = solver_opts(cfg, "fp64")
+    sol.pop("pc_precision")
+    pr = P.make_config(cfg)
+    t0 = time.perf_counter()
+    o = O.Oracle.from_problem(pr, **sol)
+    t1 = time.perf_counter()
+    out = o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=restart * sample_cycles)
+    t2 = time.perf_counter()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_fgmres_iters.json")))
+    iters = gold[cfg]["iters"]
+    est = (t1 - t0) + (t2 - t1) * iters / max(out["iters"], 1)
+    return dict(value=1.0 / est, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"oracle setup + {out['iters']} FGMRES({restart}) steps of {pr.name} "
+                        f"({t2 - t1:.2f} s), scaled to the oracle's {iters} steps to rtol 1e-8"),
+                time_to_rtol_s=est, setup_s=t1 - t0, iters=iters)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):   # warm-up: the oracle's setup phase on the same workload
+        sol, _ = solver_opts(args.config, "fp64")
+        sol.pop("pc_precision")
+        oracle.Oracle.from_problem(P.make_config(args.config), **sol)
+    vals, times = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.config)
+        vals.append(cb["value"])
+        times.append(cb["time_to_rtol_s"])
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.config)},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+
+
+def workload_name(cfg):
+    pr_spec = dict(P.FULL_CONFIGS[cfg])
+    sol = P.CONFIG_SOLVER[cfg]
+    fn = pr_spec.pop("fn")
+    shape = "_".join(f"{k}{v}" for k, v in pr_spec.items())
+    return (f"{fn}_{shape}_{sol['variant']}_{sol['factor_B']}+{sol['factor_S']}_"
+            f"{sol['prec']}pc_fgmres{sol['restart']}_rtol1e-8")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="2")
+    ap.add_argument("--impl", default="ilu2l", choices=["ilu2l", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2303_08881_gb300 as ilu
+    from paper_2303_08881_gb300 import _build
+    _build.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cfg = args.config
+    sol, restart = solver_opts(cfg, P.CONFIG_SOLVER[cfg]["prec"])
+    prec = sol["pc_precision"]
+    pr = P.make_config(cfg, seed=0)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(**sol))
+    setup_s = time.perf_counter() - t0
+    b = torch.from_numpy(pr.b).to(dev)
+    x = torch.zeros_like(b)
+
+    def solve(hh):
+        x.zero_()
+        return ilu.gmres_solve(hh, b, x, rtol=RTOL, restart=restart, maxit=20000)
+
+    for _ in range(args.warmup):
+        info = solve(h)
+    torch.cuda.synchronize()
+    launches0 = h.stats()["kernel_launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()   # an external profiler started with capture off sees only this region
+        ev0.record(stream)
+        infos = [solve(h) for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    t_ms = max_over_ranks(t_ms)
+    launches = h.stats()["kernel_launches"] - launches0
+    info = infos[-1]
+    xs = x.cpu().numpy()
+    relres = float(np.linalg.norm(pr.b - pr.scipy() @ xs) / np.linalg.norm(pr.b))
+    err_true = float(np.linalg.norm(xs - pr.x_true) / np.linalg.norm(pr.x_true))
+    time_to_rtol = t_ms / 1000.0 / args.steps
+    value = world * args.steps / (t_ms / 1000.0)
+
+    # ---- preconditioner apply bandwidth (standalone applies, events on the same stream)
+    sz = h.sizes()
+    k_inner = sol.get("inner_iters", 3)
+    r = torch.randn(pr.n, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        ilu.ilu_apply(h, r, z)
+    reps = 20
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ea.record(stream)
+    for _ in range(reps):
+        ilu.ilu_apply(h, r, z)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = ea.elapsed_time(eb) / reps
+    cb_model = class_bytes(sz, prec, 1, restart, k_inner)
+    apply_bytes = cb_model.get("_apply_one") or cb_model.get("apply_bj")
+    hbm, peak_kind = _peaks()
+    pc_apply = {"ms": apply_ms, "bytes": apply_bytes, "gbs": apply_bytes / apply_ms / 1e6,
+                "frac": apply_bytes / apply_ms / 1e6 / hbm, "peak_gbs": hbm, "peak_kind": peak_kind,
+                "levels": {k: sz[f"prog_{k}"]["levels"] for k in ("bj", "fwd", "s", "bwd")}}
+
+    # ---- profiled solve: per kernel class device time (events on the launching stream)
+    h.profile(True)
+    pinfo = solve(h)
+    prof = h.profile_read()
+    h.profile(False)
+    cbytes = class_bytes(sz, prec, pinfo["iters"], restart, k_inner)
+    classes = {}
+    for name, (ms, nl) in prof.items():
+        if nl == 0:
+            continue
+        by = cbytes.get(name)
+        classes[name] = {"ms": ms, "launches": nl, "avg_us": 1000.0 * ms / nl,
+                         "gbs": (by / ms / 1e6) if by else None}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    total_prof = sum(c["ms"] for c in classes.values())
+    d = classes[dom]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": (d["gbs"] / hbm) if d["gbs"] else None, "traffic": None,
+                "share": d["ms"] / total_prof, "peak_kind": peak_kind,
+                "avg_launch_us": d["avg_us"], "launches": d["launches"]}
+
+    # ---- mixed vs FP64 (same workload, FP64 preconditioner)
+    mixed = None
+    if not args.no_fp64 and prec == "fp32":
+        sol64 = dict(sol)
+        sol64["pc_precision"] = "fp64"
+        h64 = ilu.ilu_setup_problem(pr, ilu.Opts(**sol64))
+        for _ in range(max(1, args.warmup - 1)):
+            i64 = solve(h64)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        n64 = max(1, min(args.steps, 3))
+        for _ in range(n64):
+            i64 = solve(h64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t64 = ev0.elapsed_time(ev1) / 1000.0 / n64
+        mixed = {"fp64_time_to_rtol_s": t64, "fp64_iters": i64["iters"], "fp32_time_to_rtol_s": time_to_rtol,
+                 "fp32_iters": info["iters"], "speedup": t64 / time_to_rtol,
+                 "fp64_rel_res_true": i64["rel_res_true"]}
+        h64.close()
+
+    # ---- end to end through the C ABI with host buffers (setup included)
+    e2e = None
+    if not args.no_e2e:
+        b_host = torch.from_numpy(pr.b).pin_memory()
+        x_host = torch.empty(pr.n, dtype=torch.float64).pin_memory()
+        ne2e = max(1, min(args.steps, 3))
+        o = ilu.Opts(**sol)
+        he = ilu.ilu_setup_problem(pr, o)   # warm (first-touch allocations, module load)
+        he.close()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne2e):
+            he = ilu.ilu_setup_problem(pr, o)
+            bd = b_host.to(dev, non_blocking=True)
+            xd = torch.zeros_like(bd)
+            ilu.gmres_solve(he, bd, xd, rtol=RTOL, restart=restart, maxit=20000)
+            x_host.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+            he.close()
+        te = max_over_ranks((time.perf_counter() - t0) / ne2e)
+        h2d = pr.rowptr.nbytes + pr.colind.nbytes + pr.val.nbytes + pr.part.nbytes + pr.b.nbytes
+        e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * pr.n),
+               "time_s": te, "includes": "ilu_setup from host CSR + H2D b + gmres_solve + D2H x + ilu_free"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(cfg)
+
+    h.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "n": pr.n, "nnz": pr.nnz, "p": pr.p,
+                       "restart": restart, "rtol": RTOL, "pc_precision": prec, "parallelism": f"replicas{world}",
+                       "l2": "working set larger than L2 (FGMRES basis alone 0.8 GB)"},
+            "time_to_rtol_s": time_to_rtol, "iters": info["iters"], "rel_res_true": relres,
+            "err_vs_x_true": err_true, "setup_s": setup_s,
+            "pc_apply": pc_apply, "roofline": roofline, "kernels": classes, "mixed_vs_fp64": mixed,
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

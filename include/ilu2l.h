@@ -134,8 +134,11 @@ const char* ilu_status_str(ilu_status s);
  * All host outputs are caller-allocated; all device pointers are caller-owned.
  * --------------------------------------------------------------------------------- */
 
-/* out[0..11] = n, p, n1, n2, nnz(A), nnz(C_off), perturbed pivots, max levels of
-   (L_B, U_B, L_S, U_S, L_A, U_A) over subdomains, max rows of a local block A_i. */
+/* out[0..11] = n, p, n1, n2, nnz(A), nnz(C_off), perturbed pivots, max levels over
+   subdomains of L_B, U_B, L_S, U_S, max rows of a local block A_i;
+   out[12..23] = (scheduled rows, factor entries, levels summed over subdomains) of the
+   four level programs the apply runs: block Jacobi L_A+U_A; forward (L_B and W, or L_B,
+   U_B and E); local Schur L_S+U_S; backward (Z and U_B, or F, L_B and U_B). */
 ilu_status ilu_get_sizes(void* h, int64_t* out);
 
 /* Permutation (host int32 outputs, each may be NULL): perm[new] = old, iperm[old] = new,
@@ -165,13 +168,19 @@ ilu_status ilu_spmv(void* h, const double* x, double* y);
    gp, y DEVICE double[n2] in interface numbering. Asynchronous. */
 ilu_status ilu_inner_solve(void* h, const double* gp, double* y);
 
-/* Accumulated device time per kernel class since the last reset, when profiling is
-   enabled with ilu_profile(h, 1): names[i] (static strings), ms[i], launches[i] for
-   i < *count (capacity in *count on entry). Profiling brackets each class's launches
-   with CUDA events on opts.stream and disables graph capture while on. */
+/* Device time per kernel class since ilu_profile(h, 1) (which resets the counters):
+   names[i] (static strings), ms[i], launches[i] for i < *count (capacity in *count on
+   entry; the number of classes on return). Profiling brackets each class's launches
+   with CUDA events on opts.stream and disables cycle-graph replay while on; reading
+   synchronises on the last event. ilu_profile(h, 0) turns it off. */
 ilu_status ilu_profile(void* h, int32_t enable);
 ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* launches,
                             int32_t* count);
+
+/* Launch accounting: out[0] = kernels enqueued by this handle so far (direct launches
+   plus the kernel nodes of every replayed cycle graph), out[1] = cycle-graph replays,
+   out[2] = kernel nodes per cycle graph, out[3] = CTAs of the row-partitioned kernels. */
+ilu_status ilu_get_stats(void* h, int64_t* out);
 
 #ifdef __cplusplus
 }

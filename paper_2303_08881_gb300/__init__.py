@@ -81,6 +81,7 @@ def lib():
             "ilu_inner_solve": (I, [P, P, P]),
             "ilu_profile": (I, [P, I]),
             "ilu_profile_read": (I, [P, P, P, P, P]),
+            "ilu_get_stats": (I, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -181,11 +182,15 @@ class Handle:
 
     # ---- introspection ----
     def sizes(self) -> dict:
-        out = np.zeros(12, np.int64)
+        out = np.zeros(24, np.int64)
         _check(lib().ilu_get_sizes(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_sizes")
         keys = ["n", "p", "n1", "n2", "nnz", "nnz_coff", "npert", "nlev_LB", "nlev_UB",
                 "nlev_LS", "nlev_US", "max_ns"]
-        return dict(zip(keys, [int(v) for v in out]))
+        d = dict(zip(keys, [int(v) for v in out[:12]]))
+        for i, name in enumerate(["bj", "fwd", "s", "bwd"]):
+            d[f"prog_{name}"] = dict(rows=int(out[12 + 3 * i]), entries=int(out[13 + 3 * i]),
+                                     levels=int(out[14 + 3 * i]))
+        return d
 
     def perm(self) -> dict:
         n, p = self.n, self.p
@@ -217,6 +222,12 @@ class Handle:
 
     def inner_solve(self, gp, y):
         _check(lib().ilu_inner_solve(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve")
+
+    def stats(self) -> dict:
+        out = np.zeros(4, np.int64)
+        _check(lib().ilu_get_stats(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_stats")
+        return dict(kernel_launches=int(out[0]), graph_launches=int(out[1]),
+                    kernels_per_cycle=int(out[2]), row_ctas=int(out[3]))
 
     def profile(self, enable: bool):
         _check(lib().ilu_profile(self.ptr, int(enable)), "ilu_profile")

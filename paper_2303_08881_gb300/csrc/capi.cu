@@ -10,8 +10,9 @@
 
 namespace ilu2l {
 
-const char* kProfNames[PC_COUNT] = {"apply_fwd", "apply_inner", "apply_bwd", "apply_bj", "spmv_dot",
-                                    "cgs", "norm_givens", "update", "residual"};
+const char* kProfNames[PC_COUNT] = {"apply_fwd",  "apply_inner", "apply_bwd", "apply_bj",
+                                    "fg_spmv_dot", "fg_cgs",      "fg_norm",   "fg_next",
+                                    "fg_update",  "fg_resid",    "fg_scale0"};
 
 namespace {
 
@@ -184,30 +185,95 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     return ILU_OK;
 }
 
+// Brackets a group of nkern kernels of one class with CUDA events on the launching
+// stream when profiling is on (graphs are off then); always counts the launches.
+struct Scope {
+    Handle& h;
+    int cls, nkern;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool capturing;
+    static cudaEvent_t take(Handle& h) {
+        if (h.ev_used == h.ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            h.ev_pool.push_back(e);
+        }
+        return h.ev_pool[h.ev_used++];
+    }
+    Scope(Handle& hh, int c, int nk, cudaStream_t s, bool cap) : h(hh), cls(c), nkern(nk), st(s), capturing(cap) {
+        if (!capturing) h.kernel_launches += nk;
+        if (h.prof && !capturing) {
+            a = take(h);
+            b = take(h);
+            if (a && b) cudaEventRecord(a, st);
+        }
+    }
+    ~Scope() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            h.prof_recs.push_back({cls, nkern, a, b});
+        }
+    }
+};
+
 template <class T>
-cudaError_t apply_t(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
-    if (h.variant == ILU_VARIANT_BJ) return launch_bj<T>(h, r, z, done, st);
-    cudaError_t e = launch_schur_fwd<T>(h, r, done, st);
-    if (e == cudaSuccess) e = launch_inner<T>(h, done, st);
-    if (e == cudaSuccess) e = launch_schur_bwd<T>(h, r, z, done, st);
+cudaError_t apply_t(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st, bool cap) {
+    if (h.variant == ILU_VARIANT_BJ) {
+        Scope sc(h, PC_BJ, 1, st, cap);
+        return launch_bj<T>(h, r, z, done, st);
+    }
+    cudaError_t e;
+    {
+        Scope sc(h, PC_APPLY_FWD, 1, st, cap);
+        e = launch_schur_fwd<T>(h, r, done, st);
+    }
+    if (e == cudaSuccess && h.n2 > 0) {
+        Scope sc(h, PC_INNER, 3 * h.inner_k, st, cap);
+        e = launch_inner<T>(h, done, st);
+    }
+    if (e == cudaSuccess) {
+        Scope sc(h, PC_APPLY_BWD, 1, st, cap);
+        e = launch_schur_bwd<T>(h, r, z, done, st);
+    }
     return e;
 }
 
-cudaError_t apply_any(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
-    return (h.prec == ILU_PREC_FP32) ? apply_t<float>(h, r, z, done, st) : apply_t<double>(h, r, z, done, st);
+cudaError_t apply_any(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st,
+                      bool cap = false) {
+    return (h.prec == ILU_PREC_FP32) ? apply_t<float>(h, r, z, done, st, cap)
+                                     : apply_t<double>(h, r, z, done, st, cap);
+}
+
+#define ILU2L_SCOPED(cls, nk, call)              \
+    do {                                        \
+        Scope sc_(h, cls, nk, st, cap);          \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) return e_;        \
+    } while (0)
+
+cudaError_t enqueue_start(Handle& h, const double* b, const double* x, cudaStream_t st, bool cap = false) {
+    ILU2L_SCOPED(PC_RESID, 1, launch_fg_resid(h, b, x, 1, st));
+    ILU2L_SCOPED(PC_SCALE, 1, launch_fg_scale0(h, st));
+    return cudaSuccess;
 }
 
 // one FGMRES cycle: m steps (each a no-op once the cycle is done), update, true residual
-cudaError_t enqueue_cycle(const Handle& h, const double* b, double* x, cudaStream_t st) {
+cudaError_t enqueue_cycle(Handle& h, const double* b, double* x, cudaStream_t st, bool cap) {
     const size_t n = (size_t)h.n;
     const int32_t* done = &h.fg.ctl->cycle_done;
     for (int j = 0; j < h.fg.m; j++) {
-        cudaError_t e = apply_any(h, h.fg.V + (size_t)j * n, h.fg.Z + (size_t)j * n, done, st);
+        cudaError_t e = apply_any(h, h.fg.V + (size_t)j * n, h.fg.Z + (size_t)j * n, done, st, cap);
         if (e != cudaSuccess) return e;
-        e = launch_fg_step(h, j, st);
-        if (e != cudaSuccess) return e;
+        ILU2L_SCOPED(PC_SPMV_DOT, 1, launch_fg_spmv_dot(h, j, st));
+        ILU2L_SCOPED(PC_CGS, 1, launch_fg_cgs(h, j, st));
+        ILU2L_SCOPED(PC_NORM, 1, launch_fg_norm(h, j, st));
+        ILU2L_SCOPED(PC_NEXT, 1, launch_fg_next(h, j, st));
     }
-    return launch_fg_end(h, b, x, st);
+    ILU2L_SCOPED(PC_UPDATE, 1, launch_fg_update(h, x, st));
+    ILU2L_SCOPED(PC_RESID, 1, launch_fg_resid(h, b, x, 0, st));
+    ILU2L_SCOPED(PC_SCALE, 1, launch_fg_scale0(h, st));
+    return cudaSuccess;
 }
 
 double now_ms() {
@@ -266,8 +332,7 @@ ilu_status ilu_free(void* hp) {
     if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
-    if (h->ev0) cudaEventDestroy(h->ev0);
-    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return ILU_OK;
 }
@@ -358,6 +423,7 @@ ilu_status ilu_spmv(void* hp, const double* x, double* y) {
     if (!hp || !x || !y || x == y) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
     if (h->o.analysis_only) return ILU_ERR_ARG;
+    h->kernel_launches += 1;
     return map_err(launch_spmv(*h, x, y, h->st));
 }
 
@@ -386,7 +452,7 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
     init.m = restart;
     *h->h_ctl = init;
     CK(cudaMemcpyAsync(h->fg.ctl, h->h_ctl, sizeof(FgCtl), cudaMemcpyHostToDevice, h->st));
-    CK(launch_fg_start(*h, b, x, h->st));
+    CK(enqueue_start(*h, b, x, h->st));
     const bool graphs = h->o.use_graphs && !h->prof;
     if (graphs && (h->cycle_exec == nullptr || h->cycle_b != b || h->cycle_x != x || h->cycle_m != restart)) {
         if (h->cycle_exec) {
@@ -398,10 +464,13 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = enqueue_cycle(*h, b, x, cs);
+            cudaError_t e2 = enqueue_cycle(*h, b, x, cs, true);
             e = cudaStreamEndCapture(cs, &g);
             if (e2 != cudaSuccess) e = e2;
         }
+        size_t nodes = 0;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nodes);
+        h->cycle_nodes = (int64_t)nodes;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&h->cycle_exec, g, 0);
         if (g) cudaGraphDestroy(g);
         cudaStreamDestroy(cs);
@@ -425,10 +494,13 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
             result = ILU_ERR_NOT_CONVERGED;
             break;
         }
-        if (graphs)
+        if (graphs) {
             CK(cudaGraphLaunch(h->cycle_exec, h->st));
-        else
-            CK(enqueue_cycle(*h, b, x, h->st));
+            h->graph_launches++;
+            h->kernel_launches += h->cycle_nodes;
+        } else {
+            CK(enqueue_cycle(*h, b, x, h->st, false));
+        }
         cycles++;
     }
     CK(cudaStreamSynchronize(h->st));
@@ -461,6 +533,12 @@ ilu_status ilu_get_sizes(void* hp, int64_t* out) {
     out[9] = h->nlev[4];
     out[10] = h->nlev[5];
     out[11] = h->max_ns;
+    for (int pr = 0; pr < PR_COUNT; pr++) {
+        const ProgHost& P = h->prog[pr];
+        out[12 + 3 * pr] = (int64_t)P.prow.size();
+        out[13 + 3 * pr] = (int64_t)P.pcol.size();
+        out[14 + 3 * pr] = P.lvl_ptr.empty() ? 0 : (int64_t)P.lvl_ptr.size() - 1;
+    }
     return ILU_OK;
 }
 
@@ -501,7 +579,10 @@ ilu_status ilu_get_local_factor(void* hp, int32_t s, int32_t fact, double* val) 
 ilu_status ilu_profile(void* hp, int32_t enable) {
     if (!hp) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
+    if (!h->o.analysis_only) CK(cudaStreamSynchronize(h->st));
     h->prof = enable != 0;
+    h->prof_recs.clear();
+    h->ev_used = 0;
     for (int i = 0; i < PC_COUNT; i++) {
         h->prof_ms[i] = 0.0;
         h->prof_n[i] = 0;
@@ -512,6 +593,17 @@ ilu_status ilu_profile(void* hp, int32_t enable) {
 ilu_status ilu_profile_read(void* hp, const char** names, double* ms, int64_t* launches, int32_t* count) {
     if (!hp || !count) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
+    if (!h->prof_recs.empty()) {
+        CK(cudaEventSynchronize(h->prof_recs.back().b));
+        for (const auto& r : h->prof_recs) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, r.a, r.b));
+            h->prof_ms[r.cls] += t;
+            h->prof_n[r.cls] += r.nkern;
+        }
+        h->prof_recs.clear();
+        h->ev_used = 0;
+    }
     const int m = std::min<int>(*count, PC_COUNT);
     for (int i = 0; i < m; i++) {
         if (names) names[i] = kProfNames[i];
@@ -519,6 +611,16 @@ ilu_status ilu_profile_read(void* hp, const char** names, double* ms, int64_t* l
         if (launches) launches[i] = h->prof_n[i];
     }
     *count = PC_COUNT;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_stats(void* hp, int64_t* out) {
+    if (!hp || !out) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    out[0] = h->kernel_launches;
+    out[1] = h->graph_launches;
+    out[2] = h->cycle_nodes;
+    out[3] = (int64_t)h->fg_G;
     return ILU_OK;
 }
 

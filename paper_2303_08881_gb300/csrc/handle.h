@@ -91,11 +91,22 @@ struct Handle {
     double* cycle_x = nullptr;
     FgCtl* h_ctl = nullptr;          // pinned host mirror of the control block
 
-    // profiling
+    // profiling: one event pair per bracketed launch group, summed at read time
+    struct ProfRec {
+        int cls;
+        int nkern;
+        cudaEvent_t a, b;
+    };
     bool prof = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
     double prof_ms[PC_COUNT] = {};
     int64_t prof_n[PC_COUNT] = {};
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch accounting: kernels enqueued directly or as graph nodes
+    int64_t kernel_launches = 0;
+    int64_t graph_launches = 0;
+    int64_t cycle_nodes = 0;
 
     template <class T>
     T* alloc(size_t count, cudaError_t* err) {

@@ -114,7 +114,7 @@ struct CsrDev {
 
 // ---- profiling classes ----------------------------------------------------------------
 enum ProfClass { PC_APPLY_FWD = 0, PC_INNER, PC_APPLY_BWD, PC_BJ, PC_SPMV_DOT, PC_CGS, PC_NORM,
-                 PC_UPDATE, PC_RESID, PC_COUNT };
+                 PC_NEXT, PC_UPDATE, PC_RESID, PC_SCALE, PC_COUNT };
 extern const char* kProfNames[PC_COUNT];
 
 struct Handle;
@@ -143,8 +143,12 @@ cudaError_t launch_pack(const ProgHost& ph, const int32_t* d_psrc, const int32_t
                         const double* vals, T* pval, T* pdinv, cudaStream_t st);
 // Krylov / SpMV
 cudaError_t launch_spmv(const Handle& h, const double* x, double* y, cudaStream_t st);
-cudaError_t launch_fg_start(const Handle& h, const double* b, const double* x, cudaStream_t st);
-cudaError_t launch_fg_step(const Handle& h, int j, cudaStream_t st);
-cudaError_t launch_fg_end(const Handle& h, const double* b, double* x, cudaStream_t st);
+cudaError_t launch_fg_resid(const Handle& h, const double* b, const double* x, int first, cudaStream_t st);
+cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st);
+cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st);
+cudaError_t launch_fg_cgs(const Handle& h, int j, cudaStream_t st);
+cudaError_t launch_fg_norm(const Handle& h, int j, cudaStream_t st);
+cudaError_t launch_fg_next(const Handle& h, int j, cudaStream_t st);
+cudaError_t launch_fg_update(const Handle& h, double* x, cudaStream_t st);
 
 }  // namespace ilu2l

@@ -360,27 +360,40 @@ cudaError_t launch_spmv(const Handle& h, const double* x, double* y, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_fg_start(const Handle& h, const double* b, const double* x, cudaStream_t st) {
+cudaError_t launch_fg_resid(const Handle& h, const double* b, const double* x, int first, cudaStream_t st) {
     const int vl = pick_vl(h);
-    ILU2L_VL_SWITCH(vl, (k_fg_resid<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, b, x, 1)));
+    ILU2L_VL_SWITCH(vl, (k_fg_resid<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, b, x, first)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st) {
     k_fg_scale0<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fg_step(const Handle& h, int j, cudaStream_t st) {
+cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
     const int vl = pick_vl(h);
     ILU2L_VL_SWITCH(vl, (k_fg_spmv_dot<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, j)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_cgs(const Handle& h, int j, cudaStream_t st) {
     k_fg_cgs<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_norm(const Handle& h, int j, cudaStream_t st) {
     k_fg_norm<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fg_next(const Handle& h, int j, cudaStream_t st) {
     k_fg_next<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n, j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fg_end(const Handle& h, const double* b, double* x, cudaStream_t st) {
-    const int vl = pick_vl(h);
+cudaError_t launch_fg_update(const Handle& h, double* x, cudaStream_t st) {
     k_fg_update<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, x);
-    ILU2L_VL_SWITCH(vl, (k_fg_resid<V><<<h.fg_G, h.fg_threads, 0, st>>>(csr_of(h), h.fg, b, x, 0)));
-    k_fg_scale0<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n);
     return cudaGetLastError();
 }
 

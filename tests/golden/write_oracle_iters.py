@@ -1,0 +1,40 @@
+"""Writes tests/golden/oracle_fgmres_iters.json: the FP64 oracle's FGMRES iteration count
+and time-to-solution on the named workloads (calls only oracle/ and the seeded
+generators). The CPU baseline scales a one-cycle oracle sample by this count.
+
+    python tests/golden/write_oracle_iters.py 2 [1 ...]
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_2303_08881_gb300 import problems as P  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fgmres_iters.json")
+
+
+def main(keys):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for k in keys:
+        sol = dict(P.CONFIG_SOLVER[k])
+        restart = sol.pop("restart")
+        sol.pop("prec")
+        pr = P.make_config(k)
+        t0 = time.perf_counter()
+        o = O.Oracle.from_problem(pr, **sol)
+        t1 = time.perf_counter()
+        out = o.fgmres(pr.b, rtol=1e-8, restart=restart, maxit=20000)
+        t2 = time.perf_counter()
+        data[k] = dict(workload=pr.name, iters=out["iters"], relres=out["relres"], restart=restart,
+                       setup_s=round(t1 - t0, 3), solve_s=round(t2 - t1, 3), status=out["status"])
+        print(k, data[k], flush=True)
+    json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["2"])
