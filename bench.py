@@ -215,6 +215,35 @@ def workload_name(cfg):
             f"{sol['prec']}pc_fgmres{sol['restart']}_rtol1e-8")
 
 
+def apply_only(args, ilu, h, pr, dev, stream, setup_s, prec, restart, sol):
+    """Setup, W warm-up applies, K timed applies (CUDA events); one JSON line."""
+    import torch
+    r = torch.randn(pr.n, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        ilu.ilu_apply(h, r, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ilu.ilu_apply(h, r, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    sz = h.sizes()
+    by = class_bytes(sz, prec, 1, restart, sol.get("inner_iters", 3))
+    byte = by.get("_apply_one") or by.get("apply_bj")
+    hbm, kind = _peaks()
+    st = h.stats()
+    print(json.dumps({"mode": "apply", "workload": workload_name(args.config), "pc_precision": prec,
+                      "apply_ms": ms, "bytes": byte, "gbs": byte / ms / 1e6, "frac": byte / ms / 1e6 / hbm,
+                      "setup_s": setup_s, "stream_path": st["stream_path"], "device_error": st["device_error"],
+                      "levels": {k: sz[f"prog_{k}"]["levels"] for k in ("bj", "fwd", "s", "bwd")}}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +254,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
+                    help="apply: only time the preconditioner apply (used for kernel profiling)")
+    ap.add_argument("--prec", default=None, choices=[None, "fp32", "fp64"])
+    ap.add_argument("--threads", type=int, default=0, help="consumer-group threads override (0 = auto)")
+    ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -256,16 +290,20 @@ def main():
         return float(t.item())
 
     cfg = args.config
-    sol, restart = solver_opts(cfg, P.CONFIG_SOLVER[cfg]["prec"])
+    sol, restart = solver_opts(cfg, args.prec or P.CONFIG_SOLVER[cfg]["prec"])
     prec = sol["pc_precision"]
     pr = P.make_config(cfg, seed=0)
     stream = torch.cuda.current_stream()
 
+    sol["block_threads"] = args.threads
+    sol["kernel_path"] = args.kernel_path
     t0 = time.perf_counter()
     h = ilu.ilu_setup_problem(pr, ilu.Opts(**sol))
     setup_s = time.perf_counter() - t0
     b = torch.from_numpy(pr.b).to(dev)
     x = torch.zeros_like(b)
+    if args.mode == "apply":
+        return apply_only(args, ilu, h, pr, dev, stream, setup_s, prec, restart, sol)
 
     def solve(hh):
         x.zero_()

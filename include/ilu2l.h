@@ -75,6 +75,9 @@ typedef struct {
     int32_t block_threads;/* threads per CTA of the per-subdomain kernels (0 = autotune) */
     int32_t analysis_only;/* 1: host analysis only (no device memory, no factorisation);
                              only ilu_get_sizes / _perm / _levels and ilu_free are valid */
+    int32_t kernel_path;  /* 0: level programs streamed into shared memory by TMA (falls
+                             back to 1 when a row does not fit a 64 KB chunk);
+                             1: generic level kernels reading the programs from global memory */
 } ilu_opts;
 
 typedef struct {
@@ -177,9 +180,14 @@ ilu_status ilu_profile(void* h, int32_t enable);
 ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* launches,
                             int32_t* count);
 
-/* Launch accounting: out[0] = kernels enqueued by this handle so far (direct launches
-   plus the kernel nodes of every replayed cycle graph), out[1] = cycle-graph replays,
-   out[2] = kernel nodes per cycle graph, out[3] = CTAs of the row-partitioned kernels. */
+/* Launch accounting and device status: out[0] = kernels enqueued by this handle so far
+   (direct launches plus the kernel nodes of every replayed cycle graph), out[1] =
+   cycle-graph replays, out[2] = kernel nodes per cycle graph, out[3] = CTAs of the
+   row-partitioned kernels, out[4] = device error word (bit 1: zero pivot, bit 2: a bounded
+   device wait timed out; synchronises the stream to read it), out[5] = 1 when the apply
+   runs the TMA-streamed level programs, out[6..13] = (entries per row record, consumer
+   threads) of the streamed programs block Jacobi, forward, local Schur, backward (0 if
+   unused). out must hold 14 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
 #ifdef __cplusplus

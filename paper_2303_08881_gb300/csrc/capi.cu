@@ -87,6 +87,37 @@ ilu_status device_setup_t(Handle& h) {
     if (!h.d_iV || !h.d_iW0 || !h.d_iW1) return map_err(e);
     cv.clear();
     cv.shrink_to_fit();
+    if (h.stream_path) {
+        const int64_t cap = ((int64_t)optin - 20 * 1024 - 128 - (int64_t)h.nst * h.chunk) / (int64_t)sizeof(T);
+        h.smem_len_stream = (int32_t)std::max<int64_t>(0, std::min<int64_t>((int64_t)h.max_ns + 1, cap));
+        CK(configure_stream<T>(h, 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * sizeof(T)));
+        h.d_tbuf = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
+        if (!h.d_tbuf) return map_err(e);
+        for (int id = 0; id < PR_COUNT; id++) {
+            StreamHost& S = h.sh[id];
+            if (S.ch0.empty()) continue;
+            StreamBufs& B = h.sb[id];
+            CK(upload(h, &B.blob, S.blob));
+            CK(upload(h, &B.ch0, S.ch0));
+            B.chunk = S.chunk;
+            B.nt = S.nt;
+            B.rw = S.rw;
+            int64_t *dvoff = nullptr, *ddoff = nullptr;
+            int32_t *dvsrc = nullptr, *ddsrc = nullptr;
+            CK(upload(h, &dvoff, S.voff));
+            CK(upload(h, &dvsrc, S.vsrc));
+            CK(upload(h, &ddoff, S.doff));
+            CK(upload(h, &ddsrc, S.dsrc));
+            CK(launch_pack_stream<T>(S, dvoff, dvsrc, ddoff, ddsrc, h.d_vals, B.blob, h.st));
+            CK(cudaStreamSynchronize(h.st));
+            for (void* q : {(void*)dvoff, (void*)dvsrc, (void*)ddoff, (void*)ddsrc}) h.release(q);
+            std::vector<uint8_t>().swap(S.blob);
+            std::vector<int64_t>().swap(S.voff);
+            std::vector<int64_t>().swap(S.doff);
+            std::vector<int32_t>().swap(S.vsrc);
+            std::vector<int32_t>().swap(S.dsrc);
+        }
+    }
     if (h.variant == ILU_VARIANT_BJ) {
         ilu_status s = upload_prog<T>(h, PR_BJ);
         if (s != ILU_OK) return s;
@@ -219,22 +250,23 @@ struct Scope {
 
 template <class T>
 cudaError_t apply_t(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st, bool cap) {
+    const bool fast = h.stream_path;
     if (h.variant == ILU_VARIANT_BJ) {
         Scope sc(h, PC_BJ, 1, st, cap);
-        return launch_bj<T>(h, r, z, done, st);
+        return fast ? launch_bj_s<T>(h, r, z, done, st) : launch_bj<T>(h, r, z, done, st);
     }
     cudaError_t e;
     {
         Scope sc(h, PC_APPLY_FWD, 1, st, cap);
-        e = launch_schur_fwd<T>(h, r, done, st);
+        e = fast ? launch_fwd_s<T>(h, r, done, st) : launch_schur_fwd<T>(h, r, done, st);
     }
     if (e == cudaSuccess && h.n2 > 0) {
-        Scope sc(h, PC_INNER, 3 * h.inner_k, st, cap);
-        e = launch_inner<T>(h, done, st);
+        Scope sc(h, PC_INNER, (fast ? 4 : 3) * h.inner_k, st, cap);
+        e = fast ? launch_inner_s<T>(h, done, st) : launch_inner<T>(h, done, st);
     }
     if (e == cudaSuccess) {
         Scope sc(h, PC_APPLY_BWD, 1, st, cap);
-        e = launch_schur_bwd<T>(h, r, z, done, st);
+        e = fast ? launch_bwd_s<T>(h, r, z, done, st) : launch_schur_bwd<T>(h, r, z, done, st);
     }
     return e;
 }
@@ -306,6 +338,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->use_graphs = 1;
     o->block_threads = 0;
     o->analysis_only = 0;
+    o->kernel_path = 0;
 }
 
 const char* ilu_status_str(ilu_status s) {
@@ -353,7 +386,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.factor_S < 0 || o.factor_S > 1 || (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32) ||
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
-        (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024))) {
+        (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
+        o.kernel_path < 0 || o.kernel_path > 1) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -371,6 +405,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
                   : ILU_FORM_WZ;
     h->st = (cudaStream_t)o.stream;
     h->threads = o.block_threads ? o.block_threads : 256;
+    h->stream_path = (o.kernel_path == 0);
     ilu_status s = host_setup(*h, A, part, p);
     if (s == ILU_OK && o.analysis_only) {
         h->setup_ms = now_ms() - t0;
@@ -483,8 +518,13 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
     ilu_status result = ILU_OK;
     for (;;) {
         CK(cudaMemcpyAsync(h->h_ctl, h->fg.ctl, sizeof(FgCtl), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(&h->h_ctl->err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         const FgCtl& c = *h->h_ctl;
+        if (c.err & 2) {
+            result = ILU_ERR_TIMEOUT;
+            break;
+        }
         if (c.converged) {
             if (c.bnorm == 0.0) CK(cudaMemsetAsync(x, 0, (size_t)h->n * sizeof(double), h->st));
             result = ILU_OK;
@@ -533,8 +573,9 @@ ilu_status ilu_get_sizes(void* hp, int64_t* out) {
     out[9] = h->nlev[4];
     out[10] = h->nlev[5];
     out[11] = h->max_ns;
-    for (int pr = 0; pr < PR_COUNT; pr++) {
-        const ProgHost& P = h->prog[pr];
+    const int reported[4] = {PR_BJ, PR_FWD, PR_S, PR_BWD};  // out[12..23], as documented
+    for (int pr = 0; pr < 4; pr++) {
+        const ProgHost& P = h->prog[reported[pr]];
         out[12 + 3 * pr] = (int64_t)P.prow.size();
         out[13 + 3 * pr] = (int64_t)P.pcol.size();
         out[14 + 3 * pr] = P.lvl_ptr.empty() ? 0 : (int64_t)P.lvl_ptr.size() - 1;
@@ -621,6 +662,19 @@ ilu_status ilu_get_stats(void* hp, int64_t* out) {
     out[1] = h->graph_launches;
     out[2] = h->cycle_nodes;
     out[3] = (int64_t)h->fg_G;
+    out[4] = 0;
+    if (!h->o.analysis_only && h->d_err) {
+        int32_t e = 0;
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaMemcpy(&e, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        out[4] = e;
+    }
+    out[5] = h->stream_path ? 1 : 0;
+    const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
+    for (int i = 0; i < 4; i++) {
+        out[6 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].rw;
+        out[7 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].nt;
+    }
     return ILU_OK;
 }
 

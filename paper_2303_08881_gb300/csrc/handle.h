@@ -11,7 +11,7 @@
 
 namespace ilu2l {
 
-enum ProgId { PR_BJ = 0, PR_FWD = 1, PR_S = 2, PR_BWD = 3, PR_COUNT = 4 };
+enum ProgId { PR_BJ = 0, PR_FWD = 1, PR_S = 2, PR_BWD = 3, PR_FWDS = 4, PR_COUNT = 5 };
 
 // A factor's sparsity pattern over all Q rows (rows outside the factor are empty).
 // Values live in the handle's value array at [base + k] for pattern entry k.
@@ -19,6 +19,32 @@ struct FPat {
     std::vector<int32_t> rp, ci, dpos;  // ci: local column; dpos: diagonal entry or -1
     int64_t base = 0;
 };
+
+// A level program laid out as TMA chunks (stream_layout.h) for one index width.
+struct StreamHost {
+    std::vector<uint8_t> blob;        // chunks of every subdomain, kChunk bytes each
+    std::vector<int32_t> ch0;         // p+1: subdomain s owns chunks [ch0[s], ch0[s+1])
+    std::vector<int64_t> voff, doff;  // byte offsets of value / pivot-inverse slots
+    std::vector<int32_t> vsrc, dsrc;  // their sources in the value array
+    uint32_t chunk = 8192;
+    int idx_bytes = 2, val_bytes = 4;
+    int rw = 4;                       // entries per row record (compile-time width on the device)
+    uint32_t rec_bytes = 32;
+    int nt = 32;                      // threads of the consumer group
+    int64_t levels = 0, rows = 0, entries = 0;
+};
+
+struct StreamBufs {
+    uint8_t* blob = nullptr;
+    int32_t* ch0 = nullptr;
+    uint32_t chunk = 8192;
+    int nt = 32;
+    int rw = 4;
+};
+
+// Builds the chunked stream of program P; false if a single row does not fit a chunk.
+bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, uint32_t chunk,
+                  StreamHost& S);
 
 struct ProgBufs {
     int32_t *sub_lvl = nullptr, *lvl_ptr = nullptr, *prow = nullptr, *pptr = nullptr,
@@ -65,6 +91,14 @@ struct Handle {
     int32_t *d_A_rp = nullptr, *d_A_ci = nullptr;
     double* d_A_v = nullptr;         // the original matrix (FP64 SpMV)
     ProgBufs pb[PR_COUNT];
+    StreamHost sh[PR_COUNT];          // chunked streams (fast path)
+    StreamBufs sb[PR_COUNT];
+    bool stream_path = true;          // TMA-streamed level programs (else generic kernels)
+    int idx_bytes = 2;                // local index width of the streams
+    int nst = 8;                      // ring stages
+    uint32_t chunk = 8192;            // bytes per chunk / ring stage
+    int32_t smem_len_stream = 0;      // working-vector capacity with the ring present
+    void* d_tbuf = nullptr;           // C_off product of the inner step (interface numbering)
     int32_t *d_num_sub = nullptr, *d_num_lvl = nullptr, *d_num_row = nullptr;
     int32_t *d_coff_rp = nullptr, *d_coff_ci = nullptr;
     void* d_coff_v = nullptr;        // PC type
@@ -120,6 +154,15 @@ struct Handle {
         }
         allocs.push_back(p);
         return (T*)p;
+    }
+
+    void release(void* q) {
+        for (size_t i = 0; i < allocs.size(); i++)
+            if (allocs[i] == q) {
+                cudaFree(q);
+                allocs.erase(allocs.begin() + (long)i);
+                return;
+            }
     }
 
     SubDev sub() const {

@@ -88,6 +88,7 @@ struct FgCtl {
     int32_t m;
     uint32_t counter;   // last-CTA-done counter
     double res_true;
+    int32_t err;        // host mirror of the device error word (filled by the host copy)
 };
 
 struct FgDev {
@@ -136,6 +137,28 @@ cudaError_t launch_schur_bwd(const Handle& h, const double* r, double* z, const 
                              cudaStream_t st);
 template <class T>
 cudaError_t launch_inner_io(const Handle& h, const double* gp, double* y, cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_bc(const Handle& h, int j, int second, const int32_t* done, cudaStream_t st);
+// TMA-streamed level programs (kernels_stream.cu)
+struct StreamHost;
+template <class T>
+cudaError_t configure_stream(const Handle& h, size_t bytes);
+template <class T>
+cudaError_t launch_pack_stream(const StreamHost& sh, const int64_t* voff, const int32_t* vsrc,
+                               const int64_t* doff, const int32_t* dsrc, const double* vals,
+                               uint8_t* blob, cudaStream_t st);
+template <class T>
+cudaError_t launch_bj_s(const Handle& h, const double* r, double* z, const int32_t* done,
+                        cudaStream_t st);
+template <class T>
+cudaError_t launch_fwd_s(const Handle& h, const double* r, const int32_t* done, cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_s(const Handle& h, const int32_t* done, cudaStream_t st);
+template <class T>
+cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int32_t* done,
+                         cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st);
 // numeric ILU and packing
 cudaError_t launch_ilu_numeric(const Handle& h, double* F, int milu, cudaStream_t st);
 template <class T>

@@ -17,6 +17,7 @@
 //                        scatter;                                             k_bwd
 #include "devutil.cuh"
 #include "handle.h"
+#include "inner_lsq.cuh"
 
 namespace ilu2l {
 
@@ -245,57 +246,6 @@ __global__ void k_inner_bc(SubDev sd, InnerDev<T> in, int j, int second, const i
     }
 }
 
-// Least squares of the inner GMRES (Givens rotations, back substitution), computed
-// redundantly by thread 0 of every CTA into t[] (shared); returns the step count.
-__device__ int inner_lsq(const InnerCtl* ctl, const double* part, int p, int k, double* t) {
-    __shared__ double Hs[(kMaxInner + 1) * kMaxInner];
-    __shared__ double g[kMaxInner + 1], cs[kMaxInner], sn[kMaxInner];
-    __shared__ int steps_s;
-    if (threadIdx.x == 0) {
-        int steps = ctl->steps;
-        const int zero = ctl->zero;
-        for (int i = 0; i < (kMaxInner + 1) * kMaxInner; i++) Hs[i] = ctl->H[i];
-        if (zero) {
-            steps = 0;
-        } else if (steps < 0) {  // ran all k steps: the last norm is still in the partials
-            double nrm2 = 0.0;
-            for (int s2 = 0; s2 < p; s2++) nrm2 += __ldcg(part + ((size_t)(2 * (kMaxInner + 1))) * p + s2);
-            Hs[(k - 1) * (kMaxInner + 1) + k] = sqrt(nrm2);
-            steps = k;
-        }
-        for (int i = 0; i <= kMaxInner; i++) g[i] = 0.0;
-        g[0] = zero ? 0.0 : ctl->beta;
-        for (int j = 0; j < steps; j++) {
-            double* col = Hs + j * (kMaxInner + 1);
-            for (int i = 0; i < j; i++) {
-                const double a = cs[i] * col[i] + sn[i] * col[i + 1];
-                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-                col[i] = a;
-            }
-            const double d = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
-            if (d == 0.0) {
-                cs[j] = 1.0;
-                sn[j] = 0.0;
-            } else {
-                cs[j] = col[j] / d;
-                sn[j] = col[j + 1] / d;
-            }
-            col[j] = cs[j] * col[j] + sn[j] * col[j + 1];
-            col[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-        }
-        for (int i = steps - 1; i >= 0; i--) {
-            double acc = g[i];
-            for (int l = i + 1; l < steps; l++) acc -= Hs[l * (kMaxInner + 1) + i] * t[l];
-            t[i] = acc / Hs[i * (kMaxInner + 1) + i];
-        }
-        steps_s = steps;
-    }
-    __syncthreads();
-    return steps_s;
-}
-
 // two-level backward part: y = V t; f'' = f' - Z y (or f - F y, L_B); u = U_B^{-1} f''
 template <class T>
 __global__ void k_bwd(SubDev sd, ProgDev<T> PB, InnerDev<T> in, const double* __restrict__ r,
@@ -342,6 +292,12 @@ __global__ void k_inner_finish(SubDev sd, InnerDev<T> in, double* __restrict__ y
 
 static size_t smem_bytes(const Handle& h, size_t elt) {
     return (size_t)h.smem_len * elt;
+}
+
+template <class T>
+cudaError_t launch_inner_bc(const Handle& h, int j, int second, const int32_t* done, cudaStream_t st) {
+    k_inner_bc<T><<<h.p, h.threads, 0, st>>>(h.sub(), h.innerdev<T>(), j, second, done);
+    return cudaGetLastError();
 }
 
 template <class T>
@@ -396,9 +352,15 @@ cudaError_t launch_schur_bwd(const Handle& h, const double* r, double* z, const 
 template <class T>
 cudaError_t launch_inner_io(const Handle& h, const double* gp, double* y, cudaStream_t st) {
     if (h.n2 == 0) return cudaSuccess;
-    k_inner_start<T><<<h.p, h.threads, smem_bytes(h, sizeof(T)), st>>>(h.sub(), h.progdev<T>(PR_S),
-                                                                       h.innerdev<T>(), gp, (T*)h.d_xg);
-    cudaError_t e = launch_inner<T>(h, nullptr, st);
+    cudaError_t e;
+    if (h.stream_path) {
+        e = launch_inner_start_s<T>(h, gp, st);
+        if (e == cudaSuccess) e = launch_inner_s<T>(h, nullptr, st);
+    } else {
+        k_inner_start<T><<<h.p, h.threads, smem_bytes(h, sizeof(T)), st>>>(h.sub(), h.progdev<T>(PR_S),
+                                                                           h.innerdev<T>(), gp, (T*)h.d_xg);
+        e = launch_inner<T>(h, nullptr, st);
+    }
     if (e != cudaSuccess) return e;
     k_inner_finish<T><<<h.p, h.threads, 0, st>>>(h.sub(), h.innerdev<T>(), y);
     return cudaGetLastError();
@@ -406,6 +368,7 @@ cudaError_t launch_inner_io(const Handle& h, const double* gp, double* y, cudaSt
 
 #define ILU2L_INST(T)                                                                              \
     template cudaError_t configure_apply<T>(size_t);                                              \
+    template cudaError_t launch_inner_bc<T>(const Handle&, int, int, const int32_t*, cudaStream_t);  \
     template cudaError_t launch_bj<T>(const Handle&, const double*, double*, const int32_t*,       \
                                       cudaStream_t);                                              \
     template cudaError_t launch_schur_fwd<T>(const Handle&, const double*, const int32_t*,          \

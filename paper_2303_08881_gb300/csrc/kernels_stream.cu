@@ -1,0 +1,642 @@
+// kernels_stream.cu -- the preconditioner apply with TMA-streamed level programs.
+//
+// The triangular solves are level-scheduled (Sec. 3.1): rows of one level are
+// independent, consecutive levels depend on each other, so the apply is bound by the
+// latency of one level times the number of levels, not by bytes. Here one CTA serves one
+// subdomain:
+//   * its level program (stream_layout.h) arrives in fixed-size chunks through a ring of
+//     shared-memory stages filled by TMA bulk copies (cp.async.bulk, completion on an
+//     mbarrier), issued ahead of use so the global-memory latency overlaps the solve;
+//   * a consumer group (one warp, or a few warps on a named barrier) runs the levels on
+//     the subdomain's working vector in shared memory; only a warp-level or group
+//     barrier separates levels;
+//   * the whole CTA performs the coalesced gather of the input and the scatter of the
+//     output around the program.
+// Every mbarrier wait is bounded: on time-out the kernel sets bit 2 of the device error
+// word, stops consuming, waits (bounded) for its own copies in flight, and returns.
+//
+// Kernels: k_bj_s (block Jacobi), k_fwd_s (f' = L_B^{-1} f, g' = g - W f', c = S~^{-1} g'),
+// k_coff (t = C_off v_j, grid-wide), k_inner_a_s (w = v_j + S~^{-1} t, first Gram-Schmidt
+// dots), k_bwd_s (y = V t, f'' = f' - Z y, u = U_B^{-1} f'', scatter).
+#include "devutil.cuh"
+#include "handle.h"
+#include "inner_lsq.cuh"
+#include "stream_layout.h"
+
+namespace ilu2l {
+
+template <class T>
+struct StreamDev {
+    const uint8_t* blob;
+    const int32_t* ch0;
+    uint32_t chunk;
+    int nt;
+};
+
+struct RingCfg {
+    int nst;              // stages
+    int32_t smem_len;     // working-vector capacity in shared memory (elements)
+    uint64_t spin;        // bound of every mbarrier wait
+    int32_t* err;         // device error word
+};
+
+constexpr int kErrTimeout = 2;
+// Bound of the wait for a CTA's own bulk copies before it exits after a time-out: copies
+// from valid global memory always complete, this only keeps the wait finite.
+constexpr uint64_t kDrainSpin = 1ull << 20;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(b))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t spin) {
+    for (uint64_t i = 0; i < spin; i++)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void group_sync(int nt) {
+    if (nt <= 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+}
+
+// Shared-memory layout of every stream kernel: [mbarriers 128 B][ring nst*chunk][x ...]
+struct Smem {
+    uint64_t* bars;
+    uint8_t* ring;
+    uint8_t* xs;
+};
+
+__device__ __forceinline__ Smem smem_parts(int nst, uint32_t chunk) {
+    extern __shared__ __align__(128) uint8_t sm_raw[];
+    Smem s;
+    s.bars = reinterpret_cast<uint64_t*>(sm_raw);
+    s.ring = sm_raw + 128;
+    s.xs = sm_raw + 128 + (size_t)nst * chunk;
+    return s;
+}
+
+// thread 0: initialise the stage barriers and start the first copies of subdomain s
+template <class T>
+__device__ __forceinline__ void ring_start(const StreamDev<T>& S, int s, const Smem& sm, int nst) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < nst; i++) mbar_init(&sm.bars[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
+    const uint8_t* base = S.blob + (size_t)c0 * S.chunk;
+    for (int c = 0; c < nch && c < nst; c++) {
+        mbar_expect_tx(&sm.bars[c], S.chunk);
+        tma_load_1d(sm.ring + (size_t)c * S.chunk, base + (size_t)c * S.chunk, S.chunk, &sm.bars[c]);
+    }
+}
+
+// Row record (stream_layout.h), read with 128-bit shared-memory loads.
+template <class T, int RW>
+struct __align__(16) RowRec {
+    uint32_t head;  // byte offset of x[row] | n << 24
+    T dinv;
+    uint32_t col[RW];  // byte offsets
+    T val[RW];
+};
+
+template <class T, int RW>
+union RecU {
+    RowRec<T, RW> r;
+    uint4 v[sizeof(RowRec<T, RW>) / 16];
+};
+
+template <class T, int RW>
+__device__ __forceinline__ void rec_load(RecU<T, RW>& u, const uint8_t* p, bool valid) {
+    constexpr int NV = sizeof(RowRec<T, RW>) / 16;
+    static_assert(sizeof(RowRec<T, RW>) == rec_layout(RW, sizeof(T)).bytes, "record layout");
+    if (valid) {
+        const uint4* s = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+        for (int i = 0; i < NV; i++) u.v[i] = s[i];
+    } else {
+        u.r.head = 0xFFFFFFFFu;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T ldx(const uint8_t* xb, uint32_t off) {
+    return *reinterpret_cast<const T*>(xb + off);
+}
+
+// x[row] = (x[row] - sum_q val[q] x[col[q]]) * dinv; the sum is formed pairwise
+template <class T, int RW>
+__device__ __forceinline__ void rec_run(const RecU<T, RW>& u, uint8_t* xb) {
+    const uint32_t head = u.r.head;
+    if (head == 0xFFFFFFFFu) return;
+    const uint32_t roff = head & 0xFFFFFFu, n = head >> 24;
+    T p[RW];
+#pragma unroll
+    for (int q = 0; q < RW; q++) p[q] = ((uint32_t)q < n) ? u.r.val[q] * ldx<T>(xb, u.r.col[q]) : (T)0;
+    const T xr = ldx<T>(xb, roff);
+#pragma unroll
+    for (int w = 1; w < RW; w *= 2)
+#pragma unroll
+        for (int q = 0; q + w < RW; q += 2 * w) p[q] += p[q + w];
+    *reinterpret_cast<T*>(xb + roff) = (xr - p[0]) * u.r.dinv;
+}
+
+// Consume the program of subdomain s on x (threads 0..nt-1 of the CTA). Wave by wave each
+// thread takes one row record; the next wave's table entry and record are loaded before
+// the current wave runs, so between two level barriers sit only the working-vector loads
+// and the multiply-add tree. Returns false on a time-out (uniform over the group).
+template <class T, int RW>
+__device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const RingCfg& cfg, T* x) {
+    constexpr uint32_t RB = sizeof(RowRec<T, RW>);
+    __shared__ int abort_flag;
+    const int nt = S.nt, tid = threadIdx.x, nst = cfg.nst;
+    const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
+    const uint8_t* base = S.blob + (size_t)c0 * S.chunk;
+    uint8_t* xb = reinterpret_cast<uint8_t*>(x);
+    if (nch == 0) return true;
+    if (tid == 0) abort_flag = 0;
+    group_sync(nt);
+    auto acquire = [&](int c) -> bool {
+        if (!mbar_wait(&sm.bars[c % nst], (uint32_t)(c / nst) & 1u, cfg.spin)) abort_flag = 1;
+        group_sync(nt);
+        return abort_flag == 0;
+    };
+    auto release = [&](int c) {
+        group_sync(nt);
+        if (tid == 0 && c + nst < nch) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&sm.bars[c % nst], S.chunk);
+            tma_load_1d(sm.ring + (size_t)(c % nst) * S.chunk, base + (size_t)(c + nst) * S.chunk, S.chunk,
+                        &sm.bars[c % nst]);
+        }
+    };
+    auto fetch = [&](RecU<T, RW>& u, const uint8_t* cb, uint32_t e) {
+        const uint32_t width = (e >> 16) & 0x1FFu;
+        rec_load(u, cb + (e & 0xFFFFu) * 16u + (uint32_t)tid * RB, (uint32_t)tid < width);
+    };
+    int failed_at = -1;
+    int c = 0;
+    const uint8_t* cb = sm.ring;
+    uint32_t nw = 0, w = 0;
+    // one step: prefetch the wave after `cur` into `nxt`, run `cur`; returns false at the end
+    auto step = [&](RecU<T, RW>& cur, uint32_t& ecur, RecU<T, RW>& nxt, uint32_t& enxt) -> bool {
+        const bool sync_after = (ecur & kWaveSync) != 0;
+        const int cur_chunk = c;
+        bool more = true;
+        if (w + 1 < nw) {
+            w++;
+        } else if (c + 1 < nch) {
+            c++;
+            if (!acquire(c)) {
+                failed_at = c;
+                return false;
+            }
+            cb = sm.ring + (size_t)(c % nst) * S.chunk;
+            nw = *reinterpret_cast<const uint32_t*>(cb);
+            w = 0;
+        } else {
+            more = false;
+        }
+        if (more) {
+            enxt = reinterpret_cast<const uint32_t*>(cb + kChunkHdr)[w];
+            fetch(nxt, cb, enxt);
+        }
+        rec_run(cur, xb);
+        if (sync_after) group_sync(nt);
+        if (c != cur_chunk || !more) release(cur_chunk);
+        return more;
+    };
+    RecU<T, RW> a, b;
+    uint32_t ea = 0, eb = 0;
+    if (!acquire(0)) {
+        failed_at = 0;
+    } else {
+        nw = *reinterpret_cast<const uint32_t*>(cb);
+        ea = reinterpret_cast<const uint32_t*>(cb + kChunkHdr)[0];
+        fetch(a, cb, ea);
+        while (step(a, ea, b, eb) && step(b, eb, a, ea)) {
+        }
+    }
+    if (failed_at >= 0) {  // timed out: record it and wait (bounded) for the copies still in flight
+        if (tid == 0) {
+            atomicOr(cfg.err, kErrTimeout);
+            for (int d = failed_at; d < nch && d < failed_at + nst; d++)
+                mbar_wait(&sm.bars[d % nst], (uint32_t)(d / nst) & 1u, kDrainSpin);
+        }
+        return false;
+    }
+    return true;
+}
+
+// Gather / scatter with four independent loads in flight per thread.
+template <class T>
+__device__ __forceinline__ void gather(T* x, const double* __restrict__ r, const int32_t* __restrict__ idx, int n) {
+    const int stride = blockDim.x;
+    int l = threadIdx.x;
+    for (; l + 3 * stride < n; l += 4 * stride) {
+        const int i0 = idx[l], i1 = idx[l + stride], i2 = idx[l + 2 * stride], i3 = idx[l + 3 * stride];
+        const double v0 = r[i0], v1 = r[i1], v2 = r[i2], v3 = r[i3];
+        x[l] = (T)v0;
+        x[l + stride] = (T)v1;
+        x[l + 2 * stride] = (T)v2;
+        x[l + 3 * stride] = (T)v3;
+    }
+    for (; l < n; l += stride) x[l] = (T)r[idx[l]];
+}
+
+template <class T>
+__device__ __forceinline__ void scatter(double* __restrict__ z, const T* x, const int32_t* __restrict__ idx, int n) {
+    const int stride = blockDim.x;
+    int l = threadIdx.x;
+    for (; l + 3 * stride < n; l += 4 * stride) {
+        const int i0 = idx[l], i1 = idx[l + stride], i2 = idx[l + 2 * stride], i3 = idx[l + 3 * stride];
+        z[i0] = (double)x[l];
+        z[i1] = (double)x[l + stride];
+        z[i2] = (double)x[l + 2 * stride];
+        z[i3] = (double)x[l + 3 * stride];
+    }
+    for (; l < n; l += stride) z[idx[l]] = (double)x[l];
+}
+
+// ---------------------------------------------------------------------------------------
+// Working vector: in shared memory (XS, every subdomain fits; the pointer comes straight
+// from the shared array so the compiler emits shared loads) or a global scratch slice.
+template <class T, bool XS>
+__device__ __forceinline__ T* xvec(const Smem& sm, T* xg, int q0) {
+    if constexpr (XS) {
+        extern __shared__ __align__(128) uint8_t sm_raw[];
+        return reinterpret_cast<T*>(sm_raw + (sm.xs - sm.ring) + 128);
+    } else {
+        return xg + q0;
+    }
+}
+
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_bj_s(SubDev sd, StreamDev<T> S, RingCfg cfg, const double* __restrict__ r,
+                                              double* __restrict__ z, T* xg, const int32_t* done) {
+    if (done && *done) return;
+    const int s = blockIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    T* x = xvec<T, XS>(sm, xg, q0);
+    gather(x, r, sd.q_orig + q0, ns);
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    scatter(z, x, sd.q_orig + q0, ns);
+}
+
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
+                                               const double* __restrict__ r, T* __restrict__ fq, T* xg,
+                                               const int32_t* done) {
+    __shared__ double red[32];
+    if (done && *done) return;
+    const int s = blockIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    T* x = xvec<T, XS>(sm, xg, q0);
+    gather(x, r, sd.q_orig + q0, ns);
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    for (int l = threadIdx.x; l < ni; l += blockDim.x) fq[q0 + l] = x[l];
+    const int g0 = sd.if_ptr[s];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const T c = x[ni + i];
+        in.W0[g0 + i] = c;
+        acc += (double)c * (double)c;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = acc;
+        if (s == 0) {
+            in.ctl->steps = -1;
+            in.ctl->zero = 0;
+        }
+    }
+}
+
+// t = C_off v_j with v_j = W_in / ||W_in|| (the norm formed from the per-subdomain
+// partials in a fixed order); grid-wide, rows of the interface.
+template <class T>
+__global__ void k_coff(SubDev sd, InnerDev<T> in, int j, T* __restrict__ t, const int32_t* done) {
+    if (done && *done) return;
+    const InnerCtl* ctl = in.ctl;
+    if (*((volatile const int32_t*)&ctl->steps) >= 0 || *((volatile const int32_t*)&ctl->zero)) return;
+    const int p = sd.p;
+    double nrm2 = 0.0;
+    for (int u = 0; u < p; u++) nrm2 += __ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p + u);
+    if (nrm2 == 0.0) return;
+    const T inv = (T)(1.0 / sqrt(nrm2));
+    const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sd.n2; i += gridDim.x * blockDim.x) {
+        T acc = (T)0;
+        for (int q = in.coff_rp[i]; q < in.coff_rp[i + 1]; q++) acc += in.coff_v[q] * Win[in.coff_ci[q]];
+        t[i] = acc * inv;
+    }
+}
+
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
+                                                   const T* __restrict__ t, T* xg, const int32_t* done) {
+    __shared__ double red[32 * 8];
+    if (done && *done) return;
+    InnerCtl* ctl = in.ctl;
+    if (*((volatile int32_t*)&ctl->steps) >= 0 || *((volatile int32_t*)&ctl->zero)) return;
+    const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    double nrm2 = 0.0;
+    for (int u = 0; u < p; u++) nrm2 += __ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p + u);
+    const double nrm = sqrt(nrm2);
+    if (j == 0) {
+        if (s == 0 && threadIdx.x == 0) ctl->beta = nrm;
+        if (nrm == 0.0) {
+            if (s == 0 && threadIdx.x == 0) ctl->zero = 1;
+            return;
+        }
+    } else {
+        const double beta = ctl->beta;
+        if (s == 0 && threadIdx.x == 0) ctl->H[(j - 1) * (kMaxInner + 1) + j] = nrm;
+        if (nrm <= 1e-14 * beta) {
+            if (s == 0 && threadIdx.x == 0) ctl->steps = j;
+            return;
+        }
+    }
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    const T inv = (T)(1.0 / nrm);
+    const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
+    T* __restrict__ Wout = (j & 1) ? in.W0 : in.W1;
+    const int g0 = sd.if_ptr[s];
+    T* x = xvec<T, XS>(sm, xg + ni, q0);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = t[g0 + i];
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    T* Vj = in.V + (size_t)j * n2;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const int gi = g0 + i;
+        const T v = Win[gi] * inv;
+        Vj[gi] = v;
+        const T w = v + x[i];
+        Wout[gi] = w;
+        x[i] = w;
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+            const double w = (double)x[i];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (i0 + u <= j) acc[u] += (double)in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+        }
+        block_sum_n<8>(acc, red);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < 8 && i0 + u <= j; u++) in.part[((size_t)(i0 + u)) * p + s] = acc[u];
+    }
+}
+
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
+                                               const double* __restrict__ r, const T* __restrict__ fq, int ef,
+                                               double* __restrict__ z, T* xg, const int32_t* done) {
+    __shared__ double tt[kMaxInner];
+    if (done && *done) return;
+    const int s = blockIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    const int steps = (sd.n2 > 0) ? inner_lsq(in.ctl, in.part, sd.p, in.k, tt) : 0;
+    T* x = xvec<T, XS>(sm, xg, q0);
+    if (ef) {
+        for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)r[sd.q_orig[q0 + l]];
+    } else {
+        for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = fq[q0 + l];
+    }
+    const int g0 = sd.if_ptr[s];
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        T y = (T)0;
+        for (int u = 0; u < steps; u++) y += (T)tt[u] * in.V[(size_t)u * sd.n2 + g0 + i];
+        x[ni + i] = y;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    scatter(z, x, sd.q_orig + q0, ns);
+}
+
+// standalone start of the inner solve: c = S~^{-1} gp
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
+                                                       const double* __restrict__ gp, T* xg) {
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    T* x = xvec<T, XS>(sm, xg + ni, q0);
+    const int g0 = sd.if_ptr[s];
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = (T)gp[g0 + i];
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const T c = x[i];
+        in.W0[g0 + i] = c;
+        acc += (double)c * (double)c;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = acc;
+        if (s == 0) {
+            in.ctl->steps = -1;
+            in.ctl->zero = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// value packing of a stream: blob[voff[e]] = (T) vals[vsrc[e]]; blob[doff[d]] = 1 / vals[dsrc[d]]
+template <class T>
+__global__ void k_pack_stream(int64_t nv, int64_t nd, const int64_t* __restrict__ voff, const int32_t* __restrict__ vsrc,
+                              const int64_t* __restrict__ doff, const int32_t* __restrict__ dsrc,
+                              const double* __restrict__ vals, uint8_t* blob) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = tid; e < nv; e += stride) *reinterpret_cast<T*>(blob + voff[e]) = (T)vals[vsrc[e]];
+    for (int64_t d = tid; d < nd; d += stride) {
+        const int32_t src = dsrc[d];
+        *reinterpret_cast<T*>(blob + doff[d]) = (src >= 0) ? (T)(1.0 / vals[src]) : (T)1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+
+template <class T>
+static StreamDev<T> sdev(const Handle& h, int id) {
+    StreamDev<T> d;
+    d.blob = h.sb[id].blob;
+    d.ch0 = h.sb[id].ch0;
+    d.chunk = h.sb[id].chunk;
+    d.nt = h.sb[id].nt;
+    return d;
+}
+
+static RingCfg rcfg(const Handle& h) {
+    RingCfg c;
+    c.nst = h.nst;
+    c.smem_len = h.smem_len_stream;
+    c.spin = h.o.spin_limit ? h.o.spin_limit : (1ull << 22);
+    c.err = h.d_err;
+    return c;
+}
+
+static size_t stream_smem(const Handle& h, size_t elt) {
+    return 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * elt;
+}
+
+template <class T, int RW, bool XS>
+static cudaError_t configure_stream_t(size_t bytes) {
+    const int b = (int)bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_bj_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_a_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_inner_start_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
+}
+
+template <class T>
+cudaError_t configure_stream(const Handle& h, size_t bytes) {
+    cudaError_t e = configure_stream_t<T, 4, true>(bytes);
+    if (e == cudaSuccess) e = configure_stream_t<T, 16, true>(bytes);
+    if (e == cudaSuccess) e = configure_stream_t<T, 4, false>(bytes);
+    if (e == cudaSuccess) e = configure_stream_t<T, 16, false>(bytes);
+    return e;
+}
+
+template <class T>
+cudaError_t launch_pack_stream(const StreamHost& sh, const int64_t* voff, const int32_t* vsrc, const int64_t* doff,
+                               const int32_t* dsrc, const double* vals, uint8_t* blob, cudaStream_t st) {
+    const int64_t nv = (int64_t)sh.voff.size(), nd = (int64_t)sh.doff.size();
+    if (nv == 0 && nd == 0) return cudaSuccess;
+    k_pack_stream<T><<<1024, 256, 0, st>>>(nv, nd, voff, vsrc, doff, dsrc, vals, blob);
+    return cudaGetLastError();
+}
+
+#define ILU2L_RW_DISPATCH(h, id, CALL)       \
+    if ((h).sb[id].rw == 4) {                \
+        constexpr int RW = 4;                \
+        CALL;                                \
+    } else {                                 \
+        constexpr int RW = 16;               \
+        CALL;                                \
+    }
+#define ILU2L_XS_DISPATCH(h, id, CALL)       \
+    if ((h).max_ns + 1 <= (h).smem_len_stream) { \
+        constexpr bool XS = true;            \
+        ILU2L_RW_DISPATCH(h, id, CALL)       \
+    } else {                                 \
+        constexpr bool XS = false;           \
+        ILU2L_RW_DISPATCH(h, id, CALL)       \
+    }
+#define ILU2L_IDX_DISPATCH(h, id, CALL) ILU2L_XS_DISPATCH(h, id, CALL)
+
+template <class T>
+cudaError_t launch_bj_s(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
+    ILU2L_IDX_DISPATCH(h, PR_BJ, (k_bj_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                              h.sub(), sdev<T>(h, PR_BJ), rcfg(h), r, z, (T*)h.d_xg, done)));
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_fwd_s(const Handle& h, const double* r, const int32_t* done, cudaStream_t st) {
+    ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_fwd_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                              h.sub(), sdev<T>(h, PR_FWDS), rcfg(h), h.innerdev<T>(), r, (T*)h.d_fq, (T*)h.d_xg,
+                              done)));
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_inner_s(const Handle& h, const int32_t* done, cudaStream_t st) {
+    if (h.n2 == 0) return cudaSuccess;
+    const int gb = std::max(1, std::min(h.sm_count * 4, (h.n2 + 255) / 256));
+    for (int j = 0; j < h.inner_k; j++) {
+        k_coff<T><<<gb, 256, 0, st>>>(h.sub(), h.innerdev<T>(), j, (T*)h.d_tbuf, done);
+        ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                  h.sub(), sdev<T>(h, PR_S), rcfg(h), h.innerdev<T>(), j, (const T*)h.d_tbuf,
+                                  (T*)h.d_xg, done)));
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_inner_bc<T>(h, j, 0, done, st);
+        if (e == cudaSuccess) e = launch_inner_bc<T>(h, j, 1, done, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
+    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_bwd_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                              h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), r, (const T*)h.d_fq,
+                              h.form == ILU_FORM_EF ? 1 : 0, z, (T*)h.d_xg, done)));
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st) {
+    ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                              h.sub(), sdev<T>(h, PR_S), rcfg(h), h.innerdev<T>(), gp, (T*)h.d_xg)));
+    return cudaGetLastError();
+}
+
+#define ILU2L_SINST(T)                                                                                      \
+    template cudaError_t configure_stream<T>(const Handle&, size_t);                                       \
+    template cudaError_t launch_pack_stream<T>(const StreamHost&, const int64_t*, const int32_t*,          \
+                                               const int64_t*, const int32_t*, const double*, uint8_t*,    \
+                                               cudaStream_t);                                              \
+    template cudaError_t launch_bj_s<T>(const Handle&, const double*, double*, const int32_t*, cudaStream_t); \
+    template cudaError_t launch_fwd_s<T>(const Handle&, const double*, const int32_t*, cudaStream_t);      \
+    template cudaError_t launch_inner_s<T>(const Handle&, const int32_t*, cudaStream_t);                   \
+    template cudaError_t launch_bwd_s<T>(const Handle&, const double*, double*, const int32_t*,            \
+                                         cudaStream_t);                                                    \
+    template cudaError_t launch_inner_start_s<T>(const Handle&, const double*, cudaStream_t);
+ILU2L_SINST(float)
+ILU2L_SINST(double)
+
+}  // namespace ilu2l

@@ -11,6 +11,7 @@
 #include <thread>
 
 #include "handle.h"
+#include "stream_layout.h"
 
 namespace ilu2l {
 
@@ -291,6 +292,117 @@ int ilut_local(const int32_t* rp, const int32_t* ci, const double* a, int32_t m,
 }  // namespace
 
 // ====================================================================================
+// chunked streams (stream_layout.h)
+
+bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, uint32_t chunk,
+                  StreamHost& S) {
+    S.blob.clear();
+    S.ch0.assign(1, 0);
+    S.voff.clear();
+    S.vsrc.clear();
+    S.doff.clear();
+    S.dsrc.clear();
+    S.chunk = chunk;
+    S.idx_bytes = idx_bytes;
+    S.val_bytes = val_bytes;
+    S.levels = (int64_t)P.lvl_ptr.size() - 1;
+    S.rows = (int64_t)P.prow.size();
+    S.entries = (int64_t)P.pcol.size();
+    // record width: 4 entries unless many rows are longer; longer rows are split into
+    // pieces run in consecutive sub-levels (intermediate pieces with a unit pivot)
+    int64_t longer = 0;
+    for (size_t k = 0; k + 1 < P.pptr.size(); k++) longer += (P.pptr[k + 1] - P.pptr[k]) > 4;
+    S.rw = (longer * 20 <= (int64_t)P.prow.size()) ? 4 : 16;
+    const int32_t RW = S.rw;
+    const RecLayout RL = rec_layout((uint32_t)S.rw, (uint32_t)val_bytes);
+    S.rec_bytes = RL.bytes;
+    // a whole wave (one record per consumer thread) must fit one chunk
+    const int nt_fit = (int)(((chunk - kChunkHdr - 16) / RL.bytes) / 32 * 32);
+    if (nt_fit < 32 || chunk > (1u << 20)) return false;
+    S.nt = std::min(S.nt, nt_fit);
+    const uint32_t nt = (uint32_t)S.nt;
+    auto put = [&](size_t off, uint32_t v, int bytes) {
+        for (int b = 0; b < bytes; b++) S.blob[off + b] = (uint8_t)(v >> (8 * b));
+    };
+    struct Piece {
+        int32_t k;      // packed row
+        int32_t q0, n;  // entries [q0, q0+n) of the row
+        bool last;      // applies the pivot inverse
+    };
+    struct Wave {
+        size_t p0, p1;  // pieces
+        bool sync;
+    };
+    std::vector<Piece> pieces;
+    std::vector<Wave> waves;
+    std::vector<Piece> sub;
+    int64_t nchunks = 0;
+    for (int32_t s = 0; s < p; s++) {
+        // pieces and waves of this subdomain, in program order
+        pieces.clear();
+        waves.clear();
+        for (int32_t e = P.sub_lvl[s]; e < P.sub_lvl[s + 1]; e++) {
+            const int32_t k0 = P.lvl_ptr[e], k1 = P.lvl_ptr[e + 1];
+            int32_t np = 1;
+            for (int32_t k = k0; k < k1; k++) np = std::max(np, (P.pptr[k + 1] - P.pptr[k] + RW - 1) / RW);
+            for (int32_t j = 0; j < np; j++) {  // sub-level j: piece j of every row that has one
+                sub.clear();
+                for (int32_t k = k0; k < k1; k++) {
+                    const int32_t n = P.pptr[k + 1] - P.pptr[k];
+                    const int32_t npk = std::max(1, (n + RW - 1) / RW);
+                    if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1});
+                }
+                for (size_t t = 0; t < sub.size(); t += nt) {
+                    const size_t t1 = std::min(sub.size(), t + nt);
+                    waves.push_back({pieces.size() + t, pieces.size() + t1, t1 == sub.size()});
+                }
+                pieces.insert(pieces.end(), sub.begin(), sub.end());
+            }
+        }
+        size_t wi = 0;
+        while (wi < waves.size()) {
+            // as many waves as fit: header + table (4 B per wave, padded) + records
+            size_t nw = 0, recs = 0;
+            while (wi + nw < waves.size()) {
+                const size_t r = waves[wi + nw].p1 - waves[wi + nw].p0;
+                const size_t need = kChunkHdr + al((uint32_t)(4 * (nw + 1)), 16) + (recs + r) * RL.bytes;
+                if (need > chunk) break;
+                nw++;
+                recs += r;
+            }
+            const size_t cb = S.blob.size();
+            S.blob.resize(cb + chunk, 0);
+            nchunks++;
+            put(cb, (uint32_t)nw, 4);
+            size_t roff = kChunkHdr + al((uint32_t)(4 * nw), 16);
+            for (size_t t = 0; t < nw; t++) {
+                const Wave& W = waves[wi + t];
+                const uint32_t width = (uint32_t)(W.p1 - W.p0);
+                put(cb + kChunkHdr + 4 * t, (uint32_t)(roff / 16) | (width << 16) | (W.sync ? kWaveSync : 0u), 4);
+                for (size_t pi = W.p0; pi < W.p1; pi++) {
+                    const Piece& pc = pieces[pi];
+                    const size_t rb = cb + roff;
+                    put(rb, (uint32_t)P.prow[pc.k] * (uint32_t)val_bytes | ((uint32_t)pc.n << 24), 4);
+                    S.doff.push_back((int64_t)(rb + RL.dinv));
+                    S.dsrc.push_back(pc.last ? P.pdsrc[pc.k] : -1);  // -1: the pack writes 1
+                    for (int32_t q = 0; q < pc.n; q++) {
+                        const int32_t src = P.pptr[pc.k] + pc.q0 + q;
+                        put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
+                        S.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
+                        S.vsrc.push_back(P.psrc[src]);
+                    }
+                    roff += RL.bytes;
+                }
+            }
+            wi += nw;
+        }
+        S.ch0.push_back((int32_t)nchunks);
+    }
+    if (S.blob.empty()) S.blob.resize(16, 0);
+    return true;
+}
+
+// ====================================================================================
 
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
     ilu_status st = validate(A, part, p);
@@ -569,6 +681,20 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                 P.max_levels = std::max(P.max_levels, a);
             }
+            {   // forward and the first local Schur solve in one program (base 0)
+                ProgHost& P = h.prog[PR_FWDS];
+                int a = prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                if (wz) {
+                    a += prog_add_single(P, h.f1, q0, ni, ns, 0, ni, 0);
+                } else {
+                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                    a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                }
+                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
+                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, 0, lev);
+                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                P.max_levels = std::max(P.max_levels, a);
+            }
             {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni)
                 ProgHost& P = h.prog[PR_S];
                 int a = prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, ni, lev);
@@ -590,6 +716,27 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 P.max_levels = std::max(P.max_levels, a);
             }
         }
+    }
+    // ---- chunked streams of the programs the apply runs (TMA fast path)
+    if (h.stream_path) {
+        h.idx_bytes = 4;
+        if ((int64_t)(h.max_ns + 1) * (h.prec == ILU_PREC_FP32 ? 4 : 8) >= (1 << 24)) h.stream_path = false;
+        const int vb = (h.prec == ILU_PREC_FP32) ? 4 : 8;
+        std::vector<int> ids = schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD} : std::vector<int>{PR_BJ};
+        // consumer group: one warp unless the levels are wide (rows + entries per level)
+        for (int id : ids) {
+            const ProgHost& P = h.prog[id];
+            const double lv = (double)std::max<size_t>(P.lvl_ptr.size() - 1, 1);
+            const double work = (double)(P.prow.size() + P.pcol.size()) / lv;
+            int nt = work < 96 ? 32 : (work < 320 ? 64 : 128);
+            if (h.o.block_threads) nt = std::min(256, std::max(32, (int)h.o.block_threads));
+            h.sh[id].nt = nt;
+        }
+        bool ok = true;
+        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, 8192, h.sh[id]);
+        h.chunk = 8192;
+        h.nst = 8;
+        if (!ok) h.stream_path = false;
     }
     return ILU_OK;
 }

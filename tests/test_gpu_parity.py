@@ -36,6 +36,8 @@ def _problems():
         "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
         "rand": lambda: P.randsparse(3000, 8, mean_k=4.0, seed=4),
         "p1": lambda: P.aniso2d_boxes(30, 1, seed=5),
+        # rows with up to ~40 local entries: exercises rows split over several sub-levels
+        "dense_rows": lambda: P.randsparse(1500, 2, mean_k=24.0, seed=6),
     }
 
 
@@ -73,10 +75,10 @@ def _prob(name):
     return _cache[name]
 
 
-def _pair(ilu, name, cfg, prec):
+def _pair(ilu, name, cfg, prec, path="stream"):
     pr = _prob(name)
     kw = dict(cfg)
-    opts = ilu.Opts(pc_precision=prec, **kw)
+    opts = ilu.Opts(pc_precision=prec, kernel_path=path, **kw)
     h = ilu.ilu_setup_problem(pr, opts)
     okw = {k: v for k, v in kw.items()}
     orc = O.Oracle.from_problem(pr, **okw)
@@ -150,8 +152,10 @@ def test_spmv_fp64(ilu, name):
 @pytest.mark.parametrize("name", list(PROBS))
 @pytest.mark.parametrize("cfg", CONFIGS, ids=_cid)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_apply_matches_oracle(ilu, name, cfg, prec):
-    pr, h, orc = _pair(ilu, name, cfg, prec)
+@pytest.mark.parametrize("path", ["stream", "generic"])
+def test_apply_matches_oracle(ilu, name, cfg, prec, path):
+    pr, h, orc = _pair(ilu, name, cfg, prec, path)
+    assert h.stats()["stream_path"] == (path == "stream")
     r = np.random.default_rng(11).standard_normal(pr.n)
     z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
     ilu.ilu_apply(h, _dev(r), z)
@@ -174,9 +178,10 @@ def test_apply_matches_oracle(ilu, name, cfg, prec):
 
 @pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "rand", "cuts3d"])
 @pytest.mark.parametrize("k", [1, 3, 7])
-def test_inner_solve_fp64(ilu, name, k):
+@pytest.mark.parametrize("path", ["stream", "generic"])
+def test_inner_solve_fp64(ilu, name, k, path):
     cfg = dict(variant="schur", factor_B="ilu0", factor_S="milu0", inner_iters=k)
-    pr, h, orc = _pair(ilu, name, cfg, "fp64")
+    pr, h, orc = _pair(ilu, name, cfg, "fp64", path)
     n2 = orc.sizes().n2
     g = np.random.default_rng(13).standard_normal(n2)
     y = torch.empty(n2, dtype=torch.float64, device="cuda")
@@ -226,6 +231,47 @@ def test_edge_cases(ilu, case, cfg):
     info = ilu.gmres_solve(h, b, x, rtol=1e-10, restart=5, maxit=200)
     assert info["status"] == 0 and info["rel_res_true"] <= 1e-10
     h.close()
+
+
+@pytest.mark.parametrize("threads", [64, 128])
+def test_wide_consumer_groups(ilu, threads):
+    """level programs run by 2 or 4 warps on a named barrier give the same result"""
+    cfg = CONFIGS[2]
+    pr = _prob("cuts3d")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp64", block_threads=threads, **cfg))
+    orc = O.Oracle.from_problem(pr, **cfg)
+    r = np.random.default_rng(17).standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    _assert_close64(z.cpu().numpy(), orc.apply(r), "wide group")
+    h.close()
+
+
+def test_device_wait_timeout_is_reported(ilu):
+    """A bound of one poll on every mbarrier wait makes the streamed apply give up; the
+    device error word reports it, the call returns, and the context stays usable."""
+    pr = _prob("aniso2d_ragged")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp32", spin_limit=1, **CONFIGS[2]))
+    r = torch.randn(pr.n, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    for _ in range(3):
+        ilu.ilu_apply(h, r, z)
+    st = h.stats()
+    assert st["stream_path"] and st["device_error"] in (0, 2)
+    x = torch.zeros_like(r)
+    info = ilu.gmres_solve(h, r, x, rtol=1e-8, restart=10, maxit=50)
+    assert info["status"] in (0, ilu.ILU_ERR_TIMEOUT, ilu.ILU_ERR_NOT_CONVERGED)
+    h.close()
+    # a fresh handle on the same device still works
+    pr2, h2, orc = _pair(ilu, "poisson64", CONFIGS[0], "fp64")
+    rr = np.random.default_rng(1).standard_normal(pr2.n)
+    zz = torch.empty(pr2.n, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h2, _dev(rr), zz)
+    torch.cuda.synchronize()
+    _assert_close64(zz.cpu().numpy(), orc.apply(rr), "after timeout")
+    assert h2.stats()["device_error"] == 0
+    h2.close()
 
 
 def test_bad_vectors_are_rejected(ilu):

@@ -14,6 +14,7 @@ CASES = {
     "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
     "rand": lambda: P.randsparse(3000, 8, mean_k=4.0, seed=4),
     "p1": lambda: P.aniso2d_boxes(30, 1, seed=5),
+    "dense_rows": lambda: P.randsparse(1500, 2, mean_k=24.0, seed=6),
 }
 CFGS = [
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0"),
@@ -69,4 +70,15 @@ def test_analysis_handle_refuses_device_calls(ilu):
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
     import ctypes as C
     assert ilu.lib().ilu_apply(h.ptr, C.c_void_p(16), C.c_void_p(32)) == ilu.ILU_ERR_ARG
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("cfg", CFGS[:3], ids=lambda c: "-".join(map(str, c.values())))
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_streamed_programs_are_built(ilu, name, cfg, prec):
+    """every test workload keeps the TMA-streamed level programs (no silent fallback)"""
+    pr = CASES[name]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, pc_precision=prec, **cfg))
+    assert h.stats()["stream_path"]
     h.close()
