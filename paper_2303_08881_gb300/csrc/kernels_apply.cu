@@ -300,15 +300,27 @@ cudaError_t launch_inner_bc(const Handle& h, int j, int second, const int32_t* d
     return cudaGetLastError();
 }
 
+// Per-kernel, process-wide limit: raised to the device maximum, never lowered.
+template <class K>
+static cudaError_t raise_limit(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 template <class T>
 cudaError_t configure_apply(size_t dyn_bytes) {
-    const int b = (int)dyn_bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_bj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_a<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_inner_start<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    (void)dyn_bytes;
+    cudaError_t e = raise_limit(k_bj<T>);
+    if (e == cudaSuccess) e = raise_limit(k_fwd<T>);
+    if (e == cudaSuccess) e = raise_limit(k_inner_a<T>);
+    if (e == cudaSuccess) e = raise_limit(k_bwd<T>);
+    if (e == cudaSuccess) e = raise_limit(k_inner_start<T>);
     return e;
 }
 

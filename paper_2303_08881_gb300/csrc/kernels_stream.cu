@@ -530,24 +530,39 @@ static size_t stream_smem(const Handle& h, size_t elt) {
     return 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * elt;
 }
 
-template <class T, int RW, bool XS>
-static cudaError_t configure_stream_t(size_t bytes) {
-    const int b = (int)bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_bj_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inner_a_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+// The dynamic shared-memory limit is per kernel and process-wide: it is raised to the
+// device maximum once (never to a handle's own size, which would shrink it under
+// handles created earlier with larger subdomains).
+template <class K>
+static cudaError_t raise_smem_limit(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_inner_start_s<T, RW, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
+template <class T, int RW, bool XS>
+static cudaError_t configure_stream_t() {
+    cudaError_t e = raise_smem_limit(k_bj_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_fwd_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_a_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_bwd_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_start_s<T, RW, XS>);
     return e;
 }
 
 template <class T>
 cudaError_t configure_stream(const Handle& h, size_t bytes) {
-    cudaError_t e = configure_stream_t<T, 4, true>(bytes);
-    if (e == cudaSuccess) e = configure_stream_t<T, 16, true>(bytes);
-    if (e == cudaSuccess) e = configure_stream_t<T, 4, false>(bytes);
-    if (e == cudaSuccess) e = configure_stream_t<T, 16, false>(bytes);
+    (void)h;
+    (void)bytes;
+    cudaError_t e = configure_stream_t<T, 4, true>();
+    if (e == cudaSuccess) e = configure_stream_t<T, 16, true>();
+    if (e == cudaSuccess) e = configure_stream_t<T, 4, false>();
+    if (e == cudaSuccess) e = configure_stream_t<T, 16, false>();
     return e;
 }
 

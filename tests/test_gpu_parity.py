@@ -274,6 +274,21 @@ def test_device_wait_timeout_is_reported(ilu):
     h2.close()
 
 
+@pytest.mark.parametrize("path", ["stream", "generic"])
+def test_handles_with_different_subdomain_sizes_coexist(ilu, path):
+    """the per-kernel shared-memory limit is process-wide state: a handle created later
+    with smaller subdomains must not break an earlier handle's launches"""
+    big, h_big, orc = _pair(ilu, "p1", CONFIGS[2], "fp64", path)   # one 900-row subdomain
+    small = ilu.ilu_setup_problem(_prob("poisson64"), ilu.Opts(pc_precision="fp64", kernel_path=path))
+    r = np.random.default_rng(23).standard_normal(big.n)
+    z = torch.empty(big.n, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h_big, _dev(r), z)
+    torch.cuda.synchronize()
+    _assert_close64(z.cpu().numpy(), orc.apply(r), "big after small")
+    small.close()
+    h_big.close()
+
+
 def test_bad_vectors_are_rejected(ilu):
     pr, h, _ = _pair(ilu, "poisson64", CONFIGS[0], "fp64")
     r = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
