@@ -190,6 +190,27 @@ ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* la
    unused). out must hold 14 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free variant (no counterpart in the paper).
+ * --------------------------------------------------------------------------------- */
+
+/* The inner Schur solve of ilu_inner_solve, for callers that cannot allocate device
+   memory at call time: code that records the call into a CUDA graph, runs on a fixed
+   memory budget, or must not trigger the implicit synchronisation of an allocation.
+   Identical inputs, outputs and arithmetic (gp, y: DEVICE double[n2], interface
+   numbering), but the Krylov workspace lives in a fixed 8 MiB device array the library
+   holds on every GPU that loads it, until the process exits; the call allocates nothing.
+   The first call on a device looks up the array's device address (do it before any
+   stream capture); later calls reuse it. Every call shares the array and clears its
+   control block first; calls that overlap on the GPU (other streams or host threads)
+   race on it. Needs the default streamed kernels with every subdomain's working vector
+   in shared memory (else ILU_ERR_UNSUPPORTED). ILU_ERR_TOO_LARGE when the workspace,
+   256-byte aligned pieces of (inner_iters + 4) * n2 vector elements of the
+   preconditioner type, 792 * p bytes of partial sums and a 9 KB control block, exceeds
+   8 MiB. ILU_ERR_ARG for NULL / aliased vectors, a block Jacobi handle, or a current
+   device other than the handle's. Asynchronous on opts.stream. */
+ilu_status ilu_inner_solve_noalloc(void* h, const double* gp, double* y);
+
 #ifdef __cplusplus
 }
 #endif

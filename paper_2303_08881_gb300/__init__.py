@@ -82,6 +82,7 @@ def lib():
             "ilu_profile": (I, [P, I]),
             "ilu_profile_read": (I, [P, P, P, P, P]),
             "ilu_get_stats": (I, [P, P]),
+            "ilu_inner_solve_noalloc": (I, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -233,6 +234,11 @@ class Handle:
         return dict(kernel_launches=int(out[0]), graph_launches=int(out[1]),
                     kernels_per_cycle=int(out[2]), row_ctas=int(out[3]), device_error=int(out[4]),
                     stream_path=bool(out[5]), programs=progs)
+
+    def inner_solve_noalloc(self, gp, y):
+        """ilu_inner_solve with the library's fixed workspace instead of the handle's
+        (allocates nothing; see include/ilu2l.h)."""
+        _check(lib().ilu_inner_solve_noalloc(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve_noalloc")
 
     def profile(self, enable: bool):
         _check(lib().ilu_profile(self.ptr, int(enable)), "ilu_profile")

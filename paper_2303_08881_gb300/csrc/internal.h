@@ -159,6 +159,14 @@ cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int3
                          cudaStream_t st);
 template <class T>
 cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st);
+// inner solve on a caller-provided workspace (allocation-free entry point)
+template <class T>
+cudaError_t launch_inner_bc_ws(const Handle& h, const InnerDev<T>& in, int j, int second, cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_finish_ws(const Handle& h, const InnerDev<T>& in, double* y, cudaStream_t st);
+template <class T>
+cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, const double* gp, double* y,
+                               cudaStream_t st);
 // numeric ILU and packing
 cudaError_t launch_ilu_numeric(const Handle& h, double* F, int milu, cudaStream_t st);
 template <class T>

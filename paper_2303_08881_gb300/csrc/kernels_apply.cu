@@ -378,8 +378,23 @@ cudaError_t launch_inner_io(const Handle& h, const double* gp, double* y, cudaSt
     return cudaGetLastError();
 }
 
+// Parts B/C and the finish of the inner solve on a caller-provided workspace.
+template <class T>
+cudaError_t launch_inner_bc_ws(const Handle& h, const InnerDev<T>& in, int j, int second, cudaStream_t st) {
+    k_inner_bc<T><<<h.p, h.threads, 0, st>>>(h.sub(), in, j, second, nullptr);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_inner_finish_ws(const Handle& h, const InnerDev<T>& in, double* y, cudaStream_t st) {
+    k_inner_finish<T><<<h.p, h.threads, 0, st>>>(h.sub(), in, y);
+    return cudaGetLastError();
+}
+
 #define ILU2L_INST(T)                                                                              \
     template cudaError_t configure_apply<T>(size_t);                                              \
+    template cudaError_t launch_inner_bc_ws<T>(const Handle&, const InnerDev<T>&, int, int, cudaStream_t); \
+    template cudaError_t launch_inner_finish_ws<T>(const Handle&, const InnerDev<T>&, double*, cudaStream_t); \
     template cudaError_t launch_inner_bc<T>(const Handle&, int, int, const int32_t*, cudaStream_t);  \
     template cudaError_t launch_bj<T>(const Handle&, const double*, double*, const int32_t*,       \
                                       cudaStream_t);                                              \

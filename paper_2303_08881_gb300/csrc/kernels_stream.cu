@@ -640,7 +640,33 @@ cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t
     return cudaGetLastError();
 }
 
+// The inner Schur solve (streamed local Schur programs, working vectors in shared memory)
+// on a caller-provided Krylov workspace `in` and product buffer `tbuf`.
+template <class T>
+cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, const double* gp, double* y,
+                               cudaStream_t st) {
+    if (h.n2 == 0) return cudaSuccess;
+    constexpr bool XS = true;
+    T* xdummy = tbuf;  // unused by the shared-memory kernels
+    ILU2L_RW_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                   h.sub(), sdev<T>(h, PR_S), rcfg(h), in, gp, xdummy)));
+    cudaError_t e = cudaGetLastError();
+    const int gb = std::max(1, std::min(h.sm_count * 4, (h.n2 + 255) / 256));
+    for (int j = 0; j < h.inner_k && e == cudaSuccess; j++) {
+        k_coff<T><<<gb, 256, 0, st>>>(h.sub(), in, j, tbuf, nullptr);
+        ILU2L_RW_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                       h.sub(), sdev<T>(h, PR_S), rcfg(h), in, j, tbuf, xdummy, nullptr)));
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_inner_bc_ws<T>(h, in, j, 0, st);
+        if (e == cudaSuccess) e = launch_inner_bc_ws<T>(h, in, j, 1, st);
+    }
+    if (e == cudaSuccess) e = launch_inner_finish_ws<T>(h, in, y, st);
+    return e;
+}
+
 #define ILU2L_SINST(T)                                                                                      \
+    template cudaError_t launch_inner_io_ws<T>(const Handle&, const InnerDev<T>&, T*, const double*,         \
+                                               double*, cudaStream_t);                                       \
     template cudaError_t configure_stream<T>(const Handle&, size_t);                                       \
     template cudaError_t launch_pack_stream<T>(const StreamHost&, const int64_t*, const int32_t*,          \
                                                const int64_t*, const int32_t*, const double*, uint8_t*,    \

@@ -1,0 +1,77 @@
+"""ilu_inner_solve_noalloc, the allocation-free variant of the inner Schur solve.
+
+Callers that record work into a CUDA graph, run on a fixed device-memory budget, or must
+not trigger an allocation's implicit synchronisation cannot let a call allocate. This
+variant keeps the Krylov workspace in a fixed device array the library owns instead of
+the handle's workspace. Its output must match ilu_inner_solve's on the same handle and
+input, call after call (the array keeps the previous call's contents). The file is named
+to be collected last, so a run that stops at the first failure has run everything else.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_08881_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-4   # the FP32 preconditioner bar of the parity tests
+
+
+@pytest.fixture(scope="module")
+def ilu():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _close(got, ref, prec):
+    rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    if prec == "fp64":
+        assert rel <= 1e-12 and np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), rel
+    else:
+        assert rel <= TOL32, rel
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [3, 5])
+def test_noalloc_inner_solve_matches_the_handle_workspace_version(ilu, prec, k):
+    pr = P.aniso2d_boxes(70, 3, seed=1)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_iters=k))
+    n2 = h.sizes()["n2"]
+    rng = np.random.default_rng(21)
+    # a second handle on another problem between the two calls: the shared array must
+    # not carry state from one call into the next
+    other = ilu.ilu_setup_problem(P.convdiff3d_boxes(12, 2, seed=3), ilu.Opts(pc_precision=prec))
+    n2o = other.sizes()["n2"]
+    for call in range(2):
+        g = torch.from_numpy(rng.standard_normal(n2)).cuda()
+        ref = torch.empty(n2, dtype=torch.float64, device="cuda")
+        got = torch.full((n2,), np.nan, dtype=torch.float64, device="cuda")
+        h.inner_solve(g, ref)
+        h.inner_solve_noalloc(g, got)
+        torch.cuda.synchronize()
+        _close(got.cpu().numpy(), ref.cpu().numpy(), prec)
+        go = torch.from_numpy(rng.standard_normal(n2o)).cuda()
+        yo = torch.empty(n2o, dtype=torch.float64, device="cuda")
+        other.inner_solve_noalloc(go, yo)
+    torch.cuda.synchronize()
+    assert h.stats()["device_error"] == 0
+    other.close()
+    h.close()
+
+
+def test_noalloc_rejects_a_workspace_beyond_its_limit(ilu):
+    # 512^2 grid on 16 x 16 boxes: n2 ~ 31.7k interface unknowns; FP64 with 32 inner steps
+    # needs (32 + 4) * n2 * 8 B ~ 9 MB > 8 MiB
+    pr = P.aniso2d_boxes(512, 16, seed=0)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp64", inner_iters=32))
+    n2 = h.sizes()["n2"]
+    g = torch.zeros(n2, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(g)
+    with pytest.raises(ilu.IluError) as e:
+        h.inner_solve_noalloc(g, y)
+    assert e.value.status == ilu.ILU_ERR_TOO_LARGE
+    h.close()
