@@ -189,6 +189,7 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     const size_t n = (size_t)std::max(h.n, 1);
     h.fg_G = h.sm_count * 4;
     h.fg_threads = 256;
+    CK(configure_krylov());
     FgDev f{};
     f.V = h.alloc<double>((size_t)(m + 1) * n, &e);
     f.Z = h.alloc<double>((size_t)m * n, &e);
@@ -474,7 +475,7 @@ ilu_status ilu_inner_solve(void* hp, const double* gp, double* y) {
 
 ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_t restart, int32_t maxit,
                        ilu_solve_info* info) {
-    if (!hp || !b || !x || b == x || restart < 1 || restart > kMaxRestart || maxit < 0 || !(rtol >= 0.0))
+    if (!hp || !b || !x || b == x || restart < 1 || restart > kMaxRestartGS || maxit < 0 || !(rtol >= 0.0))
         return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
     if (h->o.analysis_only) return ILU_ERR_ARG;

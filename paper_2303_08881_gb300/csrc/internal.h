@@ -22,6 +22,7 @@ namespace ilu2l {
 
 constexpr int kMaxInner = 32;   // inner GMRES steps supported on the device
 constexpr int kMaxRestart = 400;
+constexpr int kMaxRestartGS = 64;  // restart limit of gmres_solve (register-resident Gram-Schmidt)
 
 // ---- a level program: rows of every subdomain scheduled level by level --------------
 // Rows of subdomain s are processed in levels [sub_lvl[s], sub_lvl[s+1]); level e covers
@@ -178,6 +179,7 @@ cudaError_t launch_fg_resid(const Handle& h, const double* b, const double* x, i
 cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st);
 cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st);
 cudaError_t launch_fg_cgs(const Handle& h, int j, cudaStream_t st);
+cudaError_t configure_krylov();
 cudaError_t launch_fg_norm(const Handle& h, int j, cudaStream_t st);
 cudaError_t launch_fg_next(const Handle& h, int j, cudaStream_t st);
 cudaError_t launch_fg_update(const Handle& h, double* x, cudaStream_t st);

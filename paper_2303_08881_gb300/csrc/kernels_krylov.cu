@@ -12,10 +12,14 @@
 //   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w
 //   k_fg_norm      w -= V h2, ||w||, Givens rotation, residual estimate, stop decision
 //   k_fg_next      v_{j+1} = w / ||w||
+#include <algorithm>
+
 #include "devutil.cuh"
 #include "handle.h"
 
 namespace ilu2l {
+
+constexpr int kMaxJ = 63;  // basis vectors a Gram-Schmidt kernel handles (restart <= 64)
 
 __device__ __forceinline__ void cta_rows(int n, int& r0, int& r1) {
     const int R = (n + gridDim.x - 1) / gridDim.x;
@@ -142,14 +146,78 @@ __global__ void k_fg_scale0(FgDev f, int n) {
         f.V[r] = f.V[r] * inv;
 }
 
-// w = A z_j; partial dots V_i . w, i <= j; last CTA stores h1 in column j of H
+// Gram-Schmidt kernels. Each CTA owns a contiguous row range (cta_rows). Updates
+// w -= V h run one row per thread with eight basis rows in flight. Dot products V_i . w
+// run in chunks of eight vectors: each thread accumulates its rows, each warp reduces its
+// eight sums with shuffles and adds them to its own shared accumulators (no CTA barrier
+// per chunk); one barrier at the end combines the warps in a fixed order.
+constexpr int kChunk = 8;
+
+// sacc[warp * (kMaxJ + 1) + i] += V_i . w over the CTA's rows, i <= j (w in global memory,
+// written by this CTA before a barrier)
+__device__ __forceinline__ void cta_dots(const double* __restrict__ V, const double* w, size_t n, int r0,
+                                         int r1, int j, double* sacc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = 0; i0 <= j; i0 += kChunk) {
+        double acc[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; u++) acc[u] = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const double wr = w[r];
+#pragma unroll
+            for (int u = 0; u < kChunk; u++)
+                if (i0 + u <= j) acc[u] += V[(size_t)(i0 + u) * n + r] * wr;
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; u++) {
+            const double s = warp_sum(acc[u]);
+            if (lane == 0 && i0 + u <= j) sacc[warp * (kMaxJ + 1) + i0 + u] += s;
+        }
+    }
+}
+
+// w[r] -= sum_i h[i] V_i[r] over the CTA's rows, eight basis rows in flight
+__device__ __forceinline__ void cta_update(const double* __restrict__ V, double* w, const double* hh, size_t n,
+                                           int r0, int r1, int j, double* nrm2) {
+    double acc = 0.0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double x = w[r];
+        int i = 0;
+        for (; i + 8 <= j + 1; i += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = V[(size_t)(i + u) * n + r];
+#pragma unroll
+            for (int u = 0; u < 8; u++) x -= hh[i + u] * v[u];
+        }
+        for (; i <= j; i++) x -= hh[i] * V[(size_t)i * n + r];
+        w[r] = x;
+        acc += x * x;
+    }
+    if (nrm2) *nrm2 = acc;
+}
+
+// combine the per-warp accumulators (fixed warp order) into the CTA's partials
+__device__ __forceinline__ void cta_partials(const double* sacc, int j, double* part, int G) {
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += sacc[w * (kMaxJ + 1) + u];
+        part[(size_t)u * G + blockIdx.x] = s;
+    }
+}
+
+// w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w; the last CTA stores h1 in
+// column j of H
 template <int VL>
-__global__ void k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
-    __shared__ double red[32 * 8];
+__global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
+    __shared__ double sacc[8 * (kMaxJ + 1)];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(A.n, r0, r1);
     const int n = A.n;
+    for (int u = threadIdx.x; u < 8 * (kMaxJ + 1); u += blockDim.x) sacc[u] = 0.0;
     const double* __restrict__ zj = f.Z + (size_t)j * n;
     const int sl = threadIdx.x & (VL - 1), sub = threadIdx.x / VL, nsub = blockDim.x / VL;
     for (int base = r0; base < r1; base += nsub) {
@@ -159,56 +227,29 @@ __global__ void k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
         if (valid && sl == 0) f.w[r] = s;
     }
     __syncthreads();
-    for (int i0 = 0; i0 <= j; i0 += 8) {
-        double acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) acc[u] = 0.0;
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const double w = f.w[r];
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (i0 + u <= j) acc[u] += f.V[(size_t)(i0 + u) * n + r] * w;
-        }
-        block_sum_n<8>(acc, red);
-        if (threadIdx.x == 0)
-            for (int u = 0; u < 8 && i0 + u <= j; u++) f.part[(size_t)(i0 + u) * f.G + blockIdx.x] = acc[u];
-    }
+    cta_dots(f.V, f.w, n, r0, r1, j, sacc);
+    cta_partials(sacc, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, j + 1, f.H + (size_t)j * (f.m + 1));
     if (threadIdx.x == 0) f.ctl->counter = 0;
 }
 
-// w -= V h (h = column j of H); second pass dots; last CTA adds them to column j and
-// keeps them in f.h2 for k_fg_norm
-__global__ void k_fg_cgs(FgDev f, int n, int j) {
-    __shared__ double red[32 * 8];
-    __shared__ double hh[kMaxRestart + 1];
+// w -= V h1 (h1 = column j of H) and the reorthogonalisation dots V^T w; the last CTA
+// adds them to column j and keeps them in f.h2 for k_fg_norm
+__global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
+    __shared__ double sacc[8 * (kMaxJ + 1)];
+    __shared__ double hh[kMaxJ + 1];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
     const double* Hj = f.H + (size_t)j * (f.m + 1);
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) hh[i] = __ldcg(Hj + i);
+    for (int u = threadIdx.x; u < 8 * (kMaxJ + 1); u += blockDim.x) sacc[u] = 0.0;
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) hh[u] = __ldcg(Hj + u);
     __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double w = f.w[r];
-        for (int i = 0; i <= j; i++) w -= hh[i] * f.V[(size_t)i * n + r];
-        f.w[r] = w;
-    }
+    cta_update(f.V, f.w, hh, n, r0, r1, j, nullptr);
     __syncthreads();
-    for (int i0 = 0; i0 <= j; i0 += 8) {
-        double acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) acc[u] = 0.0;
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const double w = f.w[r];
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (i0 + u <= j) acc[u] += f.V[(size_t)(i0 + u) * n + r] * w;
-        }
-        block_sum_n<8>(acc, red);
-        if (threadIdx.x == 0)
-            for (int u = 0; u < 8 && i0 + u <= j; u++) f.part[(size_t)(i0 + u) * f.G + blockIdx.x] = acc[u];
-    }
+    cta_dots(f.V, f.w, n, r0, r1, j, sacc);
+    cta_partials(sacc, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, j + 1, f.h2);
     if (threadIdx.x == 0) {
@@ -218,22 +259,17 @@ __global__ void k_fg_cgs(FgDev f, int n, int j) {
 }
 
 // w -= V h2; ||w||; Givens; estimate; stop decision
-__global__ void k_fg_norm(FgDev f, int n, int j) {
+__global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     __shared__ double red[32];
-    __shared__ double hh[kMaxRestart + 1];
+    __shared__ double hh[kMaxJ + 1];
     __shared__ double tot[1];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) hh[i] = __ldcg(f.h2 + i);
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) hh[u] = __ldcg(f.h2 + u);
     __syncthreads();
     double acc = 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double w = f.w[r];
-        for (int i = 0; i <= j; i++) w -= hh[i] * f.V[(size_t)i * n + r];
-        f.w[r] = w;
-        acc += w * w;
-    }
+    cta_update(f.V, f.w, hh, n, r0, r1, j, &acc);
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
     if (!last_cta(&f.ctl->counter)) return;
@@ -370,6 +406,8 @@ cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st) {
     k_fg_scale0<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n);
     return cudaGetLastError();
 }
+
+cudaError_t configure_krylov() { return cudaSuccess; }
 
 cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
     const int vl = pick_vl(h);
