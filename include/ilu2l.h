@@ -191,6 +191,30 @@ ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* la
    unused). out must hold 14 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
+/* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device
+   consumes it): program 0 = block Jacobi, 1 = forward (L_B, the W rows and S~), 2 = local
+   Schur S~ alone, 3 = backward. out[0] = entries per row record, out[1] = consumer
+   threads, out[2] = chunks, out[3] = waves, out[4] = row records including skip records,
+   out[5] = skip records, out[6] = group barriers of the longest subdomain program,
+   out[7] = levels of the deepest subdomain program (the barriers a plain level schedule
+   would need), out[8] = bytes of the shared-memory ring the chunks stream through,
+   out[9] = 1 when every subdomain's working vector fits in shared memory beside the ring
+   (else the kernels keep it in a global scratch vector; known once the device setup ran,
+   0 for analysis-only handles). A program the handle does not use reports zeros. out
+   must hold 10 values.
+   Host-side only: needs no device. Errors: ILU_ERR_ARG for a null pointer or a program
+   outside 0..3. */
+ilu_status ilu_get_stream_stats(void* h, int32_t program, int64_t* out);
+
+/* Copy of one streamed program as the host built it (values and pivot inverses are
+   filled on the device, so the copy holds zeros there): blob = the chunks (layout in the
+   comment of csrc/stream_layout.h), ch0 = p+1 chunk offsets per subdomain, meta[0] =
+   blob bytes, meta[1] = chunk bytes, meta[2] = entries per record, meta[3] = value bytes,
+   meta[4] = consumer threads. Call with blob = ch0 = NULL to read meta first; blob must
+   hold meta[0] bytes and ch0 p+1 values. Host-side only. Errors: ILU_ERR_ARG (null
+   handle or meta, program outside 0..3), ILU_ERR_UNSUPPORTED (program not built). */
+ilu_status ilu_get_stream(void* h, int32_t program, uint8_t* blob, int32_t* ch0, int64_t* meta);
+
 /* ---------------------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  * --------------------------------------------------------------------------------- */

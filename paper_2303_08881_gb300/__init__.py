@@ -82,6 +82,8 @@ def lib():
             "ilu_profile": (I, [P, I]),
             "ilu_profile_read": (I, [P, P, P, P, P]),
             "ilu_get_stats": (I, [P, P]),
+            "ilu_get_stream_stats": (I, [P, I, P]),
+            "ilu_get_stream": (I, [P, I, P, P, P]),
             "ilu_inner_solve_noalloc": (I, [P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -234,6 +236,31 @@ class Handle:
         return dict(kernel_launches=int(out[0]), graph_launches=int(out[1]),
                     kernels_per_cycle=int(out[2]), row_ctas=int(out[3]), device_error=int(out[4]),
                     stream_path=bool(out[5]), programs=progs)
+
+    def stream_stats(self, program: str) -> dict:
+        """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,
+        consumer threads, chunks, waves, records, skip records, group barriers of the
+        longest subdomain program, levels of the deepest one, ring bytes and whether the
+        working vectors stay in shared memory."""
+        out = np.zeros(10, np.int64)
+        idx = ["bj", "fwd", "s", "bwd"].index(program)
+        _check(lib().ilu_get_stream_stats(self.ptr, idx, out.ctypes.data_as(C.c_void_p)), "ilu_get_stream_stats")
+        keys = ["record_entries", "threads", "chunks", "waves", "records", "skips", "max_barriers", "max_levels",
+                "ring_bytes", "vector_in_shared"]
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def stream(self, program: str) -> dict:
+        """The streamed program ("bj", "fwd", "s", "bwd") as built on the host: raw chunk
+        bytes, per-subdomain chunk offsets and the record geometry."""
+        idx = ["bj", "fwd", "s", "bwd"].index(program)
+        meta = np.zeros(5, np.int64)
+        _check(lib().ilu_get_stream(self.ptr, idx, None, None, meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
+        blob = np.zeros(int(meta[0]), np.uint8)
+        ch0 = np.zeros(self.sizes()["p"] + 1, np.int32)
+        _check(lib().ilu_get_stream(self.ptr, idx, blob.ctypes.data_as(C.c_void_p), ch0.ctypes.data_as(C.c_void_p),
+                                    meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
+        return dict(blob=blob, ch0=ch0, chunk=int(meta[1]), rw=int(meta[2]), val_bytes=int(meta[3]),
+                    threads=int(meta[4]))
 
     def inner_solve_noalloc(self, gp, y):
         """ilu_inner_solve with the library's fixed workspace instead of the handle's

@@ -68,7 +68,13 @@ ilu_status device_setup_t(Handle& h) {
     const int64_t cap = std::max<int64_t>(0, (int64_t)optin - 20 * 1024) / (int64_t)sizeof(T);
     h.smem_len = (int32_t)std::min<int64_t>(h.max_ns, cap);
     CK(configure_apply<T>((size_t)h.smem_len * sizeof(T)));
-    const bool need_xg = h.max_ns > h.smem_len;
+    if (h.stream_path) {  // the streamed kernels keep the ring in shared memory too
+        const int64_t cap_s = ((int64_t)optin - 20 * 1024 - 128 - (int64_t)h.nst * h.chunk) / (int64_t)sizeof(T);
+        h.smem_len_stream = (int32_t)std::max<int64_t>(0, std::min<int64_t>((int64_t)h.max_ns + 1, cap_s));
+    }
+    // a global working vector whenever some kernel family cannot hold every subdomain in
+    // shared memory (the generic kernels need max_ns elements, the streamed max_ns + 1)
+    const bool need_xg = h.max_ns > h.smem_len || (h.stream_path && h.max_ns + 1 > h.smem_len_stream);
     h.d_xg = h.alloc<T>(need_xg ? (size_t)n : 1, &e);
     if (!h.d_xg) return map_err(e);
     h.d_fq = h.alloc<T>((size_t)std::max(n, 1), &e);
@@ -88,8 +94,6 @@ ilu_status device_setup_t(Handle& h) {
     cv.clear();
     cv.shrink_to_fit();
     if (h.stream_path) {
-        const int64_t cap = ((int64_t)optin - 20 * 1024 - 128 - (int64_t)h.nst * h.chunk) / (int64_t)sizeof(T);
-        h.smem_len_stream = (int32_t)std::max<int64_t>(0, std::min<int64_t>((int64_t)h.max_ns + 1, cap));
         CK(configure_stream<T>(h, 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * sizeof(T)));
         h.d_tbuf = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
         if (!h.d_tbuf) return map_err(e);
@@ -407,6 +411,12 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
     h->st = (cudaStream_t)o.stream;
     h->threads = o.block_threads ? o.block_threads : 256;
     h->stream_path = (o.kernel_path == 0);
+    if (!o.analysis_only) {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && optin > 0)
+            h->smem_optin = optin;
+    }
     ilu_status s = host_setup(*h, A, part, p);
     if (s == ILU_OK && o.analysis_only) {
         h->setup_ms = now_ms() - t0;
@@ -676,6 +686,42 @@ ilu_status ilu_get_stats(void* hp, int64_t* out) {
         out[6 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].rw;
         out[7 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].nt;
     }
+    return ILU_OK;
+}
+
+ilu_status ilu_get_stream_stats(void* hp, int32_t program, int64_t* out) {
+    if (!hp || !out || program < 0 || program > 3) return ILU_ERR_ARG;
+    const Handle* h = (const Handle*)hp;
+    const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
+    const StreamHost& S = h->sh[ids[program]];
+    for (int i = 0; i < 10; i++) out[i] = 0;
+    if (S.ch0.empty()) return ILU_OK;
+    out[8] = (int64_t)h->nst * h->chunk;
+    out[9] = (!h->o.analysis_only && h->max_ns + 1 <= h->smem_len_stream) ? 1 : 0;
+    out[0] = S.rw;
+    out[1] = S.nt;
+    out[2] = S.ch0.back();
+    out[3] = S.waves;
+    out[4] = S.records;
+    out[5] = S.skips;
+    out[6] = S.max_barriers;
+    out[7] = S.max_levels_sub;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_stream(void* hp, int32_t program, uint8_t* blob, int32_t* ch0, int64_t* meta) {
+    if (!hp || !meta || program < 0 || program > 3) return ILU_ERR_ARG;
+    const Handle* h = (const Handle*)hp;
+    const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
+    const StreamHost& S = h->sh[ids[program]];
+    if (S.ch0.empty()) return ILU_ERR_UNSUPPORTED;
+    meta[0] = (int64_t)S.blob.size();
+    meta[1] = S.chunk;
+    meta[2] = S.rw;
+    meta[3] = S.val_bytes;
+    meta[4] = S.nt;
+    if (blob) memcpy(blob, S.blob.data(), S.blob.size());
+    if (ch0) memcpy(ch0, S.ch0.data(), S.ch0.size() * sizeof(int32_t));
     return ILU_OK;
 }
 

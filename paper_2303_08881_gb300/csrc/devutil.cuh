@@ -45,6 +45,19 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return a[0];
 }
 
+// Sum of a[0..m) by one warp: lane l adds a[l], a[l+32], ... in order, then a butterfly
+// (xor) exchange combines the lanes. Both partners of every exchange add the same two
+// values, so all lanes -- and every warp or CTA that calls this on the same data -- end
+// with the same bits. All 32 lanes of the warp must call it.
+__device__ __forceinline__ double warp_allsum_ldcg(const double* a, int m) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += __ldcg(a + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return s;
+}
+
 // Fixed-order sum of a[0..m) (each thread obtains the same value).
 __device__ __forceinline__ double seq_sum_ldcg(const double* a, int m) {
     double s = 0.0;

@@ -32,6 +32,9 @@ struct StreamHost {
     uint32_t rec_bytes = 32;
     int nt = 32;                      // threads of the consumer group
     int64_t levels = 0, rows = 0, entries = 0;
+    int64_t waves = 0, segments = 0, records = 0, skips = 0;  // totals over the subdomains
+    int64_t max_barriers = 0;                   // group barriers of the longest subdomain program
+    int64_t max_levels_sub = 0;                 // levels of the deepest subdomain program
 };
 
 struct StreamBufs {
@@ -95,8 +98,9 @@ struct Handle {
     StreamBufs sb[PR_COUNT];
     bool stream_path = true;          // TMA-streamed level programs (else generic kernels)
     int idx_bytes = 2;                // local index width of the streams
-    int nst = 8;                      // ring stages
+    int nst = 4;                      // ring stages
     uint32_t chunk = 8192;            // bytes per chunk / ring stage
+    int smem_optin = 232448;          // the device's shared memory per block (opt-in)
     int32_t smem_len_stream = 0;      // working-vector capacity with the ring present
     void* d_tbuf = nullptr;           // C_off product of the inner step (interface numbering)
     int32_t *d_num_sub = nullptr, *d_num_lvl = nullptr, *d_num_row = nullptr;

@@ -4,26 +4,32 @@
 // left; the Krylov coefficients t[] end up in shared memory.
 #pragma once
 
+#include "devutil.cuh"
 #include "internal.h"
 
 namespace ilu2l {
 
 // Least squares of the inner GMRES (Givens rotations, back substitution), computed
-// redundantly by thread 0 of every CTA into t[] (shared); returns the step count.
+// redundantly in every CTA into t[] (shared); returns the step count. The block copies
+// the Hessenberg columns and warp 0 forms the last norm; thread 0 then rotates.
 static __device__ __noinline__ int inner_lsq(const InnerCtl* ctl, const double* part, int p, int k, double* t) {
     __shared__ double Hs[(kMaxInner + 1) * kMaxInner];
     __shared__ double g[kMaxInner + 1], cs[kMaxInner], sn[kMaxInner];
+    __shared__ double last_nrm;
     __shared__ int steps_s;
+    for (int i = threadIdx.x; i < (kMaxInner + 1) * k; i += blockDim.x) Hs[i] = ctl->H[i];
+    if (threadIdx.x < 32) {
+        const double nrm2 = warp_allsum_ldcg(part + ((size_t)(2 * (kMaxInner + 1))) * p, p);
+        if (threadIdx.x == 0) last_nrm = sqrt(nrm2);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int steps = ctl->steps;
         const int zero = ctl->zero;
-        for (int i = 0; i < (kMaxInner + 1) * kMaxInner; i++) Hs[i] = ctl->H[i];
         if (zero) {
             steps = 0;
         } else if (steps < 0) {  // ran all k steps: the last norm is still in the partials
-            double nrm2 = 0.0;
-            for (int s2 = 0; s2 < p; s2++) nrm2 += __ldcg(part + ((size_t)(2 * (kMaxInner + 1))) * p + s2);
-            Hs[(k - 1) * (kMaxInner + 1) + k] = sqrt(nrm2);
+            Hs[(k - 1) * (kMaxInner + 1) + k] = last_nrm;
             steps = k;
         }
         for (int i = 0; i <= kMaxInner; i++) g[i] = 0.0;

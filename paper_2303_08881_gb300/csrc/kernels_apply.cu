@@ -136,9 +136,7 @@ __global__ void k_inner_a(SubDev sd, ProgDev<T> PS, InnerDev<T> in, int j, T* xg
     const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
     // every CTA forms the same norm from the same partials in the same order
-    double nrm2 = 0.0;
-    for (int t = 0; t < p; t++) nrm2 += __ldcg(ipart(in.part, kBankNorm, 0, t, p));
-    const double nrm = sqrt(nrm2);
+    const double nrm = sqrt(warp_allsum_ldcg(ipart(in.part, kBankNorm, 0, 0, p), p));
     if (j == 0) {
         if (s == 0 && threadIdx.x == 0) ctl->beta = nrm;
         if (nrm == 0.0) {
@@ -203,10 +201,12 @@ __global__ void k_inner_bc(SubDev sd, InnerDev<T> in, int j, int second, const i
     const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
     const int ns = sd.qoff[s + 1] - sd.qoff[s], ni = sd.nint[s], nf = ns - ni;
     const int bank = second ? kBankDot2 : kBankDot1;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        double h = 0.0;
-        for (int t = 0; t < p; t++) h += __ldcg(ipart(in.part, bank, i, t, p));
-        hh[i] = h;
+    {  // warp w sums the partials of coefficients w, w + nwarps, ...
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = threadIdx.x >> 5; i <= j; i += nw) {
+            const double h = warp_allsum_ldcg(ipart(in.part, bank, i, 0, p), p);
+            if (lane == 0) hh[i] = h;
+        }
     }
     __syncthreads();
     if (s == 0 && threadIdx.x == 0) {

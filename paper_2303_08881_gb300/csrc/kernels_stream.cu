@@ -86,7 +86,27 @@ __device__ __forceinline__ void group_sync(int nt) {
         asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
 }
 
-// Shared-memory layout of every stream kernel: [mbarriers 128 B][ring nst*chunk][x ...]
+// Release of a ring stage by one consumer thread (the stage's "empty" barrier counts all
+// consumer threads; arrive has release semantics, the producer's wait acquires).
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// True in every consumer thread iff v holds in all of them (a group barrier).
+__device__ __forceinline__ bool group_all(bool v, int nt) {
+    if (nt <= 32) return __all_sync(kFull, v);
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(nt)
+        : "memory");
+    return r != 0;
+}
+
+// Shared-memory layout of every stream kernel:
+// [mbarriers 128 B: full[nst], empty[nst]][ring nst*chunk][x ...]
 struct Smem {
     uint64_t* bars;
     uint8_t* ring;
@@ -106,7 +126,10 @@ __device__ __forceinline__ Smem smem_parts(int nst, uint32_t chunk) {
 template <class T>
 __device__ __forceinline__ void ring_start(const StreamDev<T>& S, int s, const Smem& sm, int nst) {
     if (threadIdx.x != 0) return;
-    for (int i = 0; i < nst; i++) mbar_init(&sm.bars[i], 1);
+    for (int i = 0; i < nst; i++) {
+        mbar_init(&sm.bars[i], 1);            // full: the copy's bytes arrived
+        mbar_init(&sm.bars[nst + i], S.nt);   // empty: every consumer thread is done with it
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
@@ -120,10 +143,10 @@ __device__ __forceinline__ void ring_start(const StreamDev<T>& S, int s, const S
 // Row record (stream_layout.h), read with 128-bit shared-memory loads.
 template <class T, int RW>
 struct __align__(16) RowRec {
-    uint32_t head;  // byte offset of x[row] | n << 24
+    uint32_t head;  // byte offset of x[row] | n << 24 | skip bit
     T dinv;
-    uint32_t col[RW];  // byte offsets
-    T val[RW];
+    uint32_t col[RW];  // byte offsets (unused entries: the row's own)
+    T val[RW];         // (unused entries: zero)
 };
 
 template <class T, int RW>
@@ -133,16 +156,12 @@ union RecU {
 };
 
 template <class T, int RW>
-__device__ __forceinline__ void rec_load(RecU<T, RW>& u, const uint8_t* p, bool valid) {
+__device__ __forceinline__ void rec_load(RecU<T, RW>& u, const uint8_t* p) {
     constexpr int NV = sizeof(RowRec<T, RW>) / 16;
     static_assert(sizeof(RowRec<T, RW>) == rec_layout(RW, sizeof(T)).bytes, "record layout");
-    if (valid) {
-        const uint4* s = reinterpret_cast<const uint4*>(p);
+    const uint4* s = reinterpret_cast<const uint4*>(p);
 #pragma unroll
-        for (int i = 0; i < NV; i++) u.v[i] = s[i];
-    } else {
-        u.r.head = 0xFFFFFFFFu;
-    }
+    for (int i = 0; i < NV; i++) u.v[i] = s[i];
 }
 
 template <class T>
@@ -150,106 +169,147 @@ __device__ __forceinline__ T ldx(const uint8_t* xb, uint32_t off) {
     return *reinterpret_cast<const T*>(xb + off);
 }
 
-// x[row] = (x[row] - sum_q val[q] x[col[q]]) * dinv; the sum is formed pairwise
+// operands of a record: x[col[q]] and x[row]
 template <class T, int RW>
-__device__ __forceinline__ void rec_run(const RecU<T, RW>& u, uint8_t* xb) {
-    const uint32_t head = u.r.head;
-    if (head == 0xFFFFFFFFu) return;
-    const uint32_t roff = head & 0xFFFFFFu, n = head >> 24;
+__device__ __forceinline__ void rec_operands(const RecU<T, RW>& u, const uint8_t* xb, T (&xc)[RW], T& xr) {
+#pragma unroll
+    for (int q = 0; q < RW; q++) xc[q] = ldx<T>(xb, u.r.col[q]);
+    xr = ldx<T>(xb, u.r.head & 0xFFFFFFu);
+}
+
+// x[row] = (x[row] - sum_q val[q] x[col[q]]) * dinv, the sum formed pairwise
+template <class T, int RW>
+__device__ __forceinline__ T rec_value(const RecU<T, RW>& u, const T (&xc)[RW], T xr) {
     T p[RW];
 #pragma unroll
-    for (int q = 0; q < RW; q++) p[q] = ((uint32_t)q < n) ? u.r.val[q] * ldx<T>(xb, u.r.col[q]) : (T)0;
-    const T xr = ldx<T>(xb, roff);
+    for (int q = 0; q < RW; q++) p[q] = u.r.val[q] * xc[q];
 #pragma unroll
     for (int w = 1; w < RW; w *= 2)
 #pragma unroll
         for (int q = 0; q + w < RW; q += 2 * w) p[q] += p[q + w];
-    *reinterpret_cast<T*>(xb + roff) = (xr - p[0]) * u.r.dinv;
+    return (xr - p[0]) * u.r.dinv;
 }
 
-// Consume the program of subdomain s on x (threads 0..nt-1 of the CTA). Wave by wave each
-// thread takes one row record; the next wave's table entry and record are loaded before
-// the current wave runs, so between two level barriers sit only the working-vector loads
-// and the multiply-add tree. Returns false on a time-out (uniform over the group).
+// One consumer thread's column of a segment: records p, p + stride, ... (nw of them; the
+// first one already in registers).
+// Software-pipelined: the record two ahead is loaded, and the operands of the next row
+// are loaded before the current row's arithmetic; where the next row reads the slot
+// the current row writes, the value is forwarded in registers (the early load predates
+// the store). Every address stays inside the chunk and the working vector: past the
+// end the pipeline reloads the segment's first record.
+template <class T, int RW>
+__device__ __forceinline__ void run_segment(const RecU<T, RW>& first, const uint8_t* p, uint32_t stride, uint32_t nw,
+                                            uint8_t* xb) {
+    RecU<T, RW> a = first, b;
+    T xa[RW], xra;
+    rec_operands(a, xb, xa, xra);
+    if (nw == 1) {  // a single wave: no pipeline
+        if ((a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + (a.r.head & 0xFFFFFFu)) = rec_value(a, xa, xra);
+        return;
+    }
+    rec_load(b, p + (nw > 1 ? stride : 0u));
+    for (uint32_t w = 0; w < nw; w++) {
+        T xn[RW], xrn;
+        rec_operands(b, xb, xn, xrn);
+        RecU<T, RW> c;
+        rec_load(c, p + (w + 2 < nw ? (w + 2) * stride : 0u));
+        const uint32_t ha = a.r.head;
+        const T v = rec_value(a, xa, xra);
+        const bool real = (ha & kRecSkip) == 0;
+        const uint32_t fwd = real ? (ha & 0xFFFFFFu) : 0xFFFFFFFFu;
+        if (real) *reinterpret_cast<T*>(xb + (ha & 0xFFFFFFu)) = v;
+#pragma unroll
+        for (int q = 0; q < RW; q++) xa[q] = (b.r.col[q] == fwd) ? v : xn[q];
+        xra = ((b.r.head & 0xFFFFFFu) == fwd) ? v : xrn;
+        a = b;
+        b = c;
+    }
+}
+
+// The refill side of the ring (one thread outside the consumer group): chunk c >= nst
+// goes into stage c % nst once every consumer thread released chunk c - nst. Stops when
+// the consumers abort or a wait runs out, then waits (bounded) until every copy it or
+// ring_start issued has landed, so none is in flight when the block exits.
+template <class T>
+__device__ void ring_produce(const StreamDev<T>& S, int s, const Smem& sm, const RingCfg& cfg,
+                             volatile int* abort_flag) {
+    const int nst = cfg.nst;
+    const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
+    const uint8_t* base = S.blob + (size_t)c0 * S.chunk;
+    int issued = nch < nst ? nch : nst;
+    for (int c = nst; c < nch; c++) {
+        uint64_t* empty = &sm.bars[nst + c % nst];
+        const uint32_t par = (uint32_t)(c / nst - 1) & 1u;
+        bool ok = false;
+        for (uint64_t i = 0; i < cfg.spin && !ok; i++) {
+            ok = mbar_try_wait(empty, par);
+            if (!ok && *abort_flag) break;
+        }
+        if (!ok) {
+            if (!*abort_flag) {
+                atomicOr(cfg.err, kErrTimeout);
+                *abort_flag = 1;
+            }
+            break;
+        }
+        mbar_expect_tx(&sm.bars[c % nst], S.chunk);
+        tma_load_1d(sm.ring + (size_t)(c % nst) * S.chunk, base + (size_t)c * S.chunk, S.chunk, &sm.bars[c % nst]);
+        issued = c + 1;
+    }
+    for (int d = issued - nst < 0 ? 0 : issued - nst; d < issued; d++)
+        mbar_wait(&sm.bars[d % nst], (uint32_t)(d / nst) & 1u, kDrainSpin);
+}
+
+// Run the program of subdomain s on x. Threads 0..nt-1 consume; thread nt refills the
+// ring. The caller passes whole warps: threads 0..nt+31 (the first barrier below counts
+// the consumer warps and the refill warp). Returns false on a time-out (uniform over
+// the consumer group; bit 2 of the device error word is set).
 template <class T, int RW>
 __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const RingCfg& cfg, T* x) {
     constexpr uint32_t RB = sizeof(RowRec<T, RW>);
     __shared__ int abort_flag;
     const int nt = S.nt, tid = threadIdx.x, nst = cfg.nst;
     const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
-    const uint8_t* base = S.blob + (size_t)c0 * S.chunk;
     uint8_t* xb = reinterpret_cast<uint8_t*>(x);
     if (nch == 0) return true;
     if (tid == 0) abort_flag = 0;
-    group_sync(nt);
-    auto acquire = [&](int c) -> bool {
-        if (!mbar_wait(&sm.bars[c % nst], (uint32_t)(c / nst) & 1u, cfg.spin)) abort_flag = 1;
-        group_sync(nt);
-        return abort_flag == 0;
-    };
-    auto release = [&](int c) {
-        group_sync(nt);
-        if (tid == 0 && c + nst < nch) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&sm.bars[c % nst], S.chunk);
-            tma_load_1d(sm.ring + (size_t)(c % nst) * S.chunk, base + (size_t)(c + nst) * S.chunk, S.chunk,
-                        &sm.bars[c % nst]);
-        }
-    };
-    auto fetch = [&](RecU<T, RW>& u, const uint8_t* cb, uint32_t e) {
-        const uint32_t width = (e >> 16) & 0x1FFu;
-        rec_load(u, cb + (e & 0xFFFFu) * 16u + (uint32_t)tid * RB, (uint32_t)tid < width);
-    };
-    int failed_at = -1;
-    int c = 0;
-    const uint8_t* cb = sm.ring;
-    uint32_t nw = 0, w = 0;
-    // one step: prefetch the wave after `cur` into `nxt`, run `cur`; returns false at the end
-    auto step = [&](RecU<T, RW>& cur, uint32_t& ecur, RecU<T, RW>& nxt, uint32_t& enxt) -> bool {
-        const bool sync_after = (ecur & kWaveSync) != 0;
-        const int cur_chunk = c;
-        bool more = true;
-        if (w + 1 < nw) {
-            w++;
-        } else if (c + 1 < nch) {
-            c++;
-            if (!acquire(c)) {
-                failed_at = c;
-                return false;
-            }
-            cb = sm.ring + (size_t)(c % nst) * S.chunk;
-            nw = *reinterpret_cast<const uint32_t*>(cb);
-            w = 0;
-        } else {
-            more = false;
-        }
-        if (more) {
-            enxt = reinterpret_cast<const uint32_t*>(cb + kChunkHdr)[w];
-            fetch(nxt, cb, enxt);
-        }
-        rec_run(cur, xb);
-        if (sync_after) group_sync(nt);
-        if (c != cur_chunk || !more) release(cur_chunk);
-        return more;
-    };
-    RecU<T, RW> a, b;
-    uint32_t ea = 0, eb = 0;
-    if (!acquire(0)) {
-        failed_at = 0;
-    } else {
-        nw = *reinterpret_cast<const uint32_t*>(cb);
-        ea = reinterpret_cast<const uint32_t*>(cb + kChunkHdr)[0];
-        fetch(a, cb, ea);
-        while (step(a, ea, b, eb) && step(b, eb, a, ea)) {
-        }
+    asm volatile("bar.sync 1, %0;" ::"r"(nt + 32) : "memory");  // consumers + the refill warp
+    if (tid >= nt) {
+        if (tid == nt) ring_produce(S, s, sm, cfg, &abort_flag);
+        return true;
     }
-    if (failed_at >= 0) {  // timed out: record it and wait (bounded) for the copies still in flight
-        if (tid == 0) {
-            atomicOr(cfg.err, kErrTimeout);
-            for (int d = failed_at; d < nch && d < failed_at + nst; d++)
-                mbar_wait(&sm.bars[d % nst], (uint32_t)(d / nst) & 1u, kDrainSpin);
+    for (int c = 0; c < nch; c++) {
+        const bool got = mbar_wait(&sm.bars[c % nst], (uint32_t)(c / nst) & 1u, cfg.spin);
+        if (!group_all(got, nt)) {
+            if (tid == 0) {
+                atomicOr(cfg.err, kErrTimeout);
+                *(volatile int*)&abort_flag = 1;
+            }
+            return false;
         }
-        return false;
+        const uint8_t* cb = sm.ring + (size_t)(c % nst) * S.chunk;
+        const uint32_t nseg = *reinterpret_cast<const uint32_t*>(cb);
+        const uint2* tab = reinterpret_cast<const uint2*>(cb + kChunkHdr);
+        // Lookahead: while segment g runs, the table entry of g + 2 and the first record of
+        // g + 1 are in flight, so a level costs its operand loads, arithmetic and barrier.
+        // (Every chunk holds at least one segment; reads past the table's end re-read it.)
+        auto first_of = [&](uint2 e) { return cb + (e.x & 0xFFFFu) * 16u + (uint32_t)tid * RB; };
+        auto mine = [&](uint2 e) { return (uint32_t)tid < ((e.x >> 16) & 0x1FFu); };
+        uint2 e = tab[0];
+        uint2 en = tab[nseg > 1 ? 1 : 0];
+        RecU<T, RW> r;
+        if (mine(e)) rec_load(r, first_of(e));
+        for (uint32_t g = 0; g < nseg; g++) {
+            const uint2 enn = tab[g + 2 < nseg ? g + 2 : 0];
+            RecU<T, RW> rn;
+            if (g + 1 < nseg && mine(en)) rec_load(rn, first_of(en));
+            if (mine(e)) run_segment<T, RW>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+            if (e.y & kSegBarrier) group_sync(nt);
+            e = en;
+            en = enn;
+            r = rn;
+        }
+        mbar_arrive(&sm.bars[nst + c % nst]);
     }
     return true;
 }
@@ -308,7 +368,7 @@ __global__ void __launch_bounds__(256) k_bj_s(SubDev sd, StreamDev<T> S, RingCfg
     T* x = xvec<T, XS>(sm, xg, q0);
     gather(x, r, sd.q_orig + q0, ns);
     __syncthreads();
-    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
     scatter(z, x, sd.q_orig + q0, ns);
 }
@@ -326,7 +386,7 @@ __global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCf
     T* x = xvec<T, XS>(sm, xg, q0);
     gather(x, r, sd.q_orig + q0, ns);
     __syncthreads();
-    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
     for (int l = threadIdx.x; l < ni; l += blockDim.x) fq[q0 + l] = x[l];
     const int g0 = sd.if_ptr[s];
@@ -354,8 +414,7 @@ __global__ void k_coff(SubDev sd, InnerDev<T> in, int j, T* __restrict__ t, cons
     const InnerCtl* ctl = in.ctl;
     if (*((volatile const int32_t*)&ctl->steps) >= 0 || *((volatile const int32_t*)&ctl->zero)) return;
     const int p = sd.p;
-    double nrm2 = 0.0;
-    for (int u = 0; u < p; u++) nrm2 += __ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p + u);
+    const double nrm2 = warp_allsum_ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p, p);
     if (nrm2 == 0.0) return;
     const T inv = (T)(1.0 / sqrt(nrm2));
     const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
@@ -375,9 +434,7 @@ __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, Ri
     if (*((volatile int32_t*)&ctl->steps) >= 0 || *((volatile int32_t*)&ctl->zero)) return;
     const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
-    double nrm2 = 0.0;
-    for (int u = 0; u < p; u++) nrm2 += __ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p + u);
-    const double nrm = sqrt(nrm2);
+    const double nrm = sqrt(warp_allsum_ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p, p));
     if (j == 0) {
         if (s == 0 && threadIdx.x == 0) ctl->beta = nrm;
         if (nrm == 0.0) {
@@ -401,7 +458,7 @@ __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, Ri
     T* x = xvec<T, XS>(sm, xg + ni, q0);
     for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = t[g0 + i];
     __syncthreads();
-    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
     T* Vj = in.V + (size_t)j * n2;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -453,7 +510,7 @@ __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCf
         x[ni + i] = y;
     }
     __syncthreads();
-    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
     scatter(z, x, sd.q_orig + q0, ns);
 }
@@ -471,7 +528,7 @@ __global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S
     const int g0 = sd.if_ptr[s];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = (T)gp[g0 + i];
     __syncthreads();
-    if ((int)threadIdx.x < S.nt) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
     double acc = 0.0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -517,9 +574,12 @@ static StreamDev<T> sdev(const Handle& h, int id) {
     return d;
 }
 
+// full[nst] and empty[nst] mbarriers fill the 128-byte barrier block
+constexpr int kMaxStages = 8;
+
 static RingCfg rcfg(const Handle& h) {
     RingCfg c;
-    c.nst = h.nst;
+    c.nst = h.nst < kMaxStages ? h.nst : kMaxStages;
     c.smem_len = h.smem_len_stream;
     c.spin = h.o.spin_limit ? h.o.spin_limit : (1ull << 22);
     c.err = h.d_err;

@@ -319,13 +319,13 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     // a whole wave (one record per consumer thread) must fit one chunk
     const int nt_fit = (int)(((chunk - kChunkHdr - 16) / RL.bytes) / 32 * 32);
     if (nt_fit < 32 || chunk > (1u << 20)) return false;
-    S.nt = std::min(S.nt, nt_fit);
+    S.nt = std::min(S.nt, std::min(nt_fit, kMaxConsumers));
     const uint32_t nt = (uint32_t)S.nt;
     auto put = [&](size_t off, uint32_t v, int bytes) {
         for (int b = 0; b < bytes; b++) S.blob[off + b] = (uint8_t)(v >> (8 * b));
     };
     struct Piece {
-        int32_t k;      // packed row
+        int32_t k;      // packed row (-1: skip record, a hole in a merged wave)
         int32_t q0, n;  // entries [q0, q0+n) of the row
         bool last;      // applies the pivot inverse
     };
@@ -333,14 +333,56 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
         size_t p0, p1;  // pieces
         bool sync;
     };
+    // Barrier elimination. A sub-level joins the current barrier-free stretch (no group
+    // barrier before it) when each of its pieces can run on one consumer thread that
+    // already holds, within the stretch, everything the piece touches -- the writer of
+    // every value it reads (its columns and its own slot), and every earlier reader of
+    // the slot it overwrites -- and no two pieces need the same thread. Program order on
+    // that thread then replaces the barrier; pieces touching nothing written or read in
+    // the stretch go to idle threads. Each piece sits at its thread's position in the
+    // wave, skip records filling the holes. Chains -- runs of rows each depending on the
+    // previous one, as along a subdomain's interface -- thus run as one thread's sequence
+    // instead of one barrier per row. Otherwise the previous wave ends with a barrier and
+    // the sub-level starts a new stretch, its pieces spread over the threads in order.
+    int32_t maxpos = 0;
+    for (int32_t r : P.prow) maxpos = std::max(maxpos, r);
+    for (int32_t c : P.pcol) maxpos = std::max(maxpos, c);
+    // per slot, within the current stretch: writer thread, reader thread (-2: several)
+    std::vector<int32_t> wep((size_t)maxpos + 1, -1), wth((size_t)maxpos + 1, -1);
+    std::vector<int32_t> rep((size_t)maxpos + 1, -1), rth((size_t)maxpos + 1, -1);
+    std::vector<int32_t> used(nt), assign;
+    int32_t epoch = 0;
     std::vector<Piece> pieces;
     std::vector<Wave> waves;
     std::vector<Piece> sub;
     int64_t nchunks = 0;
+    S.waves = 0;
+    S.segments = 0;
+    S.records = 0;
+    S.skips = 0;
+    S.max_barriers = 0;
+    S.max_levels_sub = 0;
+    auto mark = [&](const Piece& pc, int32_t t) {
+        auto rd = [&](int32_t pos) {
+            if (rep[pos] != epoch) {
+                rep[pos] = epoch;
+                rth[pos] = t;
+            } else if (rth[pos] != t) {
+                rth[pos] = -2;
+            }
+        };
+        for (int32_t q = 0; q < pc.n; q++) rd(P.pcol[P.pptr[pc.k] + pc.q0 + q]);
+        const int32_t w = P.prow[pc.k];
+        rd(w);
+        wep[w] = epoch;
+        wth[w] = t;
+    };
     for (int32_t s = 0; s < p; s++) {
         // pieces and waves of this subdomain, in program order
         pieces.clear();
         waves.clear();
+        epoch++;
+        S.max_levels_sub = std::max<int64_t>(S.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
         for (int32_t e = P.sub_lvl[s]; e < P.sub_lvl[s + 1]; e++) {
             const int32_t k0 = P.lvl_ptr[e], k1 = P.lvl_ptr[e + 1];
             int32_t np = 1;
@@ -352,49 +394,147 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
                     const int32_t npk = std::max(1, (n + RW - 1) / RW);
                     if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1});
                 }
-                for (size_t t = 0; t < sub.size(); t += nt) {
-                    const size_t t1 = std::min(sub.size(), t + nt);
-                    waves.push_back({pieces.size() + t, pieces.size() + t1, t1 == sub.size()});
+                bool merge = !waves.empty() && sub.size() <= nt;
+                if (merge) {
+                    std::fill(used.begin(), used.end(), -1);
+                    assign.assign(sub.size(), -1);
+                    for (size_t i = 0; i < sub.size() && merge; i++) {
+                        const Piece& pc = sub[i];
+                        int32_t t = -1;
+                        auto need = [&](int32_t u) {
+                            if (u == -2 || (t >= 0 && t != u)) merge = false;
+                            t = u;
+                        };
+                        for (int32_t q = 0; q < pc.n; q++) {
+                            const int32_t c = P.pcol[P.pptr[pc.k] + pc.q0 + q];
+                            if (wep[c] == epoch) need(wth[c]);
+                        }
+                        const int32_t w = P.prow[pc.k];
+                        if (wep[w] == epoch) need(wth[w]);
+                        if (rep[w] == epoch) need(rth[w]);
+                        if (!merge) break;
+                        if (t >= 0) {
+                            if (used[t] >= 0) {
+                                merge = false;
+                                break;
+                            }
+                            used[t] = (int32_t)i;
+                            assign[i] = t;
+                        }
+                    }
+                    if (merge) {  // free pieces onto the lowest idle threads
+                        uint32_t t = 0;
+                        for (size_t i = 0; i < sub.size(); i++) {
+                            if (assign[i] >= 0) continue;
+                            while (used[t] >= 0) t++;
+                            used[t] = (int32_t)i;
+                            assign[i] = (int32_t)t;
+                        }
+                    }
                 }
-                pieces.insert(pieces.end(), sub.begin(), sub.end());
+                if (merge) {
+                    uint32_t width = 0;
+                    for (int32_t a : assign) width = std::max(width, (uint32_t)a + 1);
+                    const size_t p0 = pieces.size();
+                    for (uint32_t t = 0; t < width; t++) {
+                        if (used[t] >= 0) {
+                            const Piece& pc = sub[(size_t)used[t]];
+                            pieces.push_back(pc);
+                            mark(pc, (int32_t)t);
+                        } else {
+                            pieces.push_back({-1, 0, 0, false});
+                        }
+                    }
+                    waves.push_back({p0, pieces.size(), false});
+                } else {
+                    if (!waves.empty()) waves.back().sync = true;
+                    epoch++;
+                    for (size_t t = 0; t < sub.size(); t += nt) {
+                        const size_t t1 = std::min(sub.size(), t + nt);
+                        waves.push_back({pieces.size() + t, pieces.size() + t1, false});
+                    }
+                    for (size_t i = 0; i < sub.size(); i++) mark(sub[i], (int32_t)(i % nt));
+                    pieces.insert(pieces.end(), sub.begin(), sub.end());
+                }
             }
         }
+        if (!waves.empty()) waves.back().sync = true;
+        int64_t barriers = 0;
+        for (const Wave& W : waves) barriers += W.sync;
+        S.max_barriers = std::max(S.max_barriers, barriers);
+        S.waves += (int64_t)waves.size();
+        // Pack the waves into chunks as segments: runs of consecutive waves of one width
+        // (a narrower wave joins when the padding at most doubles it), never crossing a
+        // barrier or a chunk.
+        struct Seg {
+            size_t w0, w1;
+            uint32_t width;
+            bool barrier;
+        };
+        std::vector<Seg> segs;
         size_t wi = 0;
         while (wi < waves.size()) {
-            // as many waves as fit: header + table (4 B per wave, padded) + records
-            size_t nw = 0, recs = 0;
-            while (wi + nw < waves.size()) {
-                const size_t r = waves[wi + nw].p1 - waves[wi + nw].p0;
-                const size_t need = kChunkHdr + al((uint32_t)(4 * (nw + 1)), 16) + (recs + r) * RL.bytes;
-                if (need > chunk) break;
-                nw++;
-                recs += r;
+            segs.clear();
+            size_t recs = 0;
+            auto fits = [&](size_t nseg, size_t nrec) {
+                return kChunkHdr + al((uint32_t)(kSegEntry * nseg), 16) + nrec * RL.bytes <= chunk;
+            };
+            while (wi < waves.size()) {
+                const uint32_t ww = (uint32_t)(waves[wi].p1 - waves[wi].p0);
+                const bool join = !segs.empty() && !segs.back().barrier && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
+                                  (ww == segs.back().width || (ww < segs.back().width && segs.back().width <= 2 * ww));
+                if (join) {
+                    if (!fits(segs.size(), recs + segs.back().width)) break;
+                    segs.back().w1 = wi + 1;
+                    recs += segs.back().width;
+                } else {
+                    if (!fits(segs.size() + 1, recs + ww)) break;
+                    segs.push_back({wi, wi + 1, ww, false});
+                    recs += ww;
+                }
+                if (waves[wi].sync) segs.back().barrier = true;
+                wi++;
             }
+            if (segs.empty()) return false;  // a wave wider than a chunk (excluded by nt_fit)
             const size_t cb = S.blob.size();
             S.blob.resize(cb + chunk, 0);
             nchunks++;
-            put(cb, (uint32_t)nw, 4);
-            size_t roff = kChunkHdr + al((uint32_t)(4 * nw), 16);
-            for (size_t t = 0; t < nw; t++) {
-                const Wave& W = waves[wi + t];
-                const uint32_t width = (uint32_t)(W.p1 - W.p0);
-                put(cb + kChunkHdr + 4 * t, (uint32_t)(roff / 16) | (width << 16) | (W.sync ? kWaveSync : 0u), 4);
-                for (size_t pi = W.p0; pi < W.p1; pi++) {
-                    const Piece& pc = pieces[pi];
-                    const size_t rb = cb + roff;
-                    put(rb, (uint32_t)P.prow[pc.k] * (uint32_t)val_bytes | ((uint32_t)pc.n << 24), 4);
-                    S.doff.push_back((int64_t)(rb + RL.dinv));
-                    S.dsrc.push_back(pc.last ? P.pdsrc[pc.k] : -1);  // -1: the pack writes 1
-                    for (int32_t q = 0; q < pc.n; q++) {
-                        const int32_t src = P.pptr[pc.k] + pc.q0 + q;
-                        put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
-                        S.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
-                        S.vsrc.push_back(P.psrc[src]);
+            S.segments += (int64_t)segs.size();
+            put(cb, (uint32_t)segs.size(), 4);
+            size_t roff = kChunkHdr + al((uint32_t)(kSegEntry * segs.size()), 16);
+            for (size_t g = 0; g < segs.size(); g++) {
+                const Seg& G = segs[g];
+                put(cb + kChunkHdr + kSegEntry * g, (uint32_t)(roff / 16) | (G.width << 16), 4);
+                put(cb + kChunkHdr + kSegEntry * g + 4, (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u), 4);
+                for (size_t w = G.w0; w < G.w1; w++) {
+                    const Wave& W = waves[w];
+                    for (uint32_t t = 0; t < G.width; t++) {
+                        const size_t rb = cb + roff;
+                        roff += RL.bytes;
+                        S.records++;
+                        const Piece* pc = (W.p0 + t < W.p1) ? &pieces[W.p0 + t] : nullptr;
+                        if (!pc || pc->k < 0) {  // skip record: reads slot 0, stores nothing
+                            S.skips++;
+                            put(rb, kRecSkip, 4);
+                            continue;
+                        }
+                        const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)val_bytes;
+                        put(rb, row_off | ((uint32_t)pc->n << 24), 4);
+                        S.doff.push_back((int64_t)(rb + RL.dinv));
+                        S.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
+                        for (int32_t q = 0; q < RW; q++) {
+                            if (q >= pc->n) {  // unused entry: the row's own slot times a zero value
+                                put(rb + RL.col + (size_t)q * 4, row_off, 4);
+                                continue;
+                            }
+                            const int32_t src = P.pptr[pc->k] + pc->q0 + q;
+                            put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
+                            S.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
+                            S.vsrc.push_back(P.psrc[src]);
+                        }
                     }
-                    roff += RL.bytes;
                 }
             }
-            wi += nw;
         }
         S.ch0.push_back((int32_t)nchunks);
     }
@@ -723,19 +863,36 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         if ((int64_t)(h.max_ns + 1) * (h.prec == ILU_PREC_FP32 ? 4 : 8) >= (1 << 24)) h.stream_path = false;
         const int vb = (h.prec == ILU_PREC_FP32) ? 4 : 8;
         std::vector<int> ids = schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD} : std::vector<int>{PR_BJ};
-        // consumer group: one warp unless the levels are wide (rows + entries per level)
+        // consumer group: enough warps for nine levels in ten to run as a single wave
+        // (a wave costs about one row's latency whatever its width), at most 128 threads
         for (int id : ids) {
             const ProgHost& P = h.prog[id];
-            const double lv = (double)std::max<size_t>(P.lvl_ptr.size() - 1, 1);
-            const double work = (double)(P.prow.size() + P.pcol.size()) / lv;
-            int nt = work < 96 ? 32 : (work < 320 ? 64 : 128);
-            if (h.o.block_threads) nt = std::min(256, std::max(32, (int)h.o.block_threads));
-            h.sh[id].nt = nt;
+            std::vector<int32_t> wid;
+            for (size_t e = 0; e + 1 < P.lvl_ptr.size(); e++) wid.push_back(P.lvl_ptr[e + 1] - P.lvl_ptr[e]);
+            int32_t w90 = 1;
+            if (!wid.empty()) {
+                std::nth_element(wid.begin(), wid.begin() + (wid.size() * 9) / 10, wid.end());
+                w90 = wid[(wid.size() * 9) / 10];
+            }
+            int nt = std::min(128, std::max(32, (w90 + 31) / 32 * 32));
+            if (h.o.block_threads) nt = std::max(32, (int)h.o.block_threads);
+            h.sh[id].nt = std::min(nt, kMaxConsumers);
         }
+        // Ring: four stages (enough to hide the copy latency) of the largest chunk that
+        // leaves every subdomain's working vector in shared memory; a chunk boundary
+        // costs a few hundred cycles, so fewer, larger chunks are faster. When the vector
+        // cannot stay in shared memory anyway, the largest chunk.
+        const int64_t room = (int64_t)h.smem_optin - 20 * 1024 - 128;
+        const int64_t xbytes = (int64_t)(h.max_ns + 1) * vb;
+        h.nst = 4;
+        h.chunk = 32768;
+        for (uint32_t c : {32768u, 16384u, 8192u})
+            if (h.nst * (int64_t)c + xbytes <= room) {
+                h.chunk = c;
+                break;
+            }
         bool ok = true;
-        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, 8192, h.sh[id]);
-        h.chunk = 8192;
-        h.nst = 8;
+        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, h.chunk, h.sh[id]);
         if (!ok) h.stream_path = false;
     }
     return ILU_OK;

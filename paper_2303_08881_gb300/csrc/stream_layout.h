@@ -3,31 +3,42 @@
 //
 // A program for one subdomain is a run of fixed-size chunks (one TMA bulk copy fills one
 // shared-memory ring stage with one chunk). A chunk holds
-//   a 16-byte header {uint32 nwaves},
-//   a wave table of nwaves uint32 entries (padded to 16 bytes):
-//       bits 0..15  offset of the wave's first record, in 16-byte units from the chunk
-//       bits 16..24 width: records in the wave (<= the consumer group's thread count)
-//       bit  25     synchronise the consumer group after this wave (end of a level)
-//   the row records of every wave, contiguous per wave.
-// A wave holds rows of ONE level, at most one per consumer thread; a level wider than
-// the group spans several consecutive waves and only its last wave carries the bit.
+//   a 16-byte header {uint32 nseg},
+//   a segment table of nseg 8-byte entries (padded to 16 bytes):
+//       word 0: bits 0..15  offset of the segment's first record, in 16-byte units
+//               bits 16..24 width: records per wave (<= the consumer group's threads)
+//       word 1: bits 0..15  waves in the segment
+//               bit  31     synchronise the consumer group after the segment
+//   the records of every segment, wave after wave, each wave `width` records.
+// Consumer thread t runs record t of every wave of a segment, in wave order; threads
+// synchronise only where a segment carries the barrier bit. Within the rows between two
+// barriers no thread reads or overwrites a slot another thread writes or reads there
+// (the builder arranges this; a thread's own program order covers everything else).
 //
 // A row record (16-byte aligned, read with 128-bit shared-memory loads) holds
-//   uint32 head      byte offset of x[row] in the working vector | (n << 24), n <= RW
+//   uint32 head      byte offset of x[row] | (n << 24); bit 31 marks a skip record
 //   T      dinv      1 / u_ii for an upper-triangular row, 1 for a unit-lower row
-//   uint32 col[RW]   byte offsets of x[col] (entries n.. unused)
-//   T      val[RW]
-// and computes x[row] = (x[row] - sum_{q<n} val[q] * x[col[q]]) * dinv. Offsets are
-// pre-scaled by the element size so the consumer adds them to the vector's base.
+//   uint32 col[RW]   byte offsets of x[col]; entries n.. hold the row's own offset
+//   T      val[RW]   entries n.. hold zero
+// and computes x[row] = (x[row] - sum_{q<RW} val[q] * x[col[q]]) * dinv, the sum formed
+// pairwise. The padded entries add exact zeros, so every record takes the same
+// branch-free path. A skip record (a hole in a wave) reads slot 0 and stores nothing.
+// Offsets are pre-scaled by the element size so the consumer adds them to the vector's
+// base.
 #pragma once
 
 #include <stdint.h>
 
 namespace ilu2l {
 
-constexpr uint32_t kWaveSync = 1u << 25;
 constexpr int kChunkHdr = 16;
-
+constexpr int kSegEntry = 8;
+constexpr uint32_t kSegBarrier = 1u << 31;
+constexpr uint32_t kSegMaxWaves = 0xFFFF;
+constexpr uint32_t kRecSkip = 1u << 31;
+// consumer threads of a stream kernel (its block has 256: one more warp hosts the
+// thread that refills the ring)
+constexpr int kMaxConsumers = 224;
 
 #ifdef __CUDACC__
 #define ILU2L_HD __host__ __device__ __forceinline__

@@ -191,6 +191,37 @@ def test_inner_solve_fp64(ilu, name, k, path):
     h.close()
 
 
+@pytest.mark.parametrize("side,prec", [(155, "fp64"), (215, "fp32"), (260, "fp32")])
+def test_streamed_apply_with_global_working_vector(ilu, side, prec):
+    """One subdomain too large for its working vector to sit in shared memory beside the
+    ring: the streamed kernels keep it in the global scratch vector. 155^2 (FP64) and
+    215^2 (FP32) lie where the generic kernels would still fit it in shared memory, so
+    the scratch vector must be sized for the streamed kernels' own limit."""
+    pr = P.aniso2d_boxes(side, 1, seed=21)
+    cfg = dict(variant="schur", factor_B="ilu0", factor_S="milu0")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, **cfg))
+    orc = O.Oracle.from_problem(pr, **cfg)
+    st = h.stream_stats("fwd")
+    assert h.stats()["stream_path"] and st["vector_in_shared"] == 0
+    r = np.random.default_rng(12).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    got, ref = z.cpu().numpy(), orc.apply(r)
+    assert h.stats()["device_error"] == 0
+    if prec == "fp64":
+        _assert_close64(got, ref, f"apply {side}")
+    else:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL32
+    h.close()
+
+
+def test_working_vector_in_shared_memory_for_the_2d_boxes(ilu):
+    pr, h, orc = _pair(ilu, "aniso2d_ragged", CONFIGS[2], "fp32")
+    assert h.stream_stats("fwd")["vector_in_shared"] == 1
+    h.close()
+
+
 def test_apply_of_zero_is_zero(ilu):
     pr, h, orc = _pair(ilu, "aniso2d_ragged", CONFIGS[2], "fp32")
     z = torch.full((pr.n,), 7.0, dtype=torch.float64, device="cuda")

@@ -1,0 +1,175 @@
+"""The streamed level programs as the host builds them (no GPU): an independent parser
+of the chunk format checks that every barrier-free stretch is race-free and that the
+records cover the program.
+
+Within a stretch the consumer threads run without synchronising, so a record on thread
+t may read a slot only if no other thread wrote it in the stretch, and may overwrite a
+slot only if no other thread read or wrote it there. The check reads the raw chunks;
+only the segment barrier bit separates stretches (chunk boundaries do not synchronise
+the consumer group). A replay with hashed values then runs every stretch thread by
+thread in two opposite thread orders and compares with the plain wave order (the
+level-by-level semantics of Sec. 3.1)."""
+import struct
+
+import numpy as np
+import pytest
+
+from paper_2303_08881_gb300 import problems as P
+
+CASES = {
+    "poisson64": lambda: P.make_config("1"),
+    "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
+    "aniso2d_128box": lambda: P.aniso2d_boxes(256, 2, seed=7),
+    "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
+    "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
+    "rand": lambda: P.randsparse(3000, 8, mean_k=4.0, seed=4),
+    "p1": lambda: P.aniso2d_boxes(30, 1, seed=5),
+    "dense_rows": lambda: P.randsparse(1500, 2, mean_k=24.0, seed=6),
+}
+CFGS = [
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0"),
+    dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
+]
+SKIP = 1 << 31
+BARRIER = 1 << 31
+
+
+@pytest.fixture(scope="module")
+def ilu():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as m
+    return m
+
+
+def _al(x, a):
+    return (x + a - 1) // a * a
+
+
+def parse(st):
+    """Per subdomain: a list of stretches (the rows between two barriers); a stretch is a
+    list of waves; a wave is a list of (thread, write_slot, [read slots]) with skip
+    records left out. Checks the geometry and the padding of every record."""
+    blob, ch0, chunk, rw, vb = st["blob"].tobytes(), st["ch0"], st["chunk"], st["rw"], st["val_bytes"]
+    col_off = 2 * vb
+    rec_bytes = _al(_al(2 * vb + 4 * rw, vb) + rw * vb, 16)
+    subs = []
+    for s in range(len(ch0) - 1):
+        stretches, cur = [], []
+        for c in range(ch0[s], ch0[s + 1]):
+            cb = c * chunk
+            nseg = struct.unpack_from("<I", blob, cb)[0]
+            end = 16 + _al(8 * nseg, 16)
+            for g in range(nseg):
+                w0, w1 = struct.unpack_from("<II", blob, cb + 16 + 8 * g)
+                off, width, nw = (w0 & 0xFFFF) * 16, (w0 >> 16) & 0x1FF, w1 & 0xFFFF
+                assert off >= end and off + nw * width * rec_bytes <= chunk and 1 <= width <= st["threads"]
+                end = off + nw * width * rec_bytes
+                for w in range(nw):
+                    wave = []
+                    for t in range(width):
+                        rb = cb + off + (w * width + t) * rec_bytes
+                        head = struct.unpack_from("<I", blob, rb)[0]
+                        cols = struct.unpack_from(f"<{rw}I", blob, rb + col_off)
+                        if head & SKIP:
+                            assert head == SKIP and not any(cols)
+                            continue
+                        n, roff = (head >> 24) & 0x7F, head & 0xFFFFFF
+                        assert n <= rw and roff % vb == 0 and all(x % vb == 0 for x in cols)
+                        assert all(x == roff for x in cols[n:]), "unused entries read the row's own slot"
+                        wave.append((t, roff // vb, [x // vb for x in cols[:n]]))
+                    cur.append(wave)
+                if w1 & BARRIER:
+                    stretches.append(cur)
+                    cur = []
+        if cur:
+            stretches.append(cur)
+        subs.append(stretches)
+    return subs
+
+
+def hazards(stretches):
+    bad = 0
+    for stretch in stretches:
+        writer, readers = {}, {}
+        for wave in stretch:
+            for t, w, cols in wave:
+                for c in list(cols) + [w]:
+                    if writer.get(c, t) != t:
+                        bad += 1
+                    readers.setdefault(c, set()).add(t)
+                if writer.get(w, t) != t or readers[w] - {t}:
+                    bad += 1
+                writer[w] = t
+    return bad
+
+
+def replay(stretches, order):
+    x = {}
+    rid = 0
+    for stretch in stretches:
+        recs = []
+        for wi, wave in enumerate(stretch):
+            for t, w, cols in wave:
+                recs.append((t, wi, w, cols, rid))
+                rid += 1
+        if order == "wave":
+            seq = recs
+        else:
+            key = (lambda r: (r[0], r[1])) if order == "up" else (lambda r: (-r[0], r[1]))
+            seq = sorted(recs, key=key)
+        for t, wi, w, cols, r in seq:
+            x[w] = hash((x.get(w, ("in", w)), tuple(x.get(c, ("in", c)) for c in cols), r))
+    return x
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: "-".join(map(str, c.values())))
+def test_stretches_are_race_free(ilu, name, cfg):
+    pr = CASES[name]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **cfg))
+    sizes = h.sizes()
+    progs = ["bj"] if cfg["variant"] == "bj" else ["fwd", "s", "bwd"]
+    for prog in progs:
+        st = h.stream(prog)
+        subs = parse(st)
+        stats = h.stream_stats(prog)
+        assert stats["threads"] == st["threads"]
+        n_rec = sum(len(w) for stretches in subs for s in stretches for w in s)
+        n_ent = sum(len(r[2]) for stretches in subs for s in stretches for w in s for r in w)
+        assert n_rec == stats["records"] - stats["skips"]
+        if prog != "fwd":  # the forward stream also holds the S~ rows
+            assert n_rec >= sizes[f"prog_{prog}"]["rows"]
+            assert n_ent == sizes[f"prog_{prog}"]["entries"]
+        assert max(len(s) for s in subs) - 1 <= stats["max_barriers"]
+        assert stats["max_barriers"] <= stats["max_levels"] * (1 + (st["rw"] < 16))
+        for s, stretches in enumerate(subs):
+            assert hazards(stretches) == 0, (prog, s)
+            ref = replay(stretches, "wave")
+            assert replay(stretches, "up") == ref and replay(stretches, "down") == ref, (prog, s)
+    h.close()
+
+
+def test_interface_chains_run_without_barriers(ilu):
+    """On 128 x 128 boxes of the 9-point problem the interface of a subdomain is a ring
+    walked as a few chains; the local Schur program keeps only a handful of barriers
+    where a plain level schedule needs one per level."""
+    pr = P.aniso2d_boxes(256, 2, seed=0)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
+    st = h.stream_stats("s")
+    assert st["max_levels"] > 250
+    assert st["max_barriers"] <= 8
+    h.close()
+
+
+def test_planted_race_is_detected():
+    """the checker itself: two threads touching one slot inside a stretch"""
+    raw = [[[(0, 5, [1]), (1, 6, [2])], [(1, 7, [5])]]]  # thread 1 reads slot 5 of thread 0
+    assert hazards(raw) == 1
+    ok = [[[(0, 5, [1]), (1, 6, [2])]], [[(1, 7, [5])]]]  # a barrier in between
+    assert hazards(ok) == 0
+    war = [[[(0, 5, [3])], [(1, 3, [])]]]  # thread 1 overwrites what thread 0 read
+    assert hazards(war) == 1
+    a, b = replay(raw, "up"), replay(raw, "down")
+    assert a != b or replay(raw, "wave") != a
