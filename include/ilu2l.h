@@ -76,8 +76,12 @@ typedef struct {
     int32_t analysis_only;/* 1: host analysis only (no device memory, no factorisation);
                              only ilu_get_sizes / _perm / _levels and ilu_free are valid */
     int32_t kernel_path;  /* 0: level programs streamed into shared memory by TMA (falls
-                             back to 1 when a row does not fit a 64 KB chunk);
+                             back to 1 when a row does not fit a chunk);
                              1: generic level kernels reading the programs from global memory */
+    int32_t inner_launch; /* streamed path, inner Schur GMRES of the apply: 0 = one
+                             cooperative launch for all inner steps when every subdomain's CTA
+                             can be resident at once (else as 1; default), 1 = four launches
+                             per inner step */
 } ilu_opts;
 
 typedef struct {
@@ -188,7 +192,8 @@ ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* la
    device wait timed out; synchronises the stream to read it), out[5] = 1 when the apply
    runs the TMA-streamed level programs, out[6..13] = (entries per row record, consumer
    threads) of the streamed programs block Jacobi, forward, local Schur, backward (0 if
-   unused). out must hold 14 values. */
+   unused), out[14] = 1 when the apply runs the inner Schur GMRES as one cooperative
+   launch. out must hold 15 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
 /* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device

@@ -45,7 +45,7 @@ class ilu_opts(C.Structure):
                 ("inner_iters", C.c_int32), ("pc_precision", C.c_int32), ("ordering", C.c_int32),
                 ("pivot_eps", C.c_double), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
-                ("analysis_only", C.c_int32), ("kernel_path", C.c_int32)]
+                ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -131,6 +131,7 @@ class Opts:
     spin_limit: int = 0
     analysis_only: bool = False
     kernel_path: str = "stream"     # "stream" (TMA-streamed level programs) or "generic"
+    inner_launch: str = "single"    # inner Schur GMRES: "single" cooperative launch or "per_step"
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -149,6 +150,7 @@ class Opts:
         o.spin_limit = int(self.spin_limit)
         o.analysis_only = int(bool(self.analysis_only))
         o.kernel_path = {"stream": 0, "generic": 1}[self.kernel_path]
+        o.inner_launch = {"single": 0, "per_step": 1}[self.inner_launch]
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:
@@ -229,13 +231,13 @@ class Handle:
         _check(lib().ilu_inner_solve(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve")
 
     def stats(self) -> dict:
-        out = np.zeros(14, np.int64)
+        out = np.zeros(15, np.int64)
         _check(lib().ilu_get_stats(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_stats")
         progs = {name: dict(record_entries=int(out[6 + 2 * i]), threads=int(out[7 + 2 * i]))
                  for i, name in enumerate(["bj", "fwd", "s", "bwd"])}
         return dict(kernel_launches=int(out[0]), graph_launches=int(out[1]),
                     kernels_per_cycle=int(out[2]), row_ctas=int(out[3]), device_error=int(out[4]),
-                    stream_path=bool(out[5]), programs=progs)
+                    stream_path=bool(out[5]), programs=progs, inner_single_launch=bool(out[14]))
 
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,

@@ -95,6 +95,8 @@ ilu_status device_setup_t(Handle& h) {
     cv.shrink_to_fit();
     if (h.stream_path) {
         CK(configure_stream<T>(h, 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * sizeof(T)));
+        if (h.variant == ILU_VARIANT_SCHUR && h.n2 > 0 && h.o.inner_launch == 0)
+            CK(inner_coop_fits<T>(h, &h.inner_coop));
         h.d_tbuf = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
         if (!h.d_tbuf) return map_err(e);
         for (int id = 0; id < PR_COUNT; id++) {
@@ -344,6 +346,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->block_threads = 0;
     o->analysis_only = 0;
     o->kernel_path = 0;
+    o->inner_launch = 0;
 }
 
 const char* ilu_status_str(ilu_status s) {
@@ -392,7 +395,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
-        o.kernel_path < 0 || o.kernel_path > 1) {
+        o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -681,6 +684,7 @@ ilu_status ilu_get_stats(void* hp, int64_t* out) {
         out[4] = e;
     }
     out[5] = h->stream_path ? 1 : 0;
+    out[14] = h->inner_coop ? 1 : 0;
     const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
     for (int i = 0; i < 4; i++) {
         out[6 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].rw;

@@ -45,6 +45,42 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return a[0];
 }
 
+// The same sums in an accumulator type A (float for the FP32 preconditioner: GB300 runs
+// FP64 arithmetic at a small fraction of the FP32 rate). scratch: 32 * NV values of A.
+template <class A>
+__device__ __forceinline__ A warp_sum_t(A v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;  // valid in lane 0
+}
+
+template <class A, int NV>
+__device__ __forceinline__ void block_sum_nt(A (&v)[NV], A* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int u = 0; u < NV; u++) v[u] = warp_sum_t(v[u]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < NV; u++) scratch[warp * NV + u] = v[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+        A s = (A)0;
+        for (int w = 0; w < nw; w++) s += scratch[w * NV + u];
+        v[u] = s;
+    }
+    __syncthreads();
+}
+
+template <class A>
+__device__ __forceinline__ A block_sum_t(A v, A* scratch) {
+    A a[1] = {v};
+    block_sum_nt<A, 1>(a, scratch);
+    return a[0];
+}
+
 // Sum of a[0..m) by one warp: lane l adds a[l], a[l+32], ... in order, then a butterfly
 // (xor) exchange combines the lanes. Both partners of every exchange add the same two
 // values, so all lanes -- and every warp or CTA that calls this on the same data -- end

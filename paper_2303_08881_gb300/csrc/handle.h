@@ -101,6 +101,7 @@ struct Handle {
     int nst = 4;                      // ring stages
     uint32_t chunk = 8192;            // bytes per chunk / ring stage
     int smem_optin = 232448;          // the device's shared memory per block (opt-in)
+    bool inner_coop = false;          // inner solve as one cooperative launch
     int32_t smem_len_stream = 0;      // working-vector capacity with the ring present
     void* d_tbuf = nullptr;           // C_off product of the inner step (interface numbering)
     int32_t *d_num_sub = nullptr, *d_num_lvl = nullptr, *d_num_row = nullptr;

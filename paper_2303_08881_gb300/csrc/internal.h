@@ -62,6 +62,10 @@ struct InnerCtl {
     double H[(kMaxInner + 1) * kMaxInner];    // column-major Hessenberg
     int32_t steps;                            // -1 while running, else the steps taken
     int32_t zero;                             // c == 0
+    // grid barrier of the single-launch inner solve (cleared by the kernel that starts it)
+    uint32_t gbar_count;                      // CTAs arrived at the current barrier
+    uint32_t gbar_gen;                        // barriers completed (wraps)
+    int32_t gbar_abort;                       // a CTA gave up waiting: the others stop too
 };
 
 template <class T>
@@ -160,6 +164,8 @@ cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int3
                          cudaStream_t st);
 template <class T>
 cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st);
+template <class T>
+cudaError_t inner_coop_fits(const Handle& h, bool* fits);
 // inner solve on a caller-provided workspace (allocation-free entry point)
 template <class T>
 cudaError_t launch_inner_bc_ws(const Handle& h, const InnerDev<T>& in, int j, int second, cudaStream_t st);

@@ -81,15 +81,15 @@ __global__ void k_fwd(SubDev sd, ProgDev<T> PF, ProgDev<T> PS, InnerDev<T> in,
     for (int l = threadIdx.x; l < ni; l += blockDim.x) fq[q0 + l] = x[l];
     run_prog(PS, s, x + ni);
     const int g0 = sd.if_ptr[s];
-    double acc = 0.0;
+    T acc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         const T c = x[ni + i];
         in.W0[g0 + i] = c;
-        acc += (double)c * (double)c;
+        acc += c * c;
     }
-    acc = block_sum(acc, red);
+    acc = block_sum_t<T>(acc, reinterpret_cast<T*>(red));
     if (threadIdx.x == 0) {
-        *ipart(in.part, kBankNorm, 0, s, sd.p) = acc;
+        *ipart(in.part, kBankNorm, 0, s, sd.p) = (double)acc;
         if (s == 0) {
             in.ctl->steps = -1;
             in.ctl->zero = 0;
@@ -109,15 +109,15 @@ __global__ void k_inner_start(SubDev sd, ProgDev<T> PS, InnerDev<T> in, const do
     for (int i = threadIdx.x; i < nf; i += blockDim.x) x[ni + i] = (T)gp[g0 + i];
     __syncthreads();
     run_prog(PS, s, x + ni);
-    double acc = 0.0;
+    T acc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         const T c = x[ni + i];
         in.W0[g0 + i] = c;
-        acc += (double)c * (double)c;
+        acc += c * c;
     }
-    acc = block_sum(acc, red);
+    acc = block_sum_t<T>(acc, reinterpret_cast<T*>(red));
     if (threadIdx.x == 0) {
-        *ipart(in.part, kBankNorm, 0, s, sd.p) = acc;
+        *ipart(in.part, kBankNorm, 0, s, sd.p) = (double)acc;
         if (s == 0) {
             in.ctl->steps = -1;
             in.ctl->zero = 0;
@@ -175,18 +175,18 @@ __global__ void k_inner_a(SubDev sd, ProgDev<T> PS, InnerDev<T> in, int j, T* xg
     }
     __syncthreads();
     for (int i0 = 0; i0 <= j; i0 += 8) {
-        double acc[8];
+        T acc[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int u = 0; u < 8; u++) acc[u] = (T)0;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const double w = (double)x[i];
+            const T w = x[i];
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (i0 + u <= j) acc[u] += (double)in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+                if (i0 + u <= j) acc[u] += in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
         }
-        block_sum_n<8>(acc, red);
+        block_sum_nt<T, 8>(acc, reinterpret_cast<T*>(red));
         if (threadIdx.x == 0)
-            for (int u = 0; u < 8 && i0 + u <= j; u++) *ipart(in.part, kBankDot1, i0 + u, s, p) = acc[u];
+            for (int u = 0; u < 8 && i0 + u <= j; u++) *ipart(in.part, kBankDot1, i0 + u, s, p) = (double)acc[u];
     }
 }
 
@@ -217,32 +217,32 @@ __global__ void k_inner_bc(SubDev sd, InnerDev<T> in, int j, int second, const i
     }
     T* __restrict__ W = (j & 1) ? in.W0 : in.W1;
     const int g0 = sd.if_ptr[s];
-    double nacc = 0.0;
+    T nacc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         T w = W[g0 + i];
         for (int t = 0; t <= j; t++) w -= (T)hh[t] * in.V[(size_t)t * n2 + g0 + i];
         W[g0 + i] = w;
-        nacc += (double)w * (double)w;
+        nacc += w * w;
     }
     if (second) {
-        nacc = block_sum(nacc, red);
-        if (threadIdx.x == 0) *ipart(in.part, kBankNorm, 0, s, p) = nacc;
+        nacc = block_sum_t<T>(nacc, reinterpret_cast<T*>(red));
+        if (threadIdx.x == 0) *ipart(in.part, kBankNorm, 0, s, p) = (double)nacc;
         return;
     }
     __syncthreads();
     for (int i0 = 0; i0 <= j; i0 += 8) {
-        double acc[8];
+        T acc[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int u = 0; u < 8; u++) acc[u] = (T)0;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const double w = (double)W[g0 + i];
+            const T w = W[g0 + i];
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (i0 + u <= j) acc[u] += (double)in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+                if (i0 + u <= j) acc[u] += in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
         }
-        block_sum_n<8>(acc, red);
+        block_sum_nt<T, 8>(acc, reinterpret_cast<T*>(red));
         if (threadIdx.x == 0)
-            for (int u = 0; u < 8 && i0 + u <= j; u++) *ipart(in.part, kBankDot2, i0 + u, s, p) = acc[u];
+            for (int u = 0; u < 8 && i0 + u <= j; u++) *ipart(in.part, kBankDot2, i0 + u, s, p) = (double)acc[u];
     }
 }
 

@@ -140,6 +140,24 @@ __device__ __forceinline__ void ring_start(const StreamDev<T>& S, int s, const S
     }
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* b) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// Before a further run of the same program in one kernel (all threads call it): when the
+// whole program stays in the ring no copy is needed (a second pass finds every stage's
+// phase complete); otherwise thread 0 re-initialises the drained barriers and restarts
+// the copies. Every copy of the previous run has landed (ring_produce drains them).
+template <class T>
+__device__ __forceinline__ void ring_rearm(const StreamDev<T>& S, int s, const Smem& sm, int nst) {
+    if (S.ch0[s + 1] - S.ch0[s] <= nst) return;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 2 * nst; i++) mbar_inval(&sm.bars[i]);
+    ring_start(S, s, sm, nst);
+    __syncthreads();
+}
+
 // Row record (stream_layout.h), read with 128-bit shared-memory loads.
 template <class T, int RW>
 struct __align__(16) RowRec {
@@ -390,18 +408,20 @@ __global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCf
     __syncthreads();
     for (int l = threadIdx.x; l < ni; l += blockDim.x) fq[q0 + l] = x[l];
     const int g0 = sd.if_ptr[s];
-    double acc = 0.0;
+    T acc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         const T c = x[ni + i];
         in.W0[g0 + i] = c;
-        acc += (double)c * (double)c;
+        acc += c * c;
     }
-    acc = block_sum(acc, red);
+    acc = block_sum_t<T>(acc, reinterpret_cast<T*>(red));
     if (threadIdx.x == 0) {
-        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = acc;
+        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = (double)acc;
         if (s == 0) {
             in.ctl->steps = -1;
             in.ctl->zero = 0;
+            in.ctl->gbar_count = 0;
+            in.ctl->gbar_abort = 0;
         }
     }
 }
@@ -471,18 +491,187 @@ __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, Ri
     }
     __syncthreads();
     for (int i0 = 0; i0 <= j; i0 += 8) {
-        double acc[8];
+        T acc[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) acc[u] = 0.0;
+        for (int u = 0; u < 8; u++) acc[u] = (T)0;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const double w = (double)x[i];
+            const T w = x[i];
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (i0 + u <= j) acc[u] += (double)in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+                if (i0 + u <= j) acc[u] += in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
         }
-        block_sum_n<8>(acc, red);
+        block_sum_nt<T, 8>(acc, reinterpret_cast<T*>(red));
         if (threadIdx.x == 0)
-            for (int u = 0; u < 8 && i0 + u <= j; u++) in.part[((size_t)(i0 + u)) * p + s] = acc[u];
+            for (int u = 0; u < 8 && i0 + u <= j; u++) in.part[((size_t)(i0 + u)) * p + s] = (double)acc[u];
+    }
+}
+
+// Grid-wide barrier of the single-launch inner solve (a cooperative launch guarantees
+// that every CTA is resident). Thread 0 of each CTA arrives on a counter; the last one
+// resets it and advances the generation the others wait for. Waits are bounded: a CTA
+// that gives up sets bit 2 of the device error word and the abort word, which ends the
+// others' waits too. Returns false (uniform over the CTA) after an abort.
+__device__ bool grid_sync(InnerCtl* ctl, uint32_t nblocks, uint64_t spin, int32_t* err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* gen = &ctl->gbar_gen;
+        volatile int32_t* abort = &ctl->gbar_abort;
+        const uint32_t g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&ctl->gbar_count, 1u) == nblocks - 1) {
+            atomicExch(&ctl->gbar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->gbar_gen, 1u);
+        } else {
+            for (uint64_t i = 0; *gen == g; i++) {
+                if (*abort || i >= spin) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (!ok || *abort) {
+            ok = 0;
+            atomicOr(err, kErrTimeout);
+            *abort = 1;
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// All k steps of the inner GMRES on the preconditioned Schur system (Eq. preSS) in one
+// cooperative launch, one CTA per subdomain, W0 = c = S~^{-1} g' and its norm partials
+// left by the forward kernel. Step j, with three grid barriers:
+//   A: v_j = W_in / ||W_in||; t = C_off v_j on the CTA's interface rows (other CTAs' W_in
+//      read through L2); x = S~_s^{-1} t (the streamed local Schur program); w = v_j + x;
+//      partial dots V_i . w (i <= j)
+//   B: h1 = sum of the partials (every CTA, fixed order); w -= V h1; partial dots again
+//   C: h2 likewise; w -= V h2; partial ||w||^2; w stored for the next step's C_off.
+// The Hessenberg entries go to ctl (CTA 0); k_bwd_s solves the least squares. Every CTA
+// forms each norm from the same partials in the same order, so the stopping decisions
+// (c = 0, breakdown) are uniform and no CTA leaves the barriers early.
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, T* xg,
+                                                    const int32_t* done) {
+    __shared__ double red[32 * 8];
+    __shared__ double hh[kMaxInner + 1];
+    if (done && *done) return;
+    InnerCtl* ctl = in.ctl;
+    const int s = blockIdx.x, p = sd.p, n2 = sd.n2, tid = threadIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const int g0 = sd.if_ptr[s];
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    T* x = xvec<T, XS>(sm, xg + ni, q0);
+    const double* nbank = in.part + ((size_t)2 * (kMaxInner + 1)) * p;
+    double beta = 0.0;
+    for (int j = 0; j < in.k; j++) {
+        // ---- A
+        const double nrm = sqrt(warp_allsum_ldcg(nbank, p));
+        if (j == 0) {
+            beta = nrm;
+            if (s == 0 && tid == 0) ctl->beta = nrm;
+            if (nrm == 0.0) {
+                if (s == 0 && tid == 0) ctl->zero = 1;
+                break;
+            }
+        } else {
+            if (s == 0 && tid == 0) ctl->H[(j - 1) * (kMaxInner + 1) + j] = nrm;
+            if (nrm <= 1e-14 * beta) {  // lucky breakdown: the Krylov space is exhausted
+                if (s == 0 && tid == 0) ctl->steps = j;
+                break;
+            }
+        }
+        const T inv = (T)(1.0 / nrm);
+        const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
+        T* __restrict__ Wout = (j & 1) ? in.W0 : in.W1;
+        // copies start only past the stopping tests: every copy issued is consumed (and
+        // drained) by the ring_run below
+        if (j == 0)
+            ring_start(S, s, sm, cfg.nst);
+        else
+            ring_rearm(S, s, sm, cfg.nst);
+        for (int i = tid; i < nf; i += blockDim.x) {
+            const int gi = g0 + i;
+            const int qa = in.coff_rp[gi], qb = in.coff_rp[gi + 1];
+            T acc = (T)0;
+            for (int q0 = qa; q0 < qb; q0 += 4) {  // four gathers in flight, summed in order
+                T cv[4], wv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const bool ok = q0 + u < qb;
+                    cv[u] = ok ? in.coff_v[q0 + u] : (T)0;
+                    wv[u] = ok ? __ldcg(Win + in.coff_ci[q0 + u]) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc += cv[u] * wv[u];
+            }
+            x[i] = acc * inv;
+        }
+        __syncthreads();
+        if (tid < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+        __syncthreads();
+        T* Vj = in.V + (size_t)j * n2;
+        for (int i = tid; i < nf; i += blockDim.x) {
+            const int gi = g0 + i;
+            const T v = __ldcg(Win + gi) * inv;
+            Vj[gi] = v;
+            x[i] = v + x[i];
+        }
+        __syncthreads();
+        for (int bank = 0; bank < 2; bank++) {
+            // partial dots V_i . w, i <= j, into bank 0 (A) or 1 (B)
+            for (int i0 = 0; i0 <= j; i0 += 8) {
+                T acc[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) acc[u] = (T)0;
+                for (int i = tid; i < nf; i += blockDim.x) {
+                    const T w = x[i];
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        if (i0 + u <= j) acc[u] += in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+                }
+                block_sum_nt<T, 8>(acc, reinterpret_cast<T*>(red));
+                if (tid == 0)
+                    for (int u = 0; u < 8 && i0 + u <= j; u++)
+                        in.part[((size_t)(bank * (kMaxInner + 1) + i0 + u)) * p + s] = (double)acc[u];
+            }
+            if (!grid_sync(ctl, (uint32_t)p, cfg.spin, cfg.err)) return;
+            // ---- B (bank 0) / C (bank 1): coefficients, Hessenberg column, update
+            {
+                const int lane = tid & 31, nw = blockDim.x >> 5;
+                for (int i = tid >> 5; i <= j; i += nw) {
+                    const double h = warp_allsum_ldcg(in.part + ((size_t)(bank * (kMaxInner + 1) + i)) * p, p);
+                    if (lane == 0) hh[i] = h;
+                }
+            }
+            __syncthreads();
+            if (s == 0 && tid == 0)
+                for (int i = 0; i <= j; i++) {
+                    double& H = ctl->H[j * (kMaxInner + 1) + i];
+                    H = bank ? H + hh[i] : hh[i];
+                }
+            T nacc = (T)0;
+            for (int i = tid; i < nf; i += blockDim.x) {
+                T w = x[i];
+                for (int t = 0; t <= j; t++) w -= (T)hh[t] * in.V[(size_t)t * n2 + g0 + i];
+                x[i] = w;
+                if (bank) {
+                    Wout[g0 + i] = w;
+                    nacc += w * w;
+                }
+            }
+            __syncthreads();
+            if (bank) {
+                nacc = block_sum_t<T>(nacc, reinterpret_cast<T*>(red));
+                if (tid == 0) in.part[((size_t)2 * (kMaxInner + 1)) * p + s] = (double)nacc;
+                if (!grid_sync(ctl, (uint32_t)p, cfg.spin, cfg.err)) return;
+            }
+        }
     }
 }
 
@@ -530,18 +719,20 @@ __global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S
     __syncthreads();
     if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
     __syncthreads();
-    double acc = 0.0;
+    T acc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         const T c = x[i];
         in.W0[g0 + i] = c;
-        acc += (double)c * (double)c;
+        acc += c * c;
     }
-    acc = block_sum(acc, red);
+    acc = block_sum_t<T>(acc, reinterpret_cast<T*>(red));
     if (threadIdx.x == 0) {
-        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = acc;
+        in.part[((size_t)2 * (kMaxInner + 1)) * sd.p + s] = (double)acc;
         if (s == 0) {
             in.ctl->steps = -1;
             in.ctl->zero = 0;
+            in.ctl->gbar_count = 0;
+            in.ctl->gbar_abort = 0;
         }
     }
 }
@@ -612,6 +803,7 @@ static cudaError_t configure_stream_t() {
     if (e == cudaSuccess) e = raise_smem_limit(k_inner_a_s<T, RW, XS>);
     if (e == cudaSuccess) e = raise_smem_limit(k_bwd_s<T, RW, XS>);
     if (e == cudaSuccess) e = raise_smem_limit(k_inner_start_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_coop<T, RW, XS>);
     return e;
 }
 
@@ -668,9 +860,42 @@ cudaError_t launch_fwd_s(const Handle& h, const double* r, const int32_t* done, 
     return cudaGetLastError();
 }
 
+// Whether the single-launch inner solve fits: every subdomain's CTA resident at once.
+template <class T>
+cudaError_t inner_coop_fits(const Handle& h, bool* fits) {
+    *fits = false;
+    int dev = 0, coop = 0, nb = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess || !coop) return e;
+    ILU2L_IDX_DISPATCH(h, PR_S, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                     &nb, k_inner_coop<T, RW, XS>, 256, stream_smem(h, sizeof(T)))));
+    if (e == cudaSuccess) *fits = (int64_t)nb * h.sm_count >= h.p;
+    return e;
+}
+
+template <class T>
+static cudaError_t launch_inner_coop(const Handle& h, const int32_t* done, cudaStream_t st) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)h.p);
+    lc.blockDim = dim3(256);
+    lc.dynamicSmemBytes = stream_smem(h, sizeof(T));
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    ILU2L_IDX_DISPATCH(h, PR_S, (e = cudaLaunchKernelEx(&lc, k_inner_coop<T, RW, XS>, h.sub(), sdev<T>(h, PR_S),
+                                                         rcfg(h), h.innerdev<T>(), (T*)h.d_xg, done)));
+    return e;
+}
+
 template <class T>
 cudaError_t launch_inner_s(const Handle& h, const int32_t* done, cudaStream_t st) {
     if (h.n2 == 0) return cudaSuccess;
+    if (h.inner_coop) return launch_inner_coop<T>(h, done, st);
     const int gb = std::max(1, std::min(h.sm_count * 4, (h.n2 + 255) / 256));
     for (int j = 0; j < h.inner_k; j++) {
         k_coff<T><<<gb, 256, 0, st>>>(h.sub(), h.innerdev<T>(), j, (T*)h.d_tbuf, done);
@@ -736,7 +961,8 @@ cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, 
     template cudaError_t launch_inner_s<T>(const Handle&, const int32_t*, cudaStream_t);                   \
     template cudaError_t launch_bwd_s<T>(const Handle&, const double*, double*, const int32_t*,            \
                                          cudaStream_t);                                                    \
-    template cudaError_t launch_inner_start_s<T>(const Handle&, const double*, cudaStream_t);
+    template cudaError_t launch_inner_start_s<T>(const Handle&, const double*, cudaStream_t);             \
+    template cudaError_t inner_coop_fits<T>(const Handle&, bool*);
 ILU2L_SINST(float)
 ILU2L_SINST(double)
 

@@ -191,6 +191,40 @@ def test_inner_solve_fp64(ilu, name, k, path):
     h.close()
 
 
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "cuts3d", "rand", "dense_rows"])
+@pytest.mark.parametrize("cfg", [CONFIGS[2], CONFIGS[5], CONFIGS[6]], ids=_cid)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_inner_launch_modes_agree(ilu, name, cfg, prec, k):
+    """The inner Schur GMRES as one cooperative launch (grid barriers between the
+    Gram-Schmidt phases) and as four launches per step give the oracle's apply."""
+    pr = _prob(name)
+    orc = O.Oracle.from_problem(pr, inner_iters=k, **cfg)
+    r = np.random.default_rng(17).standard_normal(pr.n)
+    ref = orc.apply(r)
+    got = {}
+    for mode in ("single", "per_step"):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_iters=k, inner_launch=mode, **cfg))
+        st = h.stats()
+        if orc.sizes().n2:
+            assert st["inner_single_launch"] == (mode == "single")
+        z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+        ilu.ilu_apply(h, _dev(r), z)
+        ilu.ilu_apply(h, _dev(r), z)  # twice: the cooperative grid barrier state carries over
+        torch.cuda.synchronize()
+        assert h.stats()["device_error"] == 0
+        got[mode] = z.cpu().numpy()
+        h.close()
+    for mode, z in got.items():
+        if prec == "fp64":
+            _assert_close64(z, ref, f"{mode} {name}")
+        else:
+            assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= TOL32, mode
+    scale = np.linalg.norm(ref)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(got["single"] - got["per_step"]) <= tol * scale
+
+
 @pytest.mark.parametrize("side,prec", [(155, "fp64"), (215, "fp32"), (260, "fp32")])
 def test_streamed_apply_with_global_working_vector(ilu, side, prec):
     """One subdomain too large for its working vector to sit in shared memory beside the
@@ -290,9 +324,14 @@ def test_device_wait_timeout_is_reported(ilu):
         ilu.ilu_apply(h, r, z)
     st = h.stats()
     assert st["stream_path"] and st["device_error"] in (0, 2)
+    if st["inner_single_launch"]:  # its grid barriers cannot pass with a single poll
+        assert st["device_error"] == 2
     x = torch.zeros_like(r)
-    info = ilu.gmres_solve(h, r, x, rtol=1e-8, restart=10, maxit=50)
-    assert info["status"] in (0, ilu.ILU_ERR_TIMEOUT, ilu.ILU_ERR_NOT_CONVERGED)
+    try:
+        info = ilu.gmres_solve(h, r, x, rtol=1e-8, restart=10, maxit=50)
+        assert info["status"] in (0, ilu.ILU_ERR_NOT_CONVERGED)
+    except ilu.IluError as e:
+        assert e.status == ilu.ILU_ERR_TIMEOUT
     h.close()
     # a fresh handle on the same device still works
     pr2, h2, orc = _pair(ilu, "poisson64", CONFIGS[0], "fp64")
