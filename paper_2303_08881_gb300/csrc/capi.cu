@@ -197,9 +197,10 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     h.fg_threads = 256;
     CK(configure_krylov());
     FgDev f{};
-    f.V = h.alloc<double>((size_t)(m + 1) * n, &e);
-    f.Z = h.alloc<double>((size_t)m * n, &e);
-    f.w = h.alloc<double>(n, &e);
+    f.ld = (int64_t)((n + 63) / 64 * 64);
+    f.V = h.alloc<double>((size_t)(m + 1) * (size_t)f.ld, &e);
+    f.Z = h.alloc<double>((size_t)m * (size_t)f.ld, &e);
+    f.w = h.alloc<double>((size_t)f.ld, &e);
     f.H = h.alloc<double>((size_t)(m + 1) * m, &e);
     f.cs = h.alloc<double>((size_t)m + 1, &e);
     f.sn = h.alloc<double>((size_t)m + 1, &e);
@@ -299,10 +300,9 @@ cudaError_t enqueue_start(Handle& h, const double* b, const double* x, cudaStrea
 
 // one FGMRES cycle: m steps (each a no-op once the cycle is done), update, true residual
 cudaError_t enqueue_cycle(Handle& h, const double* b, double* x, cudaStream_t st, bool cap) {
-    const size_t n = (size_t)h.n;
     const int32_t* done = &h.fg.ctl->cycle_done;
     for (int j = 0; j < h.fg.m; j++) {
-        cudaError_t e = apply_any(h, h.fg.V + (size_t)j * n, h.fg.Z + (size_t)j * n, done, st, cap);
+        cudaError_t e = apply_any(h, h.fg.V + (size_t)j * h.fg.ld, h.fg.Z + (size_t)j * h.fg.ld, done, st, cap);
         if (e != cudaSuccess) return e;
         ILU2L_SCOPED(PC_SPMV_DOT, 1, launch_fg_spmv_dot(h, j, st));
         ILU2L_SCOPED(PC_CGS, 1, launch_fg_cgs(h, j, st));

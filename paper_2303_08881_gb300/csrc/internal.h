@@ -97,8 +97,8 @@ struct FgCtl {
 };
 
 struct FgDev {
-    double* V;      // (m+1) x n
-    double* Z;      // m x n
+    double* V;      // (m+1) x ld: basis vector i at V + i * ld
+    double* Z;      // m x ld
     double* w;      // n
     double* H;      // (m+1) x m column-major
     double* cs;
@@ -109,6 +109,7 @@ struct FgDev {
     double* part;   // G x (m+1) partial sums
     FgCtl* ctl;
     int32_t m, G;
+    int64_t ld;     // leading dimension of V and Z: n rounded up to 64 (512-byte rows)
 };
 
 struct CsrDev {

@@ -21,11 +21,15 @@ namespace ilu2l {
 
 constexpr int kMaxJ = 63;  // basis vectors a Gram-Schmidt kernel handles (restart <= 64)
 
+// CTA row slices: multiples of 64 rows, so every slice starts 512-byte aligned in a
+// basis vector (leading dimension a multiple of 64) and pairs of rows load as 128 bits.
 __device__ __forceinline__ void cta_rows(int n, int& r0, int& r1) {
-    const int R = (n + gridDim.x - 1) / gridDim.x;
-    r0 = blockIdx.x * R;
+    const int R = ((n + gridDim.x - 1) / gridDim.x + 63) / 64 * 64;
+    r0 = min(n, blockIdx.x * R);
     r1 = min(n, r0 + R);
 }
+
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 
 // y_r = A_r . x with VL lanes per row; result valid in the row's first lane. Every lane
 // of the warp must call it (the shuffles use the full mask); lanes of an out-of-range row
@@ -146,79 +150,115 @@ __global__ void k_fg_scale0(FgDev f, int n) {
         f.V[r] = f.V[r] * inv;
 }
 
-// Gram-Schmidt kernels. Each CTA owns a contiguous row range (cta_rows). Updates
-// w -= V h run one row per thread with eight basis rows in flight. Dot products V_i . w
-// run in chunks of eight vectors: each thread accumulates its rows, each warp reduces its
-// eight sums with shuffles and adds them to its own shared accumulators (no CTA barrier
-// per chunk); one barrier at the end combines the warps in a fixed order.
-constexpr int kChunk = 8;
+// Gram-Schmidt kernels. Each CTA owns a row slice (cta_rows). FP64 arithmetic is the
+// bound on GB300 (2 fused multiply-adds per SM per clock), so the loops spend as few
+// instructions per multiply-add as they can: 128-bit loads of row pairs, long contiguous
+// streams per warp, several loads in flight.
+//  * Dots V_i . w: tasks (basis vector i, sub-slice) taken by the warps in turn; a warp
+//    streams one vector over its sub-slice (four row pairs per lane in flight) and leaves
+//    one partial; the sub-slice partials of a vector are added in order.
+//  * Updates w -= V h: one row pair per thread, eight basis vectors in flight, the terms
+//    subtracted in the order i = 0..j.
+constexpr int kMaxTasks = 8 * (kMaxJ + 1);
 
-// sacc[warp * (kMaxJ + 1) + i] += V_i . w over the CTA's rows, i <= j (w in global memory,
-// written by this CTA before a barrier)
-__device__ __forceinline__ void cta_dots(const double* __restrict__ V, const double* w, size_t n, int r0,
-                                         int r1, int j, double* sacc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i0 = 0; i0 <= j; i0 += kChunk) {
-        double acc[kChunk];
+// spart[i] (i <= j, shared) = sum over the CTA's rows of V_i[r] w[r]
+__device__ __forceinline__ void cta_dots(const double* __restrict__ V, int64_t ld, const double* w, int r0, int r1,
+                                         int j, double* spart, double* stask) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nsub = max(1, nw / (j + 1));
+    const int len = ((r1 - r0 + nsub - 1) / nsub + 63) / 64 * 64;
+    for (int task = warp; task < (j + 1) * nsub; task += nw) {
+        const int i = task / nsub, sb = task - i * nsub;
+        const int a = min(r1, r0 + sb * len), b = min(r1, a + len);
+        const double* __restrict__ v = V + (size_t)i * ld;
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int r = a + 2 * lane;
+        for (; r + 193 < b; r += 256) {
+            double2 x[4], y[4];
 #pragma unroll
-        for (int u = 0; u < kChunk; u++) acc[u] = 0.0;
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const double wr = w[r];
+            for (int k = 0; k < 4; k++) {
+                x[k] = ld2(v + r + 64 * k);
+                y[k] = ld2(w + r + 64 * k);
+            }
 #pragma unroll
-            for (int u = 0; u < kChunk; u++)
-                if (i0 + u <= j) acc[u] += V[(size_t)(i0 + u) * n + r] * wr;
+            for (int k = 0; k < 4; k++) {
+                acc[2 * k] += x[k].x * y[k].x;
+                acc[2 * k + 1] += x[k].y * y[k].y;
+            }
         }
-#pragma unroll
-        for (int u = 0; u < kChunk; u++) {
-            const double s = warp_sum(acc[u]);
-            if (lane == 0 && i0 + u <= j) sacc[warp * (kMaxJ + 1) + i0 + u] += s;
+        for (; r + 1 < b; r += 64) {
+            const double2 x = ld2(v + r), y = ld2(w + r);
+            acc[0] += x.x * y.x;
+            acc[1] += x.y * y.y;
         }
+        if (r < b) acc[0] += v[r] * w[r];  // the last row of an odd slice
+        double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        t = warp_sum(t);
+        if (lane == 0) stask[task] = t;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double t = 0.0;
+        for (int sb = 0; sb < nsub; sb++) t += stask[i * nsub + sb];
+        spart[i] = t;
+    }
+    __syncthreads();
 }
 
-// w[r] -= sum_i h[i] V_i[r] over the CTA's rows, eight basis rows in flight
-__device__ __forceinline__ void cta_update(const double* __restrict__ V, double* w, const double* hh, size_t n,
+// w[r] -= sum_i h[i] V_i[r] over the CTA's rows (i = 0..j in order); optionally the
+// partial ||w||^2
+__device__ __forceinline__ void cta_update(const double* __restrict__ V, int64_t ld, double* w, const double* hh,
                                            int r0, int r1, int j, double* nrm2) {
     double acc = 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double x = w[r];
+    for (int r = r0 + 2 * threadIdx.x; r < r1; r += 2 * blockDim.x) {
+        const bool pair = r + 1 < r1;
+        double2 x = pair ? ld2(w + r) : make_double2(w[r], 0.0);
         int i = 0;
         for (; i + 8 <= j + 1; i += 8) {
-            double v[8];
+            double2 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) v[u] = V[(size_t)(i + u) * n + r];
+            for (int u = 0; u < 8; u++) {
+                const double* p = V + (size_t)(i + u) * ld + r;
+                v[u] = pair ? ld2(p) : make_double2(*p, 0.0);
+            }
 #pragma unroll
-            for (int u = 0; u < 8; u++) x -= hh[i + u] * v[u];
+            for (int u = 0; u < 8; u++) {
+                x.x -= hh[i + u] * v[u].x;
+                x.y -= hh[i + u] * v[u].y;
+            }
         }
-        for (; i <= j; i++) x -= hh[i] * V[(size_t)i * n + r];
-        w[r] = x;
-        acc += x * x;
+        for (; i <= j; i++) {
+            const double* p = V + (size_t)i * ld + r;
+            const double2 v = pair ? ld2(p) : make_double2(*p, 0.0);
+            x.x -= hh[i] * v.x;
+            x.y -= hh[i] * v.y;
+        }
+        if (pair) {
+            *reinterpret_cast<double2*>(w + r) = x;
+            acc += x.x * x.x + x.y * x.y;
+        } else {
+            w[r] = x.x;
+            acc += x.x * x.x;
+        }
     }
     if (nrm2) *nrm2 = acc;
 }
 
-// combine the per-warp accumulators (fixed warp order) into the CTA's partials
-__device__ __forceinline__ void cta_partials(const double* sacc, int j, double* part, int G) {
-    const int nw = blockDim.x >> 5;
-    __syncthreads();
-    for (int u = threadIdx.x; u <= j; u += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < nw; w++) s += sacc[w * (kMaxJ + 1) + u];
-        part[(size_t)u * G + blockIdx.x] = s;
-    }
+// the CTA's partials of coefficients 0..j into part[u * G + cta]
+__device__ __forceinline__ void cta_partials(const double* spart, int j, double* part, int G) {
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) part[(size_t)u * G + blockIdx.x] = spart[u];
 }
 
 // w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w; the last CTA stores h1 in
 // column j of H
 template <int VL>
 __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
-    __shared__ double sacc[8 * (kMaxJ + 1)];
+    __shared__ double stask[kMaxTasks];
+    __shared__ double spart[kMaxJ + 1];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(A.n, r0, r1);
-    const int n = A.n;
-    for (int u = threadIdx.x; u < 8 * (kMaxJ + 1); u += blockDim.x) sacc[u] = 0.0;
-    const double* __restrict__ zj = f.Z + (size_t)j * n;
+    const double* __restrict__ zj = f.Z + (size_t)j * f.ld;
     const int sl = threadIdx.x & (VL - 1), sub = threadIdx.x / VL, nsub = blockDim.x / VL;
     for (int base = r0; base < r1; base += nsub) {
         const int r = base + sub;
@@ -227,8 +267,8 @@ __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
         if (valid && sl == 0) f.w[r] = s;
     }
     __syncthreads();
-    cta_dots(f.V, f.w, n, r0, r1, j, sacc);
-    cta_partials(sacc, j, f.part, f.G);
+    cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
+    cta_partials(spart, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, j + 1, f.H + (size_t)j * (f.m + 1));
     if (threadIdx.x == 0) f.ctl->counter = 0;
@@ -237,19 +277,19 @@ __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
 // w -= V h1 (h1 = column j of H) and the reorthogonalisation dots V^T w; the last CTA
 // adds them to column j and keeps them in f.h2 for k_fg_norm
 __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
-    __shared__ double sacc[8 * (kMaxJ + 1)];
+    __shared__ double stask[kMaxTasks];
+    __shared__ double spart[kMaxJ + 1];
     __shared__ double hh[kMaxJ + 1];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
     const double* Hj = f.H + (size_t)j * (f.m + 1);
-    for (int u = threadIdx.x; u < 8 * (kMaxJ + 1); u += blockDim.x) sacc[u] = 0.0;
     for (int u = threadIdx.x; u <= j; u += blockDim.x) hh[u] = __ldcg(Hj + u);
     __syncthreads();
-    cta_update(f.V, f.w, hh, n, r0, r1, j, nullptr);
+    cta_update(f.V, f.ld, f.w, hh, r0, r1, j, nullptr);
     __syncthreads();
-    cta_dots(f.V, f.w, n, r0, r1, j, sacc);
-    cta_partials(sacc, j, f.part, f.G);
+    cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
+    cta_partials(spart, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, j + 1, f.h2);
     if (threadIdx.x == 0) {
@@ -269,7 +309,7 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     for (int u = threadIdx.x; u <= j; u += blockDim.x) hh[u] = __ldcg(f.h2 + u);
     __syncthreads();
     double acc = 0.0;
-    cta_update(f.V, f.w, hh, n, r0, r1, j, &acc);
+    cta_update(f.V, f.ld, f.w, hh, r0, r1, j, &acc);
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
     if (!last_cta(&f.ctl->counter)) return;
@@ -315,7 +355,7 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
 __global__ void k_fg_next(FgDev f, int n, int j) {
     if (f.ctl->cycle_done) return;
     const double inv = 1.0 / __ldcg(f.hnext);
-    double* vn = f.V + (size_t)(j + 1) * n;
+    double* vn = f.V + (size_t)(j + 1) * f.ld;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
         vn[r] = f.w[r] * inv;
 }
@@ -340,7 +380,7 @@ __global__ void k_fg_update(FgDev f, int n, double* __restrict__ x) {
     cta_rows(n, r0, r1);
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         double xv = x[r];
-        for (int i = 0; i < steps; i++) xv += y[i] * f.Z[(size_t)i * n + r];
+        for (int i = 0; i < steps; i++) xv += y[i] * f.Z[(size_t)i * f.ld + r];
         x[r] = xv;
     }
 }
