@@ -386,12 +386,15 @@ __global__ void k_fg_update(FgDev f, int n, double* __restrict__ x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Lanes per CSR row: every level of the lanes' shuffle reduction is one more FP64 add per
+// row, and FP64 issue is the scarce resource on GB300, so short rows get one lane each.
 static int pick_vl(const Handle& h) {
     const double avg = h.n ? (double)h.nnz / h.n : 1.0;
-    if (avg <= 3) return 2;
-    if (avg <= 10) return 4;
-    if (avg <= 20) return 8;
-    if (avg <= 40) return 16;
+    if (avg <= 12) return 1;
+    if (avg <= 24) return 2;
+    if (avg <= 48) return 4;
+    if (avg <= 96) return 8;
+    if (avg <= 192) return 16;
     return 32;
 }
 
@@ -406,6 +409,10 @@ static CsrDev csr_of(const Handle& h) {
 
 #define ILU2L_VL_SWITCH(vl, CALL) \
     switch (vl) {                 \
+        case 1: {                 \
+            constexpr int V = 1;  \
+            CALL;                 \
+        } break;                  \
         case 2: {                 \
             constexpr int V = 2;  \
             CALL;                 \
