@@ -777,8 +777,12 @@ static RingCfg rcfg(const Handle& h) {
     return c;
 }
 
+// Dynamic shared memory of a stream kernel: barriers, ring and, when every subdomain's
+// working vector fits, the vector. Otherwise the vector lives in global memory and the
+// shared memory not requested stays L1 cache, which then holds the vector's recent levels.
 static size_t stream_smem(const Handle& h, size_t elt) {
-    return 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * elt;
+    const bool xs = h.max_ns + 1 <= h.smem_len_stream;
+    return 128 + (size_t)h.nst * h.chunk + (xs ? (size_t)h.smem_len_stream * elt : 0);
 }
 
 // The dynamic shared-memory limit is per kernel and process-wide: it is raised to the

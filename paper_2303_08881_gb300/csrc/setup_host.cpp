@@ -881,7 +881,8 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         // Ring: four stages (enough to hide the copy latency) of the largest chunk that
         // leaves every subdomain's working vector in shared memory; a chunk boundary
         // costs a few hundred cycles, so fewer, larger chunks are faster. When the vector
-        // cannot stay in shared memory anyway, the largest chunk.
+        // cannot stay in shared memory anyway, the largest chunk: the kernels then request
+        // only the ring and the rest of the on-chip memory serves the vector as L1.
         const int64_t room = (int64_t)h.smem_optin - 20 * 1024 - 128;
         const int64_t xbytes = (int64_t)(h.max_ns + 1) * vb;
         h.nst = 4;

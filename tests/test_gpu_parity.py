@@ -250,6 +250,29 @@ def test_streamed_apply_with_global_working_vector(ilu, side, prec):
     h.close()
 
 
+@pytest.mark.parametrize("side,prec", [(300, "fp64"), (430, "fp32")])
+@pytest.mark.parametrize("mode", ["single", "per_step"])
+def test_global_working_vector_with_inner_solve(ilu, side, prec, mode):
+    """2 x 2 subdomains each just too large for shared memory: the forward, inner and
+    backward kernels all keep the working vector in global memory."""
+    pr = P.aniso2d_boxes(side, 2, seed=22)
+    cfg = dict(variant="schur", factor_B="ilu0", factor_S="milu0")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_launch=mode, **cfg))
+    orc = O.Oracle.from_problem(pr, **cfg)
+    assert h.stream_stats("fwd")["vector_in_shared"] == 0 and orc.sizes().n2 > 0
+    r = np.random.default_rng(23).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    got, ref = z.cpu().numpy(), orc.apply(r)
+    assert h.stats()["device_error"] == 0
+    if prec == "fp64":
+        _assert_close64(got, ref, f"apply {side}")
+    else:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL32
+    h.close()
+
+
 def test_working_vector_in_shared_memory_for_the_2d_boxes(ilu):
     pr, h, orc = _pair(ilu, "aniso2d_ragged", CONFIGS[2], "fp32")
     assert h.stream_stats("fwd")["vector_in_shared"] == 1
