@@ -193,7 +193,8 @@ ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* la
    runs the TMA-streamed level programs, out[6..13] = (entries per row record, consumer
    threads) of the streamed programs block Jacobi, forward, local Schur, backward (0 if
    unused), out[14] = 1 when the apply runs the inner Schur GMRES as one cooperative
-   launch. out must hold 15 values. */
+   launch, out[15] = device memory the handle holds, in bytes (factors, programs, Krylov
+   workspaces; what ilu_free returns). out must hold 16 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
 /* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device

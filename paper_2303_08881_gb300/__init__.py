@@ -231,13 +231,14 @@ class Handle:
         _check(lib().ilu_inner_solve(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve")
 
     def stats(self) -> dict:
-        out = np.zeros(15, np.int64)
+        out = np.zeros(16, np.int64)
         _check(lib().ilu_get_stats(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_stats")
         progs = {name: dict(record_entries=int(out[6 + 2 * i]), threads=int(out[7 + 2 * i]))
                  for i, name in enumerate(["bj", "fwd", "s", "bwd"])}
         return dict(kernel_launches=int(out[0]), graph_launches=int(out[1]),
                     kernels_per_cycle=int(out[2]), row_ctas=int(out[3]), device_error=int(out[4]),
-                    stream_path=bool(out[5]), programs=progs, inner_single_launch=bool(out[14]))
+                    stream_path=bool(out[5]), programs=progs, inner_single_launch=bool(out[14]),
+                    device_bytes=int(out[15]))
 
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,

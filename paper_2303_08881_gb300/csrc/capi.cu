@@ -685,6 +685,7 @@ ilu_status ilu_get_stats(void* hp, int64_t* out) {
     }
     out[5] = h->stream_path ? 1 : 0;
     out[14] = h->inner_coop ? 1 : 0;
+    out[15] = (int64_t)h->device_bytes;
     const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
     for (int i = 0; i < 4; i++) {
         out[6 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].rw;

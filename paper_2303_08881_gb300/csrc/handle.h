@@ -88,6 +88,8 @@ struct Handle {
 
     // device memory
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes;  // sizes of allocs, for the device footprint
+    size_t device_bytes = 0;
     int32_t *d_qoff = nullptr, *d_nint = nullptr, *d_if_ptr = nullptr, *d_q_orig = nullptr;
     int32_t *d_q_rp = nullptr, *d_q_ci = nullptr, *d_q_dpos = nullptr;
     double* d_vals = nullptr;        // [F1 | F2 | A_local] FP64 values
@@ -158,6 +160,8 @@ struct Handle {
             return nullptr;
         }
         allocs.push_back(p);
+        alloc_bytes.push_back(bytes);
+        device_bytes += bytes;
         return (T*)p;
     }
 
@@ -165,7 +169,9 @@ struct Handle {
         for (size_t i = 0; i < allocs.size(); i++)
             if (allocs[i] == q) {
                 cudaFree(q);
+                device_bytes -= alloc_bytes[i];
                 allocs.erase(allocs.begin() + (long)i);
+                alloc_bytes.erase(alloc_bytes.begin() + (long)i);
                 return;
             }
     }

@@ -322,3 +322,60 @@ def make_config(key: str, seed: int = 0, **override) -> Problem:
     spec.update(override)
     fn = globals()[spec.pop("fn")]
     return fn(seed=seed, **spec)
+
+
+# ---------------------------------------------------------------------------------------
+# serving trace: a stream of solve requests with Poisson arrivals
+
+
+@dataclass
+class RequestSpec:
+    """One request of a serving trace: which matrix (repeats share `key`), which
+    right-hand side, and when it arrives (seconds after the trace starts)."""
+    rid: int
+    arrival: float
+    key: str
+    kind: str          # "2d" (9-point rotated anisotropic) or "3d" (7-point anisotropic)
+    side: int
+    eps: float
+    theta: float
+    boxes: int         # subdomain boxes per axis
+    rhs_seed: int
+
+
+def serving_trace(n_requests: int = 2000, rate: float = 200.0, repeat: float = 0.3, seed: int = 0):
+    """Requests for the serving workload: inter-arrival times Exp(1 / rate); half 2D
+    9-point rotated anisotropic problems (side log-uniform in [32, 512]), half 3D 7-point
+    anisotropic (side log-uniform in [16, 96], coefficients (1, 1, eps)); eps log-uniform
+    in [1e-4, 1], theta uniform in [0, pi) (2D only); subdomain boxes of about 64^2 / 16^3
+    nodes; a fraction `repeat` of the requests reuse an earlier request's matrix with a
+    new right-hand side."""
+    rng = np.random.default_rng([seed, 5])
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        if out and rng.random() < repeat:
+            src = out[int(rng.integers(len(out)))]
+            out.append(RequestSpec(i, t, src.key, src.kind, src.side, src.eps, src.theta, src.boxes,
+                                   int(rng.integers(1 << 30))))
+            continue
+        eps = float(10.0 ** rng.uniform(-4.0, 0.0))
+        if rng.random() < 0.5:
+            side = int(round(2.0 ** rng.uniform(5.0, 9.0)))
+            theta = float(rng.uniform(0.0, math.pi))
+            kind, boxes = "2d", max(1, side // 64)
+        else:
+            side = int(round(2.0 ** rng.uniform(4.0, math.log2(96.0))))
+            theta = 0.0
+            kind, boxes = "3d", max(1, side // 16)
+        out.append(RequestSpec(i, t, f"{kind}-{side}-{eps:.6g}-{theta:.6g}", kind, side, eps, theta, boxes,
+                               int(rng.integers(1 << 30))))
+    return out
+
+
+def problem_of_request(spec: RequestSpec) -> Problem:
+    """The matrix and partition of a request, with its own right-hand side."""
+    if spec.kind == "2d":
+        return aniso2d_boxes(spec.side, spec.boxes, eps=spec.eps, theta=spec.theta, seed=spec.rhs_seed)
+    return aniso3d_boxes(spec.side, spec.boxes, coef=(1.0, 1.0, spec.eps), seed=spec.rhs_seed)
