@@ -197,6 +197,13 @@ ilu_status ilu_profile_read(void* h, const char** names, double* ms, int64_t* la
    workspaces; what ilu_free returns). out must hold 16 values. */
 ilu_status ilu_get_stats(void* h, int64_t* out);
 
+/* Wall-clock times of a handle, in ms: out[0] = host analysis of ilu_setup (classification,
+   ordering, patterns, level programs, streams), out[1] = its device part (uploads, numeric
+   factorisation, packing), out[2] = the last gmres_solve, out[3] = the part of it spent
+   capturing and instantiating the cycle graph (0 when the handle's graph was reused).
+   out must hold 4 values. Errors: ILU_ERR_ARG for a null pointer. */
+ilu_status ilu_get_times(void* h, double* out);
+
 /* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device
    consumes it): program 0 = block Jacobi, 1 = forward (L_B, the W rows and S~), 2 = local
    Schur S~ alone, 3 = backward. out[0] = entries per row record, out[1] = consumer

@@ -83,6 +83,7 @@ def lib():
             "ilu_profile_read": (I, [P, P, P, P, P]),
             "ilu_get_stats": (I, [P, P]),
             "ilu_get_stream_stats": (I, [P, I, P]),
+            "ilu_get_times": (I, [P, P]),
             "ilu_get_stream": (I, [P, I, P, P, P]),
             "ilu_inner_solve_noalloc": (I, [P, P, P]),
         }
@@ -239,6 +240,13 @@ class Handle:
                     kernels_per_cycle=int(out[2]), row_ctas=int(out[3]), device_error=int(out[4]),
                     stream_path=bool(out[5]), programs=progs, inner_single_launch=bool(out[14]),
                     device_bytes=int(out[15]))
+
+    def times(self) -> dict:
+        """Wall-clock ms: host analysis and device part of the setup, the last solve and
+        its graph build."""
+        out = np.zeros(4)
+        _check(lib().ilu_get_times(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_times")
+        return dict(host_ms=float(out[0]), device_ms=float(out[1]), solve_ms=float(out[2]), graph_ms=float(out[3]))
 
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "handle.h"
@@ -26,6 +27,55 @@ ilu_status map_err(cudaError_t e) {
     if (e == cudaSuccess) return ILU_OK;
     if (e == cudaErrorMemoryAllocation) return ILU_ERR_OOM;
     return ILU_ERR_CUDA;
+}
+
+// ---- process-wide resources shared by the handles (guarded: handles live on many threads)
+static std::mutex g_res_mutex;
+
+// The default memory pool of a device keeps freed memory for reuse instead of returning it:
+// handles come and go without mapping or unmapping device memory.
+static cudaError_t pool_keep(int dev) {
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(g_res_mutex);
+    if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    uint64_t keep = UINT64_MAX;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// Kernel attributes (the dynamic shared-memory limit, raised to the device maximum) are
+// set once per device and kernel family.
+template <class F>
+static cudaError_t once_per_device(int dev, int family, F fn) {
+    static bool done[64][8] = {};
+    std::lock_guard<std::mutex> lk(g_res_mutex);
+    if (dev < 0 || dev >= 64 || family < 0 || family >= 8) return fn();
+    if (done[dev][family]) return cudaSuccess;
+    cudaError_t e = fn();
+    if (e == cudaSuccess) done[dev][family] = true;
+    return e;
+}
+
+// Pinned host control blocks of the FGMRES driver, recycled (freeing pinned memory would
+// synchronise the device).
+static std::vector<FgCtl*> g_ctl_free;
+static cudaError_t ctl_take(FgCtl** out) {
+    {
+        std::lock_guard<std::mutex> lk(g_res_mutex);
+        if (!g_ctl_free.empty()) {
+            *out = g_ctl_free.back();
+            g_ctl_free.pop_back();
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost(out, sizeof(FgCtl));
+}
+static void ctl_give(FgCtl* c) {
+    std::lock_guard<std::mutex> lk(g_res_mutex);
+    g_ctl_free.push_back(c);
 }
 
 template <class T>
@@ -67,7 +117,7 @@ ilu_status device_setup_t(Handle& h) {
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h.device));
     const int64_t cap = std::max<int64_t>(0, (int64_t)optin - 20 * 1024) / (int64_t)sizeof(T);
     h.smem_len = (int32_t)std::min<int64_t>(h.max_ns, cap);
-    CK(configure_apply<T>((size_t)h.smem_len * sizeof(T)));
+    CK(once_per_device(h.device, sizeof(T) == 4 ? 0 : 1, [&] { return configure_apply<T>((size_t)h.smem_len * sizeof(T)); }));
     if (h.stream_path) {  // the streamed kernels keep the ring in shared memory too
         const int64_t cap_s = ((int64_t)optin - 20 * 1024 - 128 - (int64_t)h.nst * h.chunk) / (int64_t)sizeof(T);
         h.smem_len_stream = (int32_t)std::max<int64_t>(0, std::min<int64_t>((int64_t)h.max_ns + 1, cap_s));
@@ -94,7 +144,9 @@ ilu_status device_setup_t(Handle& h) {
     cv.clear();
     cv.shrink_to_fit();
     if (h.stream_path) {
-        CK(configure_stream<T>(h, 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * sizeof(T)));
+        CK(once_per_device(h.device, sizeof(T) == 4 ? 2 : 3, [&] {
+            return configure_stream<T>(h, 128 + (size_t)h.nst * h.chunk + (size_t)h.smem_len_stream * sizeof(T));
+        }));
         if (h.variant == ILU_VARIANT_SCHUR && h.n2 > 0 && h.o.inner_launch == 0)
             CK(inner_coop_fits<T>(h, &h.inner_coop));
         h.d_tbuf = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
@@ -125,9 +177,10 @@ ilu_status device_setup_t(Handle& h) {
         }
     }
     if (h.variant == ILU_VARIANT_BJ) {
+        if (h.stream_path) return ILU_OK;
         ilu_status s = upload_prog<T>(h, PR_BJ);
         if (s != ILU_OK) return s;
-    } else {
+    } else if (!h.stream_path) {  // the streamed path reads its own chunks only
         for (int id : {PR_FWD, PR_S, PR_BWD}) {
             ilu_status s = upload_prog<T>(h, id);
             if (s != ILU_OK) return s;
@@ -139,6 +192,7 @@ ilu_status device_setup_t(Handle& h) {
 ilu_status device_setup(Handle& h) {
     cudaError_t e = cudaSuccess;
     CK(cudaGetDevice(&h.device));
+    CK(pool_keep(h.device));
     CK(cudaDeviceGetAttribute(&h.sm_count, cudaDevAttrMultiProcessorCount, h.device));
     const int n = h.n, p = h.p;
     CK(upload(h, &h.d_qoff, h.qoff));
@@ -201,6 +255,9 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.V = h.alloc<double>((size_t)(m + 1) * (size_t)f.ld, &e);
     f.Z = h.alloc<double>((size_t)m * (size_t)f.ld, &e);
     f.w = h.alloc<double>((size_t)f.ld, &e);
+    h.fg_b = h.alloc<double>((size_t)f.ld, &e);
+    h.fg_x = h.alloc<double>((size_t)f.ld, &e);
+    if (!h.fg_b || !h.fg_x) return map_err(e);
     f.H = h.alloc<double>((size_t)(m + 1) * m, &e);
     f.cs = h.alloc<double>((size_t)m + 1, &e);
     f.sn = h.alloc<double>((size_t)m + 1, &e);
@@ -220,7 +277,7 @@ ilu_status ensure_fgmres(Handle& h, int m) {
         cudaGraphExecDestroy(h.cycle_exec);
         h.cycle_exec = nullptr;
     }
-    if (!h.h_ctl) CK(cudaMallocHost(&h.h_ctl, sizeof(FgCtl)));
+    if (!h.h_ctl) CK(ctl_take(&h.h_ctl));
     return ILU_OK;
 }
 
@@ -269,7 +326,7 @@ cudaError_t apply_t(Handle& h, const double* r, double* z, const int32_t* done, 
         e = fast ? launch_fwd_s<T>(h, r, done, st) : launch_schur_fwd<T>(h, r, done, st);
     }
     if (e == cudaSuccess && h.n2 > 0) {
-        Scope sc(h, PC_INNER, (fast ? 4 : 3) * h.inner_k, st, cap);
+        Scope sc(h, PC_INNER, fast ? (h.inner_coop ? 1 : 4 * h.inner_k) : 3 * h.inner_k, st, cap);
         e = fast ? launch_inner_s<T>(h, done, st) : launch_inner<T>(h, done, st);
     }
     if (e == cudaSuccess) {
@@ -371,8 +428,8 @@ ilu_status ilu_free(void* hp) {
     Handle* h = (Handle*)hp;
     if (!h->o.analysis_only) cudaStreamSynchronize(h->st);
     if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
-    for (void* p : h->allocs) cudaFree(p);
-    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->st);
+    if (h->h_ctl) ctl_give(h->h_ctl);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return ILU_OK;
@@ -421,6 +478,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
             h->smem_optin = optin;
     }
     ilu_status s = host_setup(*h, A, part, p);
+    h->host_ms = now_ms() - t0;
     if (s == ILU_OK && o.analysis_only) {
         h->setup_ms = now_ms() - t0;
         *hout = h;
@@ -457,6 +515,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
     std::vector<double>().swap(h->q_v);
     std::vector<double>().swap(h->f1_host_vals);
     h->setup_ms = now_ms() - t0;
+    h->device_ms = h->setup_ms - h->host_ms;
     *hout = h;
     return ILU_OK;
 }
@@ -501,8 +560,18 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
     init.m = restart;
     *h->h_ctl = init;
     CK(cudaMemcpyAsync(h->fg.ctl, h->h_ctl, sizeof(FgCtl), cudaMemcpyHostToDevice, h->st));
+    // the cycles run on the handle's own copies of b and x, so the cycle graph captured
+    // for this handle stays valid whatever buffers later calls pass
+    const double* ub = b;
+    double* ux = x;
+    b = h->fg_b;
+    x = h->fg_x;
+    CK(cudaMemcpyAsync(h->fg_b, ub, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->fg_x, ux, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(enqueue_start(*h, b, x, h->st));
     const bool graphs = h->o.use_graphs && !h->prof;
+    const double tg = now_ms();
+    h->graph_ms_last = 0.0;
     if (graphs && (h->cycle_exec == nullptr || h->cycle_b != b || h->cycle_x != x || h->cycle_m != restart)) {
         if (h->cycle_exec) {
             cudaGraphExecDestroy(h->cycle_exec);
@@ -527,6 +596,7 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
         h->cycle_b = b;
         h->cycle_x = x;
         h->cycle_m = restart;
+        h->graph_ms_last = now_ms() - tg;
     }
     int cycles = 0;
     ilu_status result = ILU_OK;
@@ -557,7 +627,9 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
         }
         cycles++;
     }
+    CK(cudaMemcpyAsync(ux, h->fg_x, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
+    h->solve_ms_last = now_ms() - t0;
     const FgCtl& c = *h->h_ctl;
     if (info) {
         info->iters = c.total;
@@ -575,6 +647,7 @@ ilu_status gmres_solve(void* hp, const double* b, double* x, double rtol, int32_
 ilu_status ilu_get_sizes(void* hp, int64_t* out) {
     if (!hp || !out) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
+    host_levels(*h);
     out[0] = h->n;
     out[1] = h->p;
     out[2] = h->n1;
@@ -613,6 +686,7 @@ ilu_status ilu_get_perm(void* hp, int32_t* perm, int32_t* iperm, int32_t* int_pt
 ilu_status ilu_get_levels(void* hp, int32_t which, int32_t* lev, int32_t* nlev) {
     if (!hp || !lev || which < 0 || which > 5) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
+    host_levels(*h);
     std::memcpy(lev, h->lev[which].data(), h->lev[which].size() * sizeof(int32_t));
     if (nlev) *nlev = h->nlev[which];
     return ILU_OK;
@@ -691,6 +765,16 @@ ilu_status ilu_get_stats(void* hp, int64_t* out) {
         out[6 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].rw;
         out[7 + 2 * i] = h->sh[ids[i]].ch0.empty() ? 0 : h->sh[ids[i]].nt;
     }
+    return ILU_OK;
+}
+
+ilu_status ilu_get_times(void* hp, double* out) {
+    if (!hp || !out) return ILU_ERR_ARG;
+    const Handle* h = (const Handle*)hp;
+    out[0] = h->host_ms;
+    out[1] = h->device_ms;
+    out[2] = h->solve_ms_last;
+    out[3] = h->graph_ms_last;
     return ILU_OK;
 }
 

@@ -45,6 +45,9 @@ struct StreamBufs {
     int rw = 4;
 };
 
+// The introspection level sets (Handle::lev / nlev), built on the first call.
+void host_levels(Handle& h);
+
 // Builds the chunked stream of program P; false if a single row does not fit a chunk.
 bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, uint32_t chunk,
                   StreamHost& S);
@@ -66,6 +69,10 @@ struct Handle {
     bool f2_alias = false, f1_device = true;
     int npert = 0;
     double setup_ms = 0.0;
+    double host_ms = 0.0, device_ms = 0.0;        // the two parts of setup_ms
+    double solve_ms_last = 0.0, graph_ms_last = 0.0;  // last gmres_solve; its graph build
+    double* fg_b = nullptr;                       // the solve's own copies of b and x: the
+    double* fg_x = nullptr;                       // cycle graph is built once per handle
     int threads = 256;       // threads of the per-subdomain kernels
     int32_t smem_len = 0;    // working vector capacity (elements of the PC type)
     int32_t max_ns = 0;
@@ -78,6 +85,8 @@ struct Handle {
     std::vector<int32_t> lev[6];
     int32_t nlev[6] = {0, 0, 0, 0, 0, 0};
     FPat f1, f2;           // patterns of the two factorisations (f2 may equal f1)
+    FPat apat;             // pattern of the local blocks A_s themselves
+    bool lev_ready = false;  // lev / nlev computed (on the first introspection call)
     std::vector<double> f1_host_vals;  // ILUT values (host-computed factor F1)
     int64_t a_base = 0;    // region of the original local values in the value array
     int64_t nvals = 0;
@@ -149,12 +158,15 @@ struct Handle {
     int64_t graph_launches = 0;
     int64_t cycle_nodes = 0;
 
+    // Device memory is stream-ordered on the handle's stream (cudaMallocAsync / FreeAsync):
+    // freeing never synchronises the device, so handles built, used and freed by several
+    // threads at once do not stall each other's work.
     template <class T>
     T* alloc(size_t count, cudaError_t* err) {
         void* p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
         if (e != cudaSuccess) {
             *err = e;
             return nullptr;
@@ -168,7 +180,7 @@ struct Handle {
     void release(void* q) {
         for (size_t i = 0; i < allocs.size(); i++)
             if (allocs[i] == q) {
-                cudaFree(q);
+                cudaFreeAsync(q, st);
                 device_bytes -= alloc_bytes[i];
                 allocs.erase(allocs.begin() + (long)i);
                 alloc_bytes.erase(alloc_bytes.begin() + (long)i);

@@ -13,6 +13,8 @@
 #include "handle.h"
 #include "stream_layout.h"
 
+static_assert(__BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__, "streams are written little-endian, as the device reads them");
+
 namespace ilu2l {
 
 namespace {
@@ -321,8 +323,11 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     if (nt_fit < 32 || chunk > (1u << 20)) return false;
     S.nt = std::min(S.nt, std::min(nt_fit, kMaxConsumers));
     const uint32_t nt = (uint32_t)S.nt;
-    auto put = [&](size_t off, uint32_t v, int bytes) {
-        for (int b = 0; b < bytes; b++) S.blob[off + b] = (uint8_t)(v >> (8 * b));
+    auto put = [&](size_t off, uint32_t v, int bytes) {  // little-endian, like the device
+        if (bytes == 4)
+            std::memcpy(&S.blob[off], &v, 4);
+        else
+            for (int b = 0; b < bytes; b++) S.blob[off + b] = (uint8_t)(v >> (8 * b));
     };
     struct Piece {
         int32_t k;      // packed row (-1: skip record, a hole in a merged wave)
@@ -544,6 +549,41 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
 
 // ====================================================================================
 
+// Level sets of the six factor windows (A or L_A, U_A; L_B, U_B; L_S, U_S) in the global
+// interior-first numbering, for introspection (Sec. 3.1); built on the first request.
+void host_levels(Handle& h) {
+    if (h.lev_ready) return;
+    const int32_t n = h.n, p = h.p;
+    const bool schur = (h.variant == ILU_VARIANT_SCHUR);
+    for (int w = 0; w < 6; w++) {
+        h.lev[w].assign(n, -1);
+        h.nlev[w] = 0;
+    }
+    std::vector<int32_t> lev(h.max_ns + 1, 0);
+    for (int32_t s = 0; s < p; s++) {
+        const int32_t q0 = h.qoff[s];
+        const int32_t ni = h.nint[s];
+        const int32_t ns = h.qoff[s + 1] - q0;
+        auto glob = [&](int32_t l) { return l < ni ? h.int_ptr[s] + l : h.n1 + h.if_ptr[s] + (l - ni); };
+        const FPat& pa = (!schur) ? h.f1 : h.apat;
+        for (int w = 0; w < 6; w++) {
+            const FPat& F = (w < 2) ? pa : (w < 4 ? h.f1 : h.f2);
+            int32_t r0 = 0, r1 = ns, clo = 0, chi = ns;
+            if (w == 2 || w == 3) {
+                r1 = ni;
+                chi = ni;
+            } else if (w == 4 || w == 5) {
+                r0 = ni;
+                clo = ni;
+            }
+            const int nl = window_levels(F, q0, r0, r1, clo, chi, (w & 1) != 0, lev);
+            h.nlev[w] = std::max(h.nlev[w], (r1 > r0) ? nl : 0);
+            for (int32_t r = r0; r < r1; r++) h.lev[w][glob(r)] = lev[r];
+        }
+    }
+    h.lev_ready = true;
+}
+
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
     ilu_status st = validate(A, part, p);
     if (st != ILU_OK) return st;
@@ -758,11 +798,9 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     h.nvals = h.a_base + nnzQ;
     if (h.nvals >= (int64_t)INT32_MAX) return ILU_ERR_TOO_LARGE;
 
-    // ---- level sets (introspection) and level programs
-    for (int w = 0; w < 6; w++) {
-        h.lev[w].assign(n, -1);
-        h.nlev[w] = 0;
-    }
+    // ---- level programs (the introspection level sets are built on demand)
+    h.apat = apat;
+    h.lev_ready = false;
     for (int pr = 0; pr < PR_COUNT; pr++) prog_init(h.prog[pr]);
     prog_init(h.numprog);
     std::vector<int32_t> lev(h.max_ns + 1, 0);
@@ -771,23 +809,6 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         const int32_t q0 = h.qoff[s];
         const int32_t ni = h.nint[s];
         const int32_t ns = h.qoff[s + 1] - q0;
-        auto glob = [&](int32_t l) { return l < ni ? h.int_ptr[s] + l : h.n1 + h.if_ptr[s] + (l - ni); };
-        // introspection levels
-        const FPat& pa = (!schur) ? h.f1 : apat;
-        for (int w = 0; w < 6; w++) {
-            const FPat& F = (w < 2) ? pa : (w < 4 ? h.f1 : h.f2);
-            int32_t r0 = 0, r1 = ns, clo = 0, chi = ns;
-            if (w == 2 || w == 3) {
-                r1 = ni;
-                chi = ni;
-            } else if (w == 4 || w == 5) {
-                r0 = ni;
-                clo = ni;
-            }
-            const int nl = window_levels(F, q0, r0, r1, clo, chi, (w & 1) != 0, lev);
-            h.nlev[w] = std::max(h.nlev[w], (r1 > r0) ? nl : 0);
-            for (int32_t r = r0; r < r1; r++) h.lev[w][glob(r)] = lev[r];
-        }
         // numeric factorisation schedule: L levels of the pattern of A_s (all local rows)
         {
             ProgHost& N = h.numprog;

@@ -165,6 +165,11 @@ class Record:
     reused: bool = False
     rel_res: float = float("nan")
     device_bytes: int = 0
+    setup_s: float = 0.0     # handle build (host analysis + device factorisation); 0 when reused
+    solve_s: float = 0.0     # right-hand side in, FGMRES, solution out
+    host_ms: float = 0.0     # the handle's host analysis, device setup and graph build (library clocks)
+    device_ms: float = 0.0
+    graph_ms: float = 0.0
 
 
 @dataclass
@@ -216,14 +221,17 @@ def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int =
                     except Exception:
                         cache.abandon(key)
                         raise
+                    ts = time.perf_counter()
                     try:
                         h = ilu.ilu_setup_problem(pr, ilu.Opts(stream=stream.cuda_stream, **opts))
+                        rec.setup_s = time.perf_counter() - ts
                     except Exception:
                         cache.cancel(est)
                         cache.abandon(key)
                         raise
                     cache.insert(key, h, est, max(est, h.stats()["device_bytes"]))
                     held = True
+                ts = time.perf_counter()
                 with torch.cuda.stream(stream):
                     b = torch.from_numpy(pr.b).to("cuda", non_blocking=True)
                     x = torch.zeros_like(b)
@@ -232,8 +240,13 @@ def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int =
                 info = ilu.gmres_solve(h, b, x, rtol=rtol, restart=restart, maxit=maxit)
                 xs = x.cpu().numpy()
                 rec.done = now()
+                rec.solve_s = time.perf_counter() - ts
                 rec.iters, rec.status = info["iters"], info["status"]
                 rec.device_bytes = h.stats()["device_bytes"]
+                tm = h.times()
+                if not rec.reused:
+                    rec.host_ms, rec.device_ms = tm["host_ms"], tm["device_ms"]
+                rec.graph_ms = tm["graph_ms"]
                 cache.update_bytes(key, rec.device_bytes)
                 if check_residual:
                     r = pr.b - pr.scipy() @ xs
@@ -281,4 +294,12 @@ def summarize(records, wall: float) -> dict:
         "reused": sum(r.reused for r in ok),
         "max_rel_res": float(max((r.rel_res for r in ok if r.rel_res == r.rel_res), default=float("nan"))),
         "converged": sum(r.status == 0 for r in ok),
+        "mean_wait_ms": float(np.mean([r.start - r.arrival for r in ok]) * 1e3) if ok else 0.0,
+        "mean_setup_ms": float(np.mean([r.setup_s for r in ok if not r.reused]) * 1e3) if ok else 0.0,
+        "mean_solve_ms": float(np.mean([r.solve_s for r in ok]) * 1e3) if ok else 0.0,
+        "mean_host_analysis_ms": float(np.mean([r.host_ms for r in ok if not r.reused])) if ok else 0.0,
+        "mean_device_setup_ms": float(np.mean([r.device_ms for r in ok if not r.reused])) if ok else 0.0,
+        "mean_graph_ms": float(np.mean([r.graph_ms for r in ok])) if ok else 0.0,
+        "busy_setup_s": float(sum(r.setup_s for r in ok)),
+        "busy_solve_s": float(sum(r.solve_s for r in ok)),
     }
