@@ -311,7 +311,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving sample in the default run (0 = skip)")
-    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--mode", default="solve", choices=["solve", "apply", "serve"],
                     help="apply: only time the preconditioner apply (used for kernel profiling)")
     ap.add_argument("--prec", default=None, choices=[None, "fp32", "fp64"])
