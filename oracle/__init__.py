@@ -18,12 +18,12 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
 ILU0, MILU0, ILUT, EXACT = 0, 1, 2, 3
-BJ, SCHUR = 0, 1
+BJ, SCHUR, RAP = 0, 1, 2
 FORM_AUTO, FORM_WZ, FORM_EF = 0, 1, 2
 OK, ERR_ARG, ERR_CSR, ERR_OOM, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 
 _FACT = {"ilu0": ILU0, "milu0": MILU0, "ilut": ILUT, "exact": EXACT}
-_VAR = {"bj": BJ, "schur": SCHUR}
+_VAR = {"bj": BJ, "schur": SCHUR, "rap": RAP}
 
 
 def build(force: bool = False) -> str:

@@ -768,7 +768,11 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
         free(fill);
     }
 
-    /* factorisations (Sec. 3.1 / 3.2 / 2.3); readings:
+    /* factorisations (Sec. 3.1 / 3.2 / 2.3 / 3.3); readings:
+       RAP (Sec. 3.3, Algorithm "Multiplicative RAP-ILU on GPU"): F1 = factor_B(A_s), the
+         smoother applied on the whole local block (ILU(0) by default); F2 = factor_S(A_s)
+         (MILU(0) by default) gives L_B, U_B, W, Z for R and P (Eq. wzinmilu) and L_S, U_S
+         for the coarse preconditioner (Eq. miluwz3).
        BJ: F1 = factor_B(A_s), applied as U^{-1} L^{-1} on the whole local block.
        SCHUR with factor_B in {ILU0, MILU0, EXACT}: F1 = factor_B(A_s) gives L_B, U_B and
          W = L(2,1), Z = U(1,2) (Eq. BILU); F2 = factor_S(A_s) gives L_S, U_S; if the two
@@ -776,11 +780,12 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
        SCHUR with factor_B = ILUT: F1 = ILUT(B_s), and the E/F form is used. */
     {
         int kB = h->o.factor_B, kS = h->o.factor_S;
-        if (h->o.variant != ORC_BJ && h->o.variant != ORC_SCHUR) {
+        if (h->o.variant != ORC_BJ && h->o.variant != ORC_SCHUR && h->o.variant != ORC_RAP) {
             st = ORC_ERR_ARG;
             goto fail;
         }
-        if (kB < 0 || kB > 3 || kS < 0 || kS > 3 || kS == ORC_ILUT) {
+        if (kB < 0 || kB > 3 || kS < 0 || kS > 3 || kS == ORC_ILUT ||
+            (h->o.variant == ORC_RAP && kB == ORC_ILUT)) {
             st = ORC_ERR_ARG;
             goto fail;
         }
@@ -798,7 +803,7 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
             }
         }
         if (st) goto fail;
-        if (h->o.variant == ORC_SCHUR && !(kS == kB && !bonly)) {
+        if (h->o.variant != ORC_BJ && !(kS == kB && !bonly)) {
             h->F2 = (csr_t*)calloc((size_t)p, sizeof(csr_t));
             if (!h->F2) {
                 st = ORC_ERR_OOM;
@@ -1074,12 +1079,81 @@ static void givens(double a, double b, double* c, double* s) {
     }
 }
 
+/* ---- two-level multiplicative (Sec. 3.3) ---- */
+
+static void sub_block_mv(const csr_t* M, int r0, int r1, int c0, int c1, double* loc);
+
+/* full vector in the new order <- local vector of subdomain s (and back) */
+static void loc_to_new(orc_t* h, int s, const double* loc, double* xn) {
+    int ns = nint_of(h, s) + nif_of(h, s);
+    for (int l = 0; l < ns; l++) xn[glob_of(h, s, l)] = loc[l];
+}
+static void new_to_loc(orc_t* h, int s, const double* xn, double* loc) {
+    int ns = nint_of(h, s) + nif_of(h, s);
+    for (int l = 0; l < ns; l++) loc[l] = xn[glob_of(h, s, l)];
+}
+
+/* P v (Eq. wzinmilu): interior rows -U_B^{-1} Z v, interface rows v, with L_B, U_B, Z
+   from F2; out is a full vector in the new order */
+static void rap_prolong(orc_t* h, const double* v, double* out, double* loc) {
+    for (int s = 0; s < h->p; s++) {
+        int ni = nint_of(h, s), ns = ni + nif_of(h, s);
+        for (int l = 0; l < ni; l++) loc[l] = 0.0;
+        for (int l = ni; l < ns; l++) loc[l] = v[h->if_ptr[s] + (l - ni)];
+        sub_block_mv(&h->F2[s], 0, ni, ni, ns, loc); /* 0 - Z v */
+        usolve_win(&h->F2[s], 0, ni, ni, loc, loc);  /* U_B^{-1} */
+        loc_to_new(h, s, loc, out);
+    }
+}
+
+/* R u (Eq. wzinmilu): interface rows u_G - W L_B^{-1} u_I per subdomain; u a full vector
+   in the new order, out an interface vector */
+static void rap_restrict(orc_t* h, const double* u, double* out, double* loc) {
+    for (int s = 0; s < h->p; s++) {
+        int ni = nint_of(h, s), ns = ni + nif_of(h, s);
+        new_to_loc(h, s, u, loc);
+        lsolve_win(&h->F2[s], 0, ni, 0, loc, loc);   /* L_B^{-1} u_I */
+        sub_block_mv(&h->F2[s], ni, ns, 0, ni, loc); /* u_G - W (.) */
+        for (int l = ni; l < ns; l++) out[h->if_ptr[s] + (l - ni)] = loc[l];
+    }
+}
+
+/* A applied to a vector in the new order (A is stored in the original order) */
+static void a_new(orc_t* h, const double* xn, double* yn) {
+    int n = h->n;
+    double* xo = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    double* yo = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    for (int g = 0; g < n; g++) xo[h->perm[g]] = xn[g];
+    orc_spmv(n, h->A.rp, h->A.ci, h->A.v, xo, yo);
+    for (int g = 0; g < n; g++) yn[g] = yo[h->perm[g]];
+    free(xo);
+    free(yo);
+}
+
+/* the preconditioned coarse MATVEC: out = (L_S U_S)^{-1} R A P y (Eq. miluwz3: L_S U_S
+   preconditions RAP) */
+static void rap_op(orc_t* h, const double* y, double* out) {
+    int n = h->n;
+    double* pv = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    double* apv = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    double* loc = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    rap_prolong(h, y, pv, loc);
+    a_new(h, pv, apv);
+    rap_restrict(h, apv, out, loc);
+    s_solve(h, out, out);
+    free(pv);
+    free(apv);
+    free(loc);
+}
+
 /* Inner Schur solve (Sec. 3.2, Eq. preSS; "a small number of GMRES iterations", three
    in Sec. 4.1.1): GMRES with x0 = 0 and exactly k = inner_iters Arnoldi steps (classical
    Gram-Schmidt with one reorthogonalisation, Givens rotations) on
    (I + S^{-1} C_off) y = S^{-1} g', S^{-1} = blockdiag(U_S^{-1} L_S^{-1}). Reading: a
    step whose new Arnoldi norm is <= 1e-14 ||c|| ends the iteration early (lucky
-   breakdown). */
+   breakdown). RAP: the same GMRES on the coarse system left-preconditioned like Eq.
+   preSS, S^{-1} R A P y = S^{-1} r (reading: the paper gives only "GMRES on S v = r"
+   with L_S U_S as its preconditioner, Sec. 3.3). */
 int orc_inner_gmres(void* hp, const double* gp, double* y) {
     orc_t* h = (orc_t*)hp;
     int n2 = h->n2, k = h->o.inner_iters;
@@ -1104,7 +1178,10 @@ int orc_inner_gmres(void* hp, const double* gp, double* y) {
         g[0] = beta;
         for (int j = 0; j < k; j++) {
             double* vj = V + (size_t)j * n2;
-            schur_op(h, vj, w, tmp);
+            if (h->o.variant == ORC_RAP)
+                rap_op(h, vj, w); /* coarse system RAP v = r (Algorithm "Two-level multiplicative solve") */
+            else
+                schur_op(h, vj, w, tmp);
             for (int i = 0; i <= j; i++) hc[i] = 0.0;
             for (int pass = 0; pass < 2; pass++) { /* CGS2 */
                 double hh[64];
@@ -1192,6 +1269,32 @@ int orc_apply(void* hp, const double* r, double* z) {
             usolve_win(&h->F1[s], 0, ns, ns, loc, loc);
             for (int l = 0; l < ns; l++) xg[glob_of(h, s, l)] = loc[l];
         }
+    } else if (h->o.variant == ORC_RAP) {
+        /* Algorithm "Two-level multiplicative solve" in the GPU form of Algorithm
+           "Multiplicative RAP-ILU on GPU": x^ = (L_A U_A)^{-1} b blockwise (F1, the
+           smoother); r = R (b - A x^); v = inner GMRES on the coarse system; x = x^ + P v */
+        int n2 = h->n2;
+        double* xh = (double*)malloc(((size_t)n + 1) * sizeof(double));
+        double* res = (double*)malloc(((size_t)n + 1) * sizeof(double));
+        double* rc = (double*)malloc(((size_t)n2 + 1) * sizeof(double));
+        double* v = (double*)malloc(((size_t)n2 + 1) * sizeof(double));
+        for (int s = 0; s < h->p; s++) {
+            int ns = nint_of(h, s) + nif_of(h, s);
+            new_to_loc(h, s, xg, loc);
+            lsolve_win(&h->F1[s], 0, ns, 0, loc, loc);
+            usolve_win(&h->F1[s], 0, ns, ns, loc, loc);
+            loc_to_new(h, s, loc, xh);
+        }
+        a_new(h, xh, res);
+        for (int g = 0; g < n; g++) res[g] = xg[g] - res[g]; /* b - A x^ */
+        rap_restrict(h, res, rc, loc);
+        orc_inner_gmres(h, rc, v);
+        rap_prolong(h, v, res, loc);                          /* P v */
+        for (int g = 0; g < n; g++) xg[g] = xh[g] + res[g];
+        free(xh);
+        free(res);
+        free(rc);
+        free(v);
     } else {
         double* gp = (double*)malloc(((size_t)h->n2 + 1) * sizeof(double));
         double* y = (double*)malloc(((size_t)h->n2 + 1) * sizeof(double));

@@ -39,14 +39,17 @@ extern "C" {
 /* variants and forms */
 #define ORC_BJ 0
 #define ORC_SCHUR 1
+#define ORC_RAP 2     /* two-level multiplicative (Algorithm "Two-level multiplicative solve") */
 #define ORC_FORM_AUTO 0
 #define ORC_FORM_WZ 1
 #define ORC_FORM_EF 2
 
 typedef struct orc_opts {
-    int variant;        /* ORC_BJ or ORC_SCHUR */
-    int factor_B;       /* factor of the interior block (BJ: of the whole local block) */
-    int factor_S;       /* factor whose (2,2) blocks precondition the Schur system */
+    int variant;        /* ORC_BJ, ORC_SCHUR or ORC_RAP */
+    int factor_B;       /* factor of the interior block (BJ: of the whole local block;
+                           RAP: of the whole local block, the smoother) */
+    int factor_S;       /* factor whose (2,2) blocks precondition the Schur system
+                           (RAP: also the factor that gives R and P) */
     int form;           /* ORC_FORM_*: W/Z (one L_B and one U_B solve) or E/F */
     double ilut_tau;    /* ILUT relative drop tolerance */
     int ilut_p;         /* ILUT: entries kept per row in each of the L and U parts */

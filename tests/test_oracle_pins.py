@@ -579,3 +579,124 @@ def test_upwind_convection_diffusion_row():
     u = 3.0 * xs
     i = 2 + m * (2 + m * 2)                         # an interior node
     assert (A @ u)[i] == pytest.approx(bx * h * h * 3.0, rel=1e-12)
+
+
+# --------------------------------------------------------------------------------------
+# two-level multiplicative (RAP) preconditioner, Sec. 3.3
+
+
+def _rap_dense(o, A_orig, n):
+    """Dense pieces of the RAP preconditioner in the interior-first order, assembled from
+    the oracle's local factors: G = blockdiag((L_A U_A)^{-1}) from F1 (smoother), P and R
+    of Eq. wzinmilu and blockdiag(L_S U_S) from F2, and A permuted."""
+    pm = o.perm()
+    perm, n1 = pm["perm"], pm["n1"]
+    n2 = n - n1
+    Ap = A_orig.toarray()[np.ix_(perm, perm)]
+    G = np.zeros((n, n))
+    P_ = np.zeros((n, n2))
+    R_ = np.zeros((n2, n))
+    M = np.zeros((n2, n2))
+    for s in range(o.p):
+        rp, ci, a = o.local_csr(s)
+        ns = rp.size - 1
+        ni = pm["int_ptr"][s + 1] - pm["int_ptr"][s]
+        gI = pm["int_ptr"][s] + np.arange(ni)
+        gG = n1 + pm["if_ptr"][s] + np.arange(ns - ni)
+        glob = np.r_[gI, gG]
+        iG = gG - n1
+        F1 = sp.csr_matrix((o.local_factor(s, 1), ci, rp), shape=(ns, ns)).toarray()
+        F2 = sp.csr_matrix((o.local_factor(s, 2), ci, rp), shape=(ns, ns)).toarray()
+        L1, U1 = np.tril(F1, -1) + np.eye(ns), np.triu(F1)
+        L2, U2 = np.tril(F2, -1) + np.eye(ns), np.triu(F2)
+        G[np.ix_(glob, glob)] = np.linalg.inv(L1 @ U1)
+        LB, UB, W, Z = L2[:ni, :ni], U2[:ni, :ni], L2[ni:, :ni], U2[:ni, ni:]
+        P_[np.ix_(gG, iG)] = np.eye(ns - ni)
+        R_[np.ix_(iG, gG)] = np.eye(ns - ni)
+        if ni:
+            P_[np.ix_(gI, iG)] = -np.linalg.solve(UB, Z)
+            R_[np.ix_(iG, gI)] = -W @ np.linalg.inv(LB)
+        M[np.ix_(iG, iG)] = L2[ni:, ni:] @ U2[ni:, ni:]
+    return dict(Ap=Ap, G=G, P=P_, R=R_, M=M, perm=perm, n1=n1)
+
+
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "rand"])
+def test_rap_apply_is_the_multiplicative_formula(kind):
+    """Algorithm "Two-level multiplicative solve" with the GPU smoother of Algorithm
+    "Multiplicative RAP-ILU on GPU": with the coarse GMRES run to n2 steps the apply is
+    x = x^ + P (RAP)^{-1} R (b - A x^), x^ = blockdiag(L_A U_A)^{-1} b, built densely here
+    from the factors (ILU(0) smoother, MILU(0) for P, R and the coarse preconditioner)."""
+    pr = _small_dd(kind, seed=3)
+    A = pr.scipy()
+    n = pr.n
+    o0 = O.Oracle.from_problem(pr, variant="rap", factor_B="ilu0", factor_S="milu0")
+    n2 = o0.sizes().n2
+    assert n2 > 0
+    o = O.Oracle.from_problem(pr, variant="rap", factor_B="ilu0", factor_S="milu0", inner_iters=n2)
+    d = _rap_dense(o, A, n)
+    b = np.random.default_rng(5).standard_normal(n)
+    bn = b[d["perm"]]
+    xh = d["G"] @ bn
+    S = d["R"] @ d["Ap"] @ d["P"]
+    v = np.linalg.solve(S, d["R"] @ (bn - d["Ap"] @ xh))
+    xn = xh + d["P"] @ v
+    ref = np.empty(n)
+    ref[d["perm"]] = xn
+    got = o.apply(b)
+    np.testing.assert_allclose(got, ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
+
+
+def test_rap_smoother_alone_when_the_coarse_space_is_empty():
+    """A single subdomain has no interface, so the two-level multiplicative apply is the
+    smoother alone: global ILU(0) (Sec. 3.3, Algorithm "Two-level multiplicative solve"
+    with an empty coarse space), checked against scipy triangular solves."""
+    pr = P.aniso2d_boxes(12, 1, seed=2)
+    o = O.Oracle.from_problem(pr, variant="rap", factor_B="ilu0", factor_S="milu0")
+    assert o.sizes().n2 == 0
+    b = np.random.default_rng(6).standard_normal(pr.n)
+    rp, ci, v = pr.rowptr, pr.colind, pr.val
+    f, st, _ = O.ilu0(pr.n, rp, ci, v, milu=False)
+    assert st == 0
+    L, U = _split_lu(pr.n, rp, ci, f)
+    ref = spla.spsolve_triangular(U, spla.spsolve_triangular(L, b, lower=True), lower=False)
+    np.testing.assert_allclose(o.apply(b), ref, rtol=1e-12, atol=1e-13)
+
+
+def test_rap_keeps_constants_with_milu():
+    """Sec. 3.3 (Eq. miluwz3): with MILU(0) of A_i and interior rows of zero row sum,
+    P 1 = 1 and, subdomain by subdomain, R A_i P 1 = L_S U_S 1 (the coarse preconditioner
+    keeps the local operator's action on constants: R L = [0, L_S] and H 1 = 0), on a
+    periodic weighted graph Laplacian with 3 x 3 boxes."""
+    rng = np.random.default_rng(12)
+    m = 15
+    n = m * m
+    rows, cols, vals = [], [], []
+    for y in range(m):
+        for x in range(m):
+            i = x + m * y
+            for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                rows.append(i)
+                cols.append((x + dx) % m + m * ((y + dy) % m))
+                vals.append(-rng.uniform(0.5, 2.0))
+    W = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A = (W - sp.diags(np.asarray(W.sum(axis=1)).ravel())).tocsr()
+    A.sort_indices()
+    part, p = P.box_partition((m, m), (3, 3))
+    o = O.Oracle(*_mat_tuple(A), part, p, variant="rap", factor_B="ilu0", factor_S="milu0")
+    d = _rap_dense(o, A, n)
+    n2 = n - d["n1"]
+    one = np.ones(n2)
+    np.testing.assert_allclose(d["P"] @ one, np.ones(n), rtol=1e-9, atol=1e-9)
+    # blockdiag(A_i) in the interior-first order: A without the cross-subdomain couplings
+    pm = o.perm()
+    Aloc = np.zeros((n, n))
+    for s in range(p):
+        rp, ci, a = o.local_csr(s)
+        ns = rp.size - 1
+        ni = pm["int_ptr"][s + 1] - pm["int_ptr"][s]
+        glob = np.r_[pm["int_ptr"][s] + np.arange(ni), d["n1"] + pm["if_ptr"][s] + np.arange(ns - ni)]
+        Aloc[np.ix_(glob, glob)] = sp.csr_matrix((a, ci, rp), shape=(ns, ns)).toarray()
+    S_loc = d["R"] @ Aloc @ d["P"]
+    np.testing.assert_allclose(S_loc @ one, d["M"] @ one, rtol=1e-8, atol=1e-8)
+    # and the global operator annihilates constants here (zero row sums), unlike M
+    np.testing.assert_allclose(d["R"] @ d["Ap"] @ d["P"] @ one, 0.0, atol=1e-8)
