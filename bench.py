@@ -312,6 +312,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving sample in the default run (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--variant", default=None, choices=[None, "bj", "schur", "rap"],
+                    help="preconditioner variant override (rap: ILU(0) smoother, MILU(0) transfer)")
     ap.add_argument("--mode", default="solve", choices=["solve", "apply", "serve"],
                     help="apply: only time the preconditioner apply (used for kernel profiling)")
     ap.add_argument("--prec", default=None, choices=[None, "fp32", "fp64"])
@@ -357,6 +359,10 @@ def main():
 
     cfg = args.config
     sol, restart = solver_opts(cfg, args.prec or P.CONFIG_SOLVER[cfg]["prec"])
+    if args.variant:
+        sol["variant"] = args.variant
+        if args.variant == "rap":
+            sol.update(factor_B="ilu0", factor_S="milu0")
     prec = sol["pc_precision"]
     pr = P.make_config(cfg, seed=0)
     stream = torch.cuda.current_stream()
@@ -516,7 +522,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "n": pr.n, "nnz": pr.nnz, "p": pr.p,
+            "config": {"workload": workload_name(cfg), "variant": sol["variant"],
+                       "factors": f"{sol['factor_B']}+{sol['factor_S']}", "n": pr.n, "nnz": pr.nnz, "p": pr.p,
                        "restart": restart, "rtol": RTOL, "pc_precision": prec, "parallelism": f"replicas{world}",
                        "l2": "working set larger than L2 (FGMRES basis alone 0.8 GB)"},
             "time_to_rtol_s": time_to_rtol, "iters": info["iters"], "rel_res_true": relres,

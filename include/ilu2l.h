@@ -53,7 +53,11 @@ typedef struct {
     const double* val;     /* nnz */
 } ilu_csr;
 
-typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1 } ilu_variant;
+/* BJ: block Jacobi (Sec. 2.1). SCHUR: additive two-level (Algorithm "Additive SCHUR-ILU on
+   GPU"). RAP: multiplicative two-level (Algorithm "Multiplicative RAP-ILU on GPU", Sec. 3.3):
+   factor_B is the smoother on each whole local block (ILU(0) or MILU(0)), factor_S gives R,
+   P and the coarse preconditioner L_S U_S (MILU(0) in the paper); streamed path only. */
+typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1, ILU_VARIANT_RAP = 2 } ilu_variant;
 typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2 } ilu_fact;
 typedef enum { ILU_FORM_AUTO = 0, ILU_FORM_WZ = 1, ILU_FORM_EF = 2 } ilu_form;
 typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1 } ilu_prec;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libilu2l.so")
 ILU_OK, ILU_ERR_ARG, ILU_ERR_CSR, ILU_ERR_OOM, ILU_ERR_ZERO_PIVOT = 0, 1, 2, 3, 4
 ILU_ERR_NOT_CONVERGED, ILU_ERR_BREAKDOWN, ILU_ERR_TIMEOUT, ILU_ERR_CUDA = 5, 6, 7, 8
 ILU_ERR_TOO_LARGE, ILU_ERR_UNSUPPORTED = 9, 10
-VARIANTS = {"bj": 0, "schur": 1}
+VARIANTS = {"bj": 0, "schur": 1, "rap": 2}
 FACTORS = {"ilu0": 0, "milu0": 1, "ilut": 2}
 FORMS = {"auto": 0, "wz": 1, "ef": 2}
 PRECS = {"fp64": 0, "fp32": 1}

@@ -141,6 +141,12 @@ ilu_status device_setup_t(Handle& h) {
     h.d_iW0 = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
     h.d_iW1 = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
     if (!h.d_iV || !h.d_iW0 || !h.d_iW1) return map_err(e);
+    if (h.variant == ILU_VARIANT_RAP) {
+        h.rap_res = h.alloc<double>((size_t)std::max(n, 1), &e);
+        h.rap_pv = h.alloc<double>((size_t)std::max(n, 1), &e);
+        h.rap_apv = h.alloc<double>((size_t)std::max(n, 1), &e);
+        if (!h.rap_res || !h.rap_pv || !h.rap_apv) return map_err(e);
+    }
     cv.clear();
     cv.shrink_to_fit();
     if (h.stream_path) {
@@ -313,9 +319,34 @@ struct Scope {
     }
 };
 
+// Two-level multiplicative apply (Algorithm "Multiplicative RAP-ILU on GPU"):
+// x^ = smoother(r) into z; res = r - A x^; the forward program on res gives R res and
+// c = S~^{-1} R res; k GMRES steps on S~^{-1} R A P v = c, each P v, A (P v), R and S~^{-1},
+// then the Gram-Schmidt passes; z = x^ + P v.
+template <class T>
+cudaError_t apply_rap(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st, bool cap) {
+    cudaError_t e;
+    {
+        Scope sc(h, PC_APPLY_FWD, h.n2 > 0 ? 3 : 1, st, cap);
+        e = launch_bj_s<T>(h, r, z, done, st);
+        if (e == cudaSuccess && h.n2 > 0) e = launch_rap_resid(h, r, z, h.rap_res, done, st);
+        if (e == cudaSuccess && h.n2 > 0) e = launch_fwd_s<T>(h, h.rap_res, done, st);
+    }
+    if (e == cudaSuccess && h.n2 > 0) {
+        Scope sc(h, PC_INNER, 5 * h.inner_k, st, cap);
+        e = launch_rap_inner_s<T>(h, done, st);
+    }
+    if (e == cudaSuccess && h.n2 > 0) {
+        Scope sc(h, PC_APPLY_BWD, 1, st, cap);
+        e = launch_rap_fin_s<T>(h, z, done, st);
+    }
+    return e;
+}
+
 template <class T>
 cudaError_t apply_t(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st, bool cap) {
     const bool fast = h.stream_path;
+    if (h.variant == ILU_VARIANT_RAP) return apply_rap<T>(h, r, z, done, st, cap);
     if (h.variant == ILU_VARIANT_BJ) {
         Scope sc(h, PC_BJ, 1, st, cap);
         return fast ? launch_bj_s<T>(h, r, z, done, st) : launch_bj<T>(h, r, z, done, st);
@@ -447,7 +478,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
     else
         ilu_opts_default(&h->o);
     const ilu_opts& o = h->o;
-    if ((o.variant != ILU_VARIANT_BJ && o.variant != ILU_VARIANT_SCHUR) || o.factor_B < 0 || o.factor_B > 2 ||
+    if ((o.variant != ILU_VARIANT_BJ && o.variant != ILU_VARIANT_SCHUR && o.variant != ILU_VARIANT_RAP) ||
+        (o.variant == ILU_VARIANT_RAP && o.factor_B == ILU_FACT_ILUT) || o.factor_B < 0 || o.factor_B > 2 ||
         o.factor_S < 0 || o.factor_S > 1 || (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32) ||
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
@@ -456,7 +488,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         delete h;
         return ILU_ERR_ARG;
     }
-    if (o.ordering != 0) {
+    if (o.ordering != 0 || (o.variant == ILU_VARIANT_RAP && o.kernel_path != 0)) {
         delete h;
         return ILU_ERR_UNSUPPORTED;
     }
@@ -478,6 +510,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
             h->smem_optin = optin;
     }
     ilu_status s = host_setup(*h, A, part, p);
+    if (s == ILU_OK && h->variant == ILU_VARIANT_RAP && !h->stream_path) s = ILU_ERR_UNSUPPORTED;
     h->host_ms = now_ms() - t0;
     if (s == ILU_OK && o.analysis_only) {
         h->setup_ms = now_ms() - t0;

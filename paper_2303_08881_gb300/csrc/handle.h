@@ -71,6 +71,9 @@ struct Handle {
     double setup_ms = 0.0;
     double host_ms = 0.0, device_ms = 0.0;        // the two parts of setup_ms
     double solve_ms_last = 0.0, graph_ms_last = 0.0;  // last gmres_solve; its graph build
+    double* rap_res = nullptr;                    // multiplicative variant: b - A x^, P v and
+    double* rap_pv = nullptr;                     // A P v, full vectors in the original order
+    double* rap_apv = nullptr;
     double* fg_b = nullptr;                       // the solve's own copies of b and x: the
     double* fg_x = nullptr;                       // cycle graph is built once per handle
     int threads = 256;       // threads of the per-subdomain kernels

@@ -167,6 +167,13 @@ template <class T>
 cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st);
 template <class T>
 cudaError_t inner_coop_fits(const Handle& h, bool* fits);
+// multiplicative two-level variant (kernels_stream.cu, kernels_krylov.cu)
+cudaError_t launch_rap_resid(const Handle& h, const double* b, const double* x, double* out, const int32_t* done,
+                             cudaStream_t st);
+template <class T>
+cudaError_t launch_rap_inner_s(const Handle& h, const int32_t* done, cudaStream_t st);
+template <class T>
+cudaError_t launch_rap_fin_s(const Handle& h, double* z, const int32_t* done, cudaStream_t st);
 // inner solve on a caller-provided workspace (allocation-free entry point)
 template <class T>
 cudaError_t launch_inner_bc_ws(const Handle& h, const InnerDev<T>& in, int j, int second, cudaStream_t st);

@@ -386,6 +386,22 @@ __global__ void k_fg_update(FgDev f, int n, double* __restrict__ x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// out = b - A x (b null: out = A x), FP64, rows in the original order; a no-op once the
+// FGMRES cycle is done (the multiplicative apply's residual and coarse-operator SpMV)
+template <int VL>
+__global__ void k_rap_resid(CsrDev A, const double* __restrict__ b, const double* __restrict__ x,
+                            double* __restrict__ out, const int32_t* done) {
+    if (done && *done) return;
+    const int per_block = blockDim.x / VL;
+    const int sub = threadIdx.x / VL, sl = threadIdx.x & (VL - 1);
+    for (int base = blockIdx.x * per_block; base < A.n; base += gridDim.x * per_block) {
+        const int r = base + sub;
+        const bool valid = r < A.n;
+        const double s = row_dot<VL>(A, r, valid, x, sl);
+        if (valid && sl == 0) out[r] = b ? b[r] - s : s;
+    }
+}
+
 // Lanes per CSR row: every level of the lanes' shuffle reduction is one more FP64 add per
 // row, and FP64 issue is the scarce resource on GB300, so short rows get one lane each.
 static int pick_vl(const Handle& h) {
@@ -440,6 +456,15 @@ cudaError_t launch_spmv(const Handle& h, const double* x, double* y, cudaStream_
     const int vl = pick_vl(h);
     const int blocks = h.sm_count * 8;
     ILU2L_VL_SWITCH(vl, (k_spmv<V><<<blocks, 256, 0, st>>>(csr_of(h), x, y)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rap_resid(const Handle& h, const double* b, const double* x, double* out, const int32_t* done,
+                             cudaStream_t st) {
+    if (h.n == 0) return cudaSuccess;
+    const int vl = pick_vl(h);
+    const int blocks = h.sm_count * 8;
+    ILU2L_VL_SWITCH(vl, (k_rap_resid<V><<<blocks, 256, 0, st>>>(csr_of(h), b, x, out, done)));
     return cudaGetLastError();
 }
 

@@ -675,6 +675,123 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Multiplicative two-level variant (Sec. 3.3, Algorithm "Multiplicative RAP-ILU on GPU").
+// The coarse operator S v = R A P v is applied unformed: P v by the backward program on a
+// zero interior right-hand side (-U_B^{-1} Z v, v), A by the FP64 SpMV, R and S~^{-1} by the
+// forward program (L_B, the W rows, L_S, U_S), all from the factorisation defining R, P.
+
+// scatter-add of the local vector into the original ordering
+template <class T>
+__device__ __forceinline__ void scatter_add(double* __restrict__ z, const T* x, const int32_t* __restrict__ idx,
+                                            int n) {
+    for (int l = threadIdx.x; l < n; l += blockDim.x) z[idx[l]] += (double)x[l];
+}
+
+// step j, first part: v_j = W_in / ||W_in|| (stopping tests as in the additive inner
+// solve), P v_j by the backward program, scattered to a full vector in the original order
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_rap_p_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
+                                                 double* __restrict__ pv, T* xg, const int32_t* done) {
+    if (done && *done) return;
+    InnerCtl* ctl = in.ctl;
+    if (*((volatile int32_t*)&ctl->steps) >= 0 || *((volatile int32_t*)&ctl->zero)) return;
+    const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const double nrm = sqrt(warp_allsum_ldcg(in.part + ((size_t)2 * (kMaxInner + 1)) * p, p));
+    if (j == 0) {
+        if (s == 0 && threadIdx.x == 0) ctl->beta = nrm;
+        if (nrm == 0.0) {
+            if (s == 0 && threadIdx.x == 0) ctl->zero = 1;
+            return;
+        }
+    } else {
+        if (s == 0 && threadIdx.x == 0) ctl->H[(j - 1) * (kMaxInner + 1) + j] = nrm;
+        if (nrm <= 1e-14 * ctl->beta) {
+            if (s == 0 && threadIdx.x == 0) ctl->steps = j;
+            return;
+        }
+    }
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    T* x = xvec<T, XS>(sm, xg, q0);
+    const T inv = (T)(1.0 / nrm);
+    const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
+    const int g0 = sd.if_ptr[s];
+    for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)0;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const T v = Win[g0 + i] * inv;
+        in.V[(size_t)j * n2 + g0 + i] = v;
+        x[ni + i] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    scatter(pv, x, sd.q_orig + q0, ns);
+}
+
+// step j, second part: w = S~^{-1} R (A P v_j) by the forward program on the gathered
+// product, stored for the Gram-Schmidt passes, and the first dots V_i . w
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_rap_r_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
+                                                 const double* __restrict__ apv, T* xg, const int32_t* done) {
+    __shared__ double red[32 * 8];
+    if (done && *done) return;
+    const InnerCtl* ctl = in.ctl;
+    if (*((volatile const int32_t*)&ctl->steps) >= 0 || *((volatile const int32_t*)&ctl->zero)) return;
+    const int s = blockIdx.x, p = sd.p, n2 = sd.n2;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    T* x = xvec<T, XS>(sm, xg, q0);
+    gather(x, apv, sd.q_orig + q0, ns);
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    T* __restrict__ Wout = (j & 1) ? in.W0 : in.W1;
+    const int g0 = sd.if_ptr[s];
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) Wout[g0 + i] = x[ni + i];
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+        T acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] = (T)0;
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+            const T w = x[ni + i];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (i0 + u <= j) acc[u] += in.V[(size_t)(i0 + u) * n2 + g0 + i] * w;
+        }
+        block_sum_nt<T, 8>(acc, reinterpret_cast<T*>(red));
+        if (threadIdx.x == 0)
+            for (int u = 0; u < 8 && i0 + u <= j; u++) in.part[((size_t)(i0 + u)) * p + s] = (double)acc[u];
+    }
+}
+
+// last part: y = V t (least squares of the coarse GMRES), z = x^ + P y
+template <class T, int RW, bool XS>
+__global__ void __launch_bounds__(256) k_rap_fin_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
+                                                   double* __restrict__ z, T* xg, const int32_t* done) {
+    __shared__ double tt[kMaxInner];
+    if (done && *done) return;
+    const int s = blockIdx.x;
+    const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
+    const Smem sm = smem_parts(cfg.nst, S.chunk);
+    ring_start(S, s, sm, cfg.nst);
+    const int steps = inner_lsq(in.ctl, in.part, sd.p, in.k, tt);
+    T* x = xvec<T, XS>(sm, xg, q0);
+    const int g0 = sd.if_ptr[s];
+    for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)0;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        T y = (T)0;
+        for (int u = 0; u < steps; u++) y += (T)tt[u] * in.V[(size_t)u * sd.n2 + g0 + i];
+        x[ni + i] = y;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    __syncthreads();
+    scatter_add(z, x, sd.q_orig + q0, ns);
+}
+
 template <class T, int RW, bool XS>
 __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
                                                const double* __restrict__ r, const T* __restrict__ fq, int ef,
@@ -808,6 +925,9 @@ static cudaError_t configure_stream_t() {
     if (e == cudaSuccess) e = raise_smem_limit(k_bwd_s<T, RW, XS>);
     if (e == cudaSuccess) e = raise_smem_limit(k_inner_start_s<T, RW, XS>);
     if (e == cudaSuccess) e = raise_smem_limit(k_inner_coop<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_p_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_r_s<T, RW, XS>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_fin_s<T, RW, XS>);
     return e;
 }
 
@@ -953,6 +1073,37 @@ cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, 
     return e;
 }
 
+template <class T>
+cudaError_t launch_rap_inner_s(const Handle& h, const int32_t* done, cudaStream_t st) {
+    if (h.n2 == 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < h.inner_k && e == cudaSuccess; j++) {
+        ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_p_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                          h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), j, h.rap_pv,
+                                          (T*)h.d_xg, done)));
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_rap_resid(h, nullptr, h.rap_pv, h.rap_apv, done, st);
+        if (e == cudaSuccess) {
+            ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_rap_r_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                               h.sub(), sdev<T>(h, PR_FWDS), rcfg(h), h.innerdev<T>(), j,
+                                               h.rap_apv, (T*)h.d_xg, done)));
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = launch_inner_bc<T>(h, j, 0, done, st);
+        if (e == cudaSuccess) e = launch_inner_bc<T>(h, j, 1, done, st);
+    }
+    return e;
+}
+
+template <class T>
+cudaError_t launch_rap_fin_s(const Handle& h, double* z, const int32_t* done, cudaStream_t st) {
+    if (h.n2 == 0) return cudaSuccess;
+    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_fin_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+                                      h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), z, (T*)h.d_xg,
+                                      done)));
+    return cudaGetLastError();
+}
+
 #define ILU2L_SINST(T)                                                                                      \
     template cudaError_t launch_inner_io_ws<T>(const Handle&, const InnerDev<T>&, T*, const double*,         \
                                                double*, cudaStream_t);                                       \
@@ -966,7 +1117,9 @@ cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, 
     template cudaError_t launch_bwd_s<T>(const Handle&, const double*, double*, const int32_t*,            \
                                          cudaStream_t);                                                    \
     template cudaError_t launch_inner_start_s<T>(const Handle&, const double*, cudaStream_t);             \
-    template cudaError_t inner_coop_fits<T>(const Handle&, bool*);
+    template cudaError_t inner_coop_fits<T>(const Handle&, bool*);                                       \
+    template cudaError_t launch_rap_inner_s<T>(const Handle&, const int32_t*, cudaStream_t);             \
+    template cudaError_t launch_rap_fin_s<T>(const Handle&, double*, const int32_t*, cudaStream_t);
 ILU2L_SINST(float)
 ILU2L_SINST(double)
 

@@ -554,7 +554,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
 void host_levels(Handle& h) {
     if (h.lev_ready) return;
     const int32_t n = h.n, p = h.p;
-    const bool schur = (h.variant == ILU_VARIANT_SCHUR);
+    const bool schur = (h.variant != ILU_VARIANT_BJ);  // two-level structure
     for (int w = 0; w < 6; w++) {
         h.lev[w].assign(n, -1);
         h.nlev[w] = 0;
@@ -718,7 +718,8 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     apat.rp = h.q_rp;
     apat.ci = h.q_ci;
     apat.dpos = h.q_dpos;
-    const bool schur = (h.variant == ILU_VARIANT_SCHUR);
+    const bool schur = (h.variant != ILU_VARIANT_BJ);  // two-level structure (SCHUR, RAP)
+    const bool rap = (h.variant == ILU_VARIANT_RAP);
     const bool f1_ilut = (h.kB == ILU_FACT_ILUT);
     h.f1_device = !f1_ilut;
     if (!f1_ilut) {
@@ -822,21 +823,25 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
             N.sub_lvl.push_back((int32_t)N.lvl_ptr.size() - 1);
             N.max_levels = std::max(N.max_levels, nl);
         }
-        if (!schur) {
+        if (!schur || rap) {  // block Jacobi, or the smoother of the multiplicative variant
             ProgHost& P = h.prog[PR_BJ];
             int a = prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, false, 0, lev);
             a += prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, true, 0, lev);
             P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
             P.max_levels = std::max(P.max_levels, a);
-        } else {
+        }
+        if (schur) {
+            // the B parts (L_B, U_B, W, Z): factor_B's factorisation for SCHUR; for RAP the
+            // factorisation that defines R and P (Eq. wzinmilu), factor_S's
+            const FPat& fb = rap ? h.f2 : h.f1;
             {   // forward: f' = L_B^{-1} f then g' = g - W f'   (W/Z)
                 //          t = U_B^{-1} L_B^{-1} f then g' = g - E t   (E/F)
                 ProgHost& P = h.prog[PR_FWD];
-                int a = prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
                 if (wz) {
-                    a += prog_add_single(P, h.f1, q0, ni, ns, 0, ni, 0);
+                    a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
                 } else {
-                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                    a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
                     a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
                 }
                 P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
@@ -844,11 +849,11 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
             }
             {   // forward and the first local Schur solve in one program (base 0)
                 ProgHost& P = h.prog[PR_FWDS];
-                int a = prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
                 if (wz) {
-                    a += prog_add_single(P, h.f1, q0, ni, ns, 0, ni, 0);
+                    a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
                 } else {
-                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                    a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
                     a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
                 }
                 a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
@@ -867,12 +872,12 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 ProgHost& P = h.prog[PR_BWD];
                 int a = 0;
                 if (wz) {
-                    a += prog_add_single(P, h.f1, q0, 0, ni, ni, ns, 0);
+                    a += prog_add_single(P, fb, q0, 0, ni, ni, ns, 0);
                 } else {
                     a += prog_add_single(P, apat, q0, 0, ni, ni, ns, 0);
-                    a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, false, 0, lev);
+                    a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
                 }
-                a += prog_add_tri(P, h.f1, q0, 0, ni, 0, ni, true, 0, lev);
+                a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
                 P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                 P.max_levels = std::max(P.max_levels, a);
             }
@@ -883,7 +888,9 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         h.idx_bytes = 4;
         if ((int64_t)(h.max_ns + 1) * (h.prec == ILU_PREC_FP32 ? 4 : 8) >= (1 << 24)) h.stream_path = false;
         const int vb = (h.prec == ILU_PREC_FP32) ? 4 : 8;
-        std::vector<int> ids = schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD} : std::vector<int>{PR_BJ};
+        std::vector<int> ids = rap     ? std::vector<int>{PR_BJ, PR_FWDS, PR_BWD}
+                               : schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD}
+                                       : std::vector<int>{PR_BJ};
         // consumer group: enough warps for nine levels in ten to run as a single wave
         // (a wave costs about one row's latency whatever its width), at most 128 threads
         for (int id : ids) {

@@ -279,6 +279,63 @@ def test_working_vector_in_shared_memory_for_the_2d_boxes(ilu):
     h.close()
 
 
+RAP = dict(variant="rap", factor_B="ilu0", factor_S="milu0")
+
+
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "cuts3d", "rand", "p1", "dense_rows"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_rap_apply_matches_oracle(ilu, name, prec, k):
+    """Multiplicative two-level apply (Algorithm "Multiplicative RAP-ILU on GPU"): ILU(0)
+    smoother, R and P from MILU(0), k coarse GMRES steps preconditioned by L_S U_S."""
+    pr = _prob(name)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_iters=k, **RAP))
+    orc = O.Oracle.from_problem(pr, inner_iters=k, **RAP)
+    assert h.stats()["stream_path"]
+    r = np.random.default_rng(19).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    got, ref = z.cpu().numpy(), orc.apply(r)
+    assert np.isfinite(got).all() and h.stats()["device_error"] == 0
+    if prec == "fp64":
+        _assert_close64(got, ref, f"rap apply {name}")
+    else:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL32
+    z2 = torch.empty_like(z)
+    ilu.ilu_apply(h, _dev(r), z2)
+    torch.cuda.synchronize()
+    assert torch.equal(z, z2)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rap_fgmres_matches_oracle(ilu, prec):
+    pr = _prob("aniso2d_ragged")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, **RAP))
+    orc = O.Oracle.from_problem(pr, **RAP)
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros_like(b)
+    info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=2000)
+    ro = orc.fgmres(pr.b, rtol=1e-8, restart=30, maxit=2000)
+    xo, it_o = ro["x"], ro["iters"]
+    assert ro["status"] == 0
+    assert info["status"] == 0 and info["rel_res_true"] <= 1e-8
+    if prec == "fp64":
+        assert abs(info["iters"] - it_o) <= 1
+    else:
+        assert abs(info["iters"] - it_o) <= max(2, it_o // 10)
+    np.testing.assert_allclose(x.cpu().numpy(), xo, rtol=0, atol=1e-6 * np.abs(xo).max())
+    h.close()
+
+
+def test_rap_needs_the_streamed_path(ilu):
+    pr = _prob("aniso2d_ragged")
+    with pytest.raises(ilu.IluError) as e:
+        ilu.ilu_setup_problem(pr, ilu.Opts(kernel_path="generic", **RAP))
+    assert e.value.status == ilu.ILU_ERR_UNSUPPORTED
+
+
 def test_apply_of_zero_is_zero(ilu):
     pr, h, orc = _pair(ilu, "aniso2d_ragged", CONFIGS[2], "fp32")
     z = torch.full((pr.n,), 7.0, dtype=torch.float64, device="cuda")

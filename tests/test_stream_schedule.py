@@ -30,6 +30,7 @@ CFGS = [
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0"),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0"),
     dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
+    dict(variant="rap", factor_B="ilu0", factor_S="milu0"),
 ]
 SKIP = 1 << 31
 BARRIER = 1 << 31
@@ -130,7 +131,7 @@ def test_stretches_are_race_free(ilu, name, cfg):
     pr = CASES[name]()
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **cfg))
     sizes = h.sizes()
-    progs = ["bj"] if cfg["variant"] == "bj" else ["fwd", "s", "bwd"]
+    progs = {"bj": ["bj"], "schur": ["fwd", "s", "bwd"], "rap": ["bj", "fwd", "bwd"]}[cfg["variant"]]
     for prog in progs:
         st = h.stream(prog)
         subs = parse(st)
