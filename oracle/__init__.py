@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "liborc.so")
 ILU0, MILU0, ILUT, EXACT = 0, 1, 2, 3
 BJ, SCHUR, RAP = 0, 1, 2
 FORM_AUTO, FORM_WZ, FORM_EF = 0, 1, 2
+ORDER_NATURAL, ORDER_RCM = 0, 1
 OK, ERR_ARG, ERR_CSR, ERR_OOM, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 
 _FACT = {"ilu0": ILU0, "milu0": MILU0, "ilut": ILUT, "exact": EXACT}
@@ -40,7 +41,7 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("factor_B", C.c_int), ("factor_S", C.c_int),
                 ("form", C.c_int), ("ilut_tau", C.c_double), ("ilut_p", C.c_int),
-                ("inner_iters", C.c_int), ("pivot_eps", C.c_double)]
+                ("inner_iters", C.c_int), ("pivot_eps", C.c_double), ("local_order", C.c_int)]
 
 
 _lib = None
@@ -66,6 +67,7 @@ def lib():
             "orc_levels_csr": (I, [I, P, P, I, P]),
             "orc_classify": (I, [I, P, P, P, I, P]),
             "orc_permutation": (I, [I, P, I, P, P, P, P, P]),
+            "orc_rcm": (I, [I, P, P, P]),
             "orc_opts_default": (None, [P]),
             "orc_setup": (P, [I, P, P, P, P, I, P, P]),
             "orc_free": (None, [P]),
@@ -175,6 +177,17 @@ def classify(n, rowptr, colind, part, p):
     return iface
 
 
+def rcm(n, rowptr, colind):
+    """Reverse Cuthill-McKee order of the symmetrised graph of a square pattern:
+    order[k] = the node placed k-th."""
+    rowptr, colind = _i32(rowptr), _i32(colind)
+    order = np.empty(n, np.int32)
+    st = lib().orc_rcm(int(n), _p(rowptr), _p(colind), _p(order))
+    if st != OK:
+        raise RuntimeError(f"rcm status {st}")
+    return order
+
+
 def permutation(n, part, p, iface):
     part, iface = _i32(part), _i32(iface)
     perm = np.empty(n, np.int32)
@@ -206,7 +219,7 @@ class Oracle:
 
     def __init__(self, n, rowptr, colind, val, part, p, variant="schur", factor_B="ilu0",
                  factor_S="milu0", form="auto", ilut_tau=1e-3, ilut_p=10, inner_iters=3,
-                 pivot_eps=1e-8):
+                 pivot_eps=1e-8, local_order="natural"):
         self._keep = [_i32(rowptr), _i32(colind), _f64(val), _i32(part)]
         o = _Opts()
         lib().orc_opts_default(C.byref(o))
@@ -218,6 +231,7 @@ class Oracle:
         o.ilut_p = int(ilut_p)
         o.inner_iters = int(inner_iters)
         o.pivot_eps = pivot_eps
+        o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM}[local_order]
         self.opts = o
         st = C.c_int(0)
         rp, ci, v, pt = self._keep

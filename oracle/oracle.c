@@ -511,6 +511,158 @@ int orc_classify(int n, const int* rp, const int* ci, const int* part, int p, in
     return ORC_OK;
 }
 
+/* Reverse Cuthill-McKee (Sec. 3.1: the local block is put in RCM order before its ILU).
+   The graph is that of the pattern made symmetric: i ~ j when a_ij or a_ji is stored and
+   i != j; deg(i) = number of distinct neighbours. Cuthill-McKee is a breadth-first search:
+   each node taken from the front of the sequence appends its not yet placed neighbours in
+   increasing (degree, index). Readings (the paper names the method only): a connected
+   component starts at its not yet placed node of smallest (degree, index); the complete
+   sequence over all components is reversed at the end. order[k] = node placed k-th. */
+typedef struct {
+    int deg;
+    int idx;
+} degidx_t;
+
+static int degidx_cmp(const void* a, const void* b) {
+    const degidx_t* x = (const degidx_t*)a;
+    const degidx_t* y = (const degidx_t*)b;
+    if (x->deg != y->deg) return (x->deg < y->deg) ? -1 : 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+static int int_cmp(const void* a, const void* b) {
+    int x = *(const int*)a, y = *(const int*)b;
+    return (x < y) ? -1 : (x > y);
+}
+
+int orc_rcm(int n, const int* rp, const int* ci, int* order) {
+    if (n <= 0) return ORC_OK;
+    int st = ORC_OK;
+    int* cnt = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* deg = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* seen = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* cm = (int*)malloc(((size_t)n + 1) * sizeof(int));
+    degidx_t* start = (degidx_t*)malloc(((size_t)n + 1) * sizeof(degidx_t));
+    degidx_t* buf = (degidx_t*)malloc(((size_t)n + 1) * sizeof(degidx_t));
+    int* adj = NULL;
+    if (!cnt || !deg || !seen || !cm || !start || !buf) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    /* adjacency lists of the symmetrised graph: both directions of every stored
+       off-diagonal entry, then each list sorted and duplicates removed */
+    for (int i = 0; i < n; i++)
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+            if (ci[q] != i) {
+                cnt[i + 1]++;
+                cnt[ci[q] + 1]++;
+            }
+    for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    adj = (int*)malloc(((size_t)cnt[n] + 1) * sizeof(int));
+    if (!adj) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int i = 0; i < n; i++) deg[i] = cnt[i]; /* fill positions */
+    for (int i = 0; i < n; i++)
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+            if (ci[q] != i) {
+                adj[deg[i]++] = ci[q];
+                adj[deg[ci[q]]++] = i;
+            }
+    for (int i = 0; i < n; i++) {
+        int a = cnt[i], b = cnt[i + 1], u = a;
+        qsort(adj + a, (size_t)(b - a), sizeof(int), int_cmp);
+        for (int t = a; t < b; t++)
+            if (t == a || adj[t] != adj[t - 1]) adj[u++] = adj[t];
+        deg[i] = u - a; /* the distinct neighbours are adj[cnt[i] .. cnt[i] + deg[i]) */
+    }
+    for (int i = 0; i < n; i++) {
+        start[i].deg = deg[i];
+        start[i].idx = i;
+    }
+    qsort(start, (size_t)n, sizeof(degidx_t), degidx_cmp);
+    int placed = 0, next_start = 0;
+    while (placed < n) {
+        while (seen[start[next_start].idx]) next_start++;
+        int s = start[next_start].idx;
+        seen[s] = 1;
+        cm[placed++] = s;
+        for (int head = placed - 1; head < placed; head++) {
+            int u = cm[head], nb = 0;
+            for (int t = cnt[u]; t < cnt[u] + deg[u]; t++) {
+                int v = adj[t];
+                if (!seen[v]) {
+                    seen[v] = 1;
+                    buf[nb].deg = deg[v];
+                    buf[nb++].idx = v;
+                }
+            }
+            qsort(buf, (size_t)nb, sizeof(degidx_t), degidx_cmp);
+            for (int t = 0; t < nb; t++) cm[placed++] = buf[t].idx;
+        }
+    }
+    for (int k = 0; k < n; k++) order[k] = cm[n - 1 - k];
+done:
+    free(cnt);
+    free(deg);
+    free(seen);
+    free(cm);
+    free(start);
+    free(buf);
+    free(adj);
+    return st;
+}
+
+/* Put the nodes perm[g0 .. g0 + m) of one group in RCM order of the graph they induce
+   (the pattern of A restricted to the group, with local labels in the current order). */
+static int rcm_group(const csr_t* A, int* perm, int* iperm, int g0, int m, int* lab) {
+    if (m <= 1) return ORC_OK;
+    int st = ORC_OK;
+    int* grp = (int*)malloc((size_t)m * sizeof(int));
+    int* srp = (int*)calloc((size_t)m + 1, sizeof(int));
+    int* ord = (int*)malloc((size_t)m * sizeof(int));
+    int* sci = NULL;
+    if (!grp || !srp || !ord) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int k = 0; k < m; k++) {
+        grp[k] = perm[g0 + k];
+        lab[grp[k]] = k;
+    }
+    for (int k = 0; k < m; k++) {
+        int i = grp[k], c = 0;
+        for (int q = A->rp[i]; q < A->rp[i + 1]; q++)
+            if (lab[A->ci[q]] >= 0) c++;
+        srp[k + 1] = srp[k] + c;
+    }
+    sci = (int*)malloc(((size_t)srp[m] + 1) * sizeof(int));
+    if (!sci) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int k = 0, at = 0; k < m; k++) {
+        int i = grp[k];
+        for (int q = A->rp[i]; q < A->rp[i + 1]; q++)
+            if (lab[A->ci[q]] >= 0) sci[at++] = lab[A->ci[q]];
+    }
+    st = orc_rcm(m, srp, sci, ord);
+    if (!st)
+        for (int k = 0; k < m; k++) {
+            perm[g0 + k] = grp[ord[k]];
+            iperm[grp[ord[k]]] = g0 + k;
+        }
+done:
+    if (grp)
+        for (int k = 0; k < m; k++) lab[grp[k]] = -1;
+    free(grp);
+    free(srp);
+    free(ord);
+    free(sci);
+    return st;
+}
+
 /* Interior-first relabelling (Fig. DD, Eq. equ22): the new order lists the interior
    nodes grouped by subdomain, then the interface nodes grouped by subdomain, each group
    in ascending original index. perm[new] = old, iperm[old] = new; interior nodes of
@@ -579,6 +731,7 @@ void orc_opts_default(orc_opts* o) {
     o->ilut_p = 10;
     o->inner_iters = 3;
     o->pivot_eps = 1e-8;
+    o->local_order = ORC_ORDER_NATURAL;
 }
 
 static inline int nint_of(const orc_t* h, int s) { return h->int_ptr[s + 1] - h->int_ptr[s]; }
@@ -691,11 +844,35 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
     }
     memcpy(h->part, part, (size_t)n * sizeof(int));
 
-    /* Sec. 2.2.1: classify and relabel */
+    /* Sec. 2.2.1: classify and relabel. Block Jacobi (Sec. 2.1, Algorithm "Block Jacobi
+       ILU on GPU") factors the whole A_s: it has no interface, every node of a subdomain
+       is in one group. */
+    if (h->o.local_order != ORC_ORDER_NATURAL && h->o.local_order != ORC_ORDER_RCM) {
+        st = ORC_ERR_ARG;
+        goto fail;
+    }
     st = orc_classify(n, rp, ci, part, p, h->iface);
     if (st) goto fail;
+    if (h->o.variant == ORC_BJ)
+        for (int i = 0; i < n; i++) h->iface[i] = 0;
     h->n1 = orc_permutation(n, part, p, h->iface, h->perm, h->iperm, h->int_ptr, h->if_ptr);
     h->n2 = n - h->n1;
+    /* Sec. 3.1: RCM order inside each group (BJ: all of A_s; two-level: the interior
+       nodes, then the interface nodes, so that A_s keeps its [B F; E C] form) */
+    if (h->o.local_order == ORC_ORDER_RCM) {
+        int* lab = (int*)malloc(((size_t)n + 1) * sizeof(int));
+        if (!lab) {
+            st = ORC_ERR_OOM;
+            goto fail;
+        }
+        for (int i = 0; i < n; i++) lab[i] = -1;
+        for (int s = 0; s < p && !st; s++) {
+            st = rcm_group(&h->A, h->perm, h->iperm, h->int_ptr[s], nint_of(h, s), lab);
+            if (!st) st = rcm_group(&h->A, h->perm, h->iperm, h->n1 + h->if_ptr[s], nif_of(h, s), lab);
+        }
+        free(lab);
+        if (st) goto fail;
+    }
 
     /* Eq. localA: local blocks A_s = [B_s F_s; E_s C_s], and C_off (Eq. SS) */
     h->Aloc = (csr_t*)calloc((size_t)p, sizeof(csr_t));
@@ -705,10 +882,11 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
         goto fail;
     }
     {
-        int coff_cnt = 0;
+        int coff_cnt = 0; /* couplings of interface rows (none for block Jacobi) */
         for (int i = 0; i < n; i++)
-            for (int q = rp[i]; q < rp[i + 1]; q++)
-                if (part[ci[q]] != part[i]) coff_cnt++;
+            if (h->iface[i])
+                for (int q = rp[i]; q < rp[i + 1]; q++)
+                    if (part[ci[q]] != part[i]) coff_cnt++;
         st = csr_init(&h->Coff, h->n2, h->n2, coff_cnt);
         if (st) goto fail;
         int* cnt = (int*)calloc((size_t)p, sizeof(int));

@@ -43,6 +43,9 @@ extern "C" {
 #define ORC_FORM_AUTO 0
 #define ORC_FORM_WZ 1
 #define ORC_FORM_EF 2
+/* local order of each group of a subdomain (Sec. 3.1) */
+#define ORC_ORDER_NATURAL 0   /* ascending original index */
+#define ORC_ORDER_RCM 1       /* reverse Cuthill-McKee of the group's graph */
 
 typedef struct orc_opts {
     int variant;        /* ORC_BJ, ORC_SCHUR or ORC_RAP */
@@ -55,6 +58,10 @@ typedef struct orc_opts {
     int ilut_p;         /* ILUT: entries kept per row in each of the L and U parts */
     int inner_iters;    /* GMRES steps on the preconditioned Schur system */
     double pivot_eps;   /* small-pivot perturbation, relative to the row's max |a_ij| */
+    int local_order;    /* ORC_ORDER_*: order inside each group. Groups: block Jacobi, the
+                           whole subdomain (no interior / interface split, Sec. 2.1); the
+                           two-level variants, the interior and the interface nodes of each
+                           subdomain (Sec. 2.2.1) */
 } orc_opts;
 
 /* ---- primitives on one CSR matrix ---- */
@@ -84,6 +91,9 @@ int orc_levels_csr(int n, const int* rowptr, const int* colind, int upper, int* 
 /* ---- domain decomposition ---- */
 int orc_classify(int n, const int* rowptr, const int* colind, const int* part, int p,
                  int* iface);
+/* Reverse Cuthill-McKee order of the symmetrised graph of a square pattern (i ~ j when
+   a_ij or a_ji is stored, i != j): order[k] = the node placed k-th. */
+int orc_rcm(int n, const int* rowptr, const int* colind, int* order);
 /* returns n1 (number of interior unknowns) */
 int orc_permutation(int n, const int* part, int p, const int* iface, int* perm, int* iperm,
                     int* int_ptr, int* if_ptr);

@@ -309,11 +309,14 @@ def test_classification_and_permutation_properties(seed):
 
 def test_structural_counts_of_the_2d_workload():
     """64x64 5-point Poisson on 2x2 boxes: interface = the two grid lines next to each cut
-    (each box side has 32 nodes): n2 = 4*2*32 - 4 = 252, n1 = 4096 - 252."""
+    (each box side has 32 nodes): n2 = 4*2*32 - 4 = 252, n1 = 4096 - 252. Block Jacobi
+    factors whole blocks (Sec. 2.1): no interface, no C_off."""
     pr = P.make_config("1")
-    o = O.Oracle.from_problem(pr, variant="bj", factor_B="ilu0", factor_S="ilu0")
+    o = O.Oracle.from_problem(pr, variant="schur", factor_B="ilu0", factor_S="milu0")
     s = o.sizes()
     assert (s.n, s.nnz, s.n1, s.n2, s.nnz_coff) == (4096, 20224, 3844, 252, 256)
+    s = O.Oracle.from_problem(pr, variant="bj", factor_B="ilu0", factor_S="ilu0").sizes()
+    assert (s.n, s.nnz, s.n1, s.n2, s.nnz_coff) == (4096, 20224, 4096, 0, 0)
 
 
 # --------------------------------------------------------------------------------------
@@ -459,9 +462,7 @@ def test_bj_apply_is_blockwise_ilu0():
     zz = np.zeros(pr.n)
     for s in range(pr.p):
         idx = np.nonzero(pr.part == s)[0]
-        pm = o.perm()
-        # local order: interior nodes then interface nodes, each ascending
-        idx = np.concatenate([idx[pm["iface"][idx] == 0], idx[pm["iface"][idx] == 1]])
+        # block Jacobi has no interface: the local order is the subdomain's nodes ascending
         Ai = A[idx][:, idx].tocsr()
         Ai.sort_indices()
         f, _, _ = O.ilu0(idx.size, Ai.indptr, Ai.indices, Ai.data)
@@ -469,6 +470,154 @@ def test_bj_apply_is_blockwise_ilu0():
         zz[idx] = spla.spsolve_triangular(U, spla.spsolve_triangular(L, r[idx], lower=True),
                                           lower=False)
     np.testing.assert_allclose(z, zz, rtol=1e-12, atol=1e-13)
+
+
+# --------------------------------------------------------------------------------------
+# RCM local order (Sec. 3.1)
+
+
+def _sym_pattern(n, edges):
+    rows = [a for a, b in edges] + [b for a, b in edges]
+    cols = [b for a, b in edges] + [a for a, b in edges]
+    G = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    G.sum_duplicates()
+    G.sort_indices()
+    return G
+
+
+def _random_graph_with_unique_start(n, extra, seed):
+    """connected random graph whose every node has degree >= 2, plus one pendant node:
+    the pendant is then the unique node of least degree"""
+    rng = np.random.default_rng(seed)
+    lab = rng.permutation(n)
+    edges = [(lab[k], lab[rng.integers(0, k)]) for k in range(1, n)]  # random tree
+    edges += [tuple(rng.choice(n, 2, replace=False)) for _ in range(extra)]
+    while True:
+        deg = np.diff(_sym_pattern(n, edges).indptr)
+        low = np.nonzero(deg < 2)[0]
+        if low.size == 0:
+            break
+        for i in low:
+            edges.append((int(i), int((i + 1 + rng.integers(0, n - 1)) % n)))
+    edges.append((n, int(rng.integers(0, n))))
+    return _sym_pattern(n + 1, edges)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_rcm_equals_scipy_when_the_start_node_is_unique(seed):
+    """scipy.sparse.csgraph.reverse_cuthill_mckee starts each component at a node of least
+    degree and appends neighbours by degree, keeping their index order on ties; with a
+    unique least-degree node the two orders must agree node for node."""
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    G = _random_graph_with_unique_start(60 + 40 * seed, 30 + 50 * seed, seed)
+    deg = np.diff(G.indptr)
+    assert np.sum(deg == deg.min()) == 1
+    got = O.rcm(G.shape[0], G.indptr, G.indices)
+    ref = reverse_cuthill_mckee(G, symmetric_mode=True)
+    assert np.array_equal(got, ref)
+
+
+def test_rcm_of_a_grid_with_a_pendant_equals_scipy_and_is_banded():
+    """5-point grid 23 x 9 with one pendant node: same order as scipy, and (Cuthill-McKee
+    being a breadth-first search from the start node, which RCM puts last) the graph
+    distance from the start never increases along the RCM order."""
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    mx, my = 23, 9
+    n, rp, ci, _ = P.poisson2d_5pt(mx, my)
+    A = sp.csr_matrix((np.ones(rp[n]), ci, rp), shape=(n, n)).tolil()
+    A.resize((n + 1, n + 1))
+    A[n, 5 + mx * 4] = 1.0
+    A[5 + mx * 4, n] = 1.0
+    G = A.tocsr()
+    G.setdiag(0)
+    G.eliminate_zeros()
+    G.sort_indices()
+    got = O.rcm(n + 1, G.indptr, G.indices)
+    assert np.array_equal(got, reverse_cuthill_mckee(G, symmetric_mode=True))
+    from scipy.sparse.csgraph import shortest_path
+    assert got[-1] == n  # the pendant, the only node of degree 1
+    d = shortest_path(G, unweighted=True, indices=n)
+    assert np.all(np.diff(d[got]) <= 0)
+
+
+def test_rcm_hand_worked_with_ties_and_components():
+    """A 12-node pattern worked by hand (tests/golden/rcm_hand.json): degree ties broken by
+    index, degree before index among neighbours, three components, entries stored in one
+    direction only, duplicates and diagonal entries ignored."""
+    g = json.load(open(os.path.join(GOLD, "rcm_hand.json")))
+    n = g["n"]
+    r = [a for a, b in g["stored"]]
+    c = [b for a, b in g["stored"]]
+    M = sp.csr_matrix((np.ones(len(r)), (r, c)), shape=(n, n))
+    M.sort_indices()
+    S = ((M + M.T) > 0).astype(float).tolil()
+    S.setdiag(0)
+    S = S.tocsr()
+    S.eliminate_zeros()
+    assert list(np.diff(S.indptr)) == g["degrees"]
+    assert list(O.rcm(n, M.indptr, M.indices)) == g["order"]
+
+
+def test_rcm_depends_only_on_the_symmetrised_graph():
+    M = _rand_sparse(80, 0.04, seed=9)
+    S = (abs(M) + abs(M).T).tocsr()
+    S.sort_indices()
+    a = O.rcm(80, M.indptr, M.indices)
+    assert np.array_equal(np.sort(a), np.arange(80))
+    assert np.array_equal(a, O.rcm(80, S.indptr, S.indices))
+
+
+def test_bj_rcm_apply_is_blockwise_ilu0_in_rcm_order():
+    """Algorithm 'Block Jacobi ILU on GPU': each A_i put in its RCM order, ILU(0) of the
+    reordered block, two triangular solves, scattered back (scipy solves)."""
+    pr = P.convdiff3d_boxes(8, 2)
+    o = O.Oracle.from_problem(pr, variant="bj", factor_B="ilu0", local_order="rcm")
+    perm = o.perm()["perm"]
+    r = np.random.default_rng(4).standard_normal(pr.n)
+    z = o.apply(r)
+    A = pr.scipy()
+    zz = np.zeros(pr.n)
+    at = 0
+    for s in range(pr.p):
+        nat = np.nonzero(pr.part == s)[0]
+        B = A[nat][:, nat].tocsr()
+        B.sort_indices()
+        idx = nat[O.rcm(nat.size, B.indptr, B.indices)]
+        assert np.array_equal(perm[at:at + idx.size], idx)
+        at += idx.size
+        Ai = A[idx][:, idx].tocsr()
+        Ai.sort_indices()
+        f, _, _ = O.ilu0(idx.size, Ai.indptr, Ai.indices, Ai.data)
+        L, U = _split_lu(idx.size, Ai.indptr, Ai.indices, f)
+        zz[idx] = spla.spsolve_triangular(U, spla.spsolve_triangular(L, r[idx], lower=True),
+                                          lower=False)
+    np.testing.assert_allclose(z, zz, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "rand"])
+def test_two_level_rcm_orders_each_group_and_stays_exact(kind):
+    """Two-level with the RCM local order: every interior group and every interface group
+    is the RCM order of the graph it induces, the split is unchanged, and with exact local
+    factors and n2 inner steps the apply is still A^{-1} (Eq. blockldusolve)."""
+    pr = _small_dd(kind)
+    A = pr.scipy()
+    nat = O.Oracle.from_problem(pr).perm()
+    o = O.Oracle.from_problem(pr, factor_B="exact", factor_S="exact", local_order="rcm",
+                              inner_iters=max(nat["n2"], 1))
+    pm = o.perm()
+    for k in ("int_ptr", "if_ptr", "iface"):
+        assert np.array_equal(pm[k], nat[k])
+    n1 = pm["n1"]
+    groups = [(pm["int_ptr"][s], pm["int_ptr"][s + 1]) for s in range(pr.p)]
+    groups += [(n1 + pm["if_ptr"][s], n1 + pm["if_ptr"][s + 1]) for s in range(pr.p)]
+    for a, b in groups:
+        g = np.sort(nat["perm"][a:b])
+        G = A[g][:, g].tocsr()
+        G.sort_indices()
+        assert np.array_equal(pm["perm"][a:b], g[O.rcm(g.size, G.indptr, G.indices)])
+    assert np.array_equal(pm["iperm"][pm["perm"]], np.arange(pr.n))
+    r = np.random.default_rng(5).standard_normal(pr.n)
+    np.testing.assert_allclose(o.apply(r), np.linalg.solve(A.toarray(), r), rtol=1e-9, atol=1e-10)
 
 
 # --------------------------------------------------------------------------------------
@@ -532,13 +681,15 @@ def _run_paper_case(c):
         mat = P.aniso3d_7pt(*c["grid"], 1.0, 1.0, 1.0)
     n = mat[0]
     part, p = P.contiguous_partition(n, c["p"])
-    o = O.Oracle(*mat, part, p, variant="bj", factor_B="ilu0", factor_S="ilu0")
+    o = O.Oracle(*mat, part, p, variant="bj", factor_B="ilu0", factor_S="ilu0",
+                 local_order=c.get("local_order", "natural"))
     out = o.fgmres(np.ones(n), rtol=c["rtol"], restart=c["restart"], maxit=20000)
     assert out["status"] == O.OK
     return out["iters"]
 
 
-@pytest.mark.parametrize("case", _golden_cases(False), ids=lambda c: c["problem"])
+@pytest.mark.parametrize("case", _golden_cases(False),
+                         ids=lambda c: c["problem"] + "-" + c.get("local_order", "natural"))
 def test_paper_iteration_counts(case):
     """The paper's printed FGMRES(50) + ILU(0) iteration counts (tests/golden)."""
     assert _run_paper_case(case) == case["iters"]
