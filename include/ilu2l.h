@@ -61,6 +61,14 @@ typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1, ILU_VARIANT_RAP = 2 } 
 typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2 } ilu_fact;
 typedef enum { ILU_FORM_AUTO = 0, ILU_FORM_WZ = 1, ILU_FORM_EF = 2 } ilu_form;
 typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1 } ilu_prec;
+/* Order inside each group of a subdomain before the factorisation. The groups: block
+   Jacobi, the whole subdomain (it has no interface, Sec. 2.1); SCHUR and RAP, the interior
+   nodes and the interface nodes of each subdomain (Sec. 2.2.1), so A_i keeps its
+   [B F; E C] form. NATURAL: ascending original index. RCM: reverse Cuthill-McKee of the
+   graph the group induces in A + A^T (Sec. 3.1, Algorithm "Block Jacobi ILU on GPU"); each
+   component starts at its unplaced node of least (degree, index), neighbours are appended
+   by (degree, index), the sequence is then reversed. */
+typedef enum { ILU_ORDER_NATURAL = 0, ILU_ORDER_RCM = 1 } ilu_order;
 
 typedef struct {
     int32_t variant;      /* ilu_variant */
@@ -71,7 +79,7 @@ typedef struct {
     int32_t ilut_p;       /* ILUT entries kept per row in each of the L and U parts */
     int32_t inner_iters;  /* GMRES steps on the preconditioned Schur system (Eq. preSS) */
     int32_t pc_precision; /* ilu_prec: arithmetic of the factors and of M^{-1} */
-    int32_t ordering;     /* 0 = natural (ascending original index); others reserved */
+    int32_t ordering;     /* ilu_order: order inside each group of a subdomain */
     double pivot_eps;     /* small-pivot perturbation relative to max_j |a_ij| (0 = off) */
     void* stream;         /* cudaStream_t for every device call (NULL = legacy stream) */
     uint64_t spin_limit;  /* iteration bound of every device-side wait (0 = default) */

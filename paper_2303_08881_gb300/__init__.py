@@ -133,6 +133,7 @@ class Opts:
     analysis_only: bool = False
     kernel_path: str = "stream"     # "stream" (TMA-streamed level programs) or "generic"
     inner_launch: str = "single"    # inner Schur GMRES: "single" cooperative launch or "per_step"
+    local_order: str = "natural"    # order inside each group of a subdomain: "natural" or "rcm"
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -152,6 +153,7 @@ class Opts:
         o.analysis_only = int(bool(self.analysis_only))
         o.kernel_path = {"stream": 0, "generic": 1}[self.kernel_path]
         o.inner_launch = {"single": 0, "per_step": 1}[self.inner_launch]
+        o.ordering = {"natural": 0, "rcm": 1}[self.local_order]
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:

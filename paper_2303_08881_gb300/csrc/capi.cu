@@ -484,11 +484,12 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
-        o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1) {
+        o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
+        (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM)) {
         delete h;
         return ILU_ERR_ARG;
     }
-    if (o.ordering != 0 || (o.variant == ILU_VARIANT_RAP && o.kernel_path != 0)) {
+    if (o.variant == ILU_VARIANT_RAP && o.kernel_path != 0) {
         delete h;
         return ILU_ERR_UNSUPPORTED;
     }

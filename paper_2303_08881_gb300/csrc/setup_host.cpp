@@ -584,6 +584,76 @@ void host_levels(Handle& h) {
     h.lev_ready = true;
 }
 
+// Reverse Cuthill-McKee (Sec. 3.1: the local block is put in RCM order before its ILU) of
+// the graph that the nodes `grp` (original indices, ascending) induce in A, symmetrised:
+// a ~ b when a_ab or a_ba is stored, a != b. Each component is searched breadth first from
+// its unplaced node of least (degree, index); a node taken from the front of the sequence
+// appends its unplaced neighbours by increasing (degree, index); the finished sequence is
+// reversed. `grp` (all in subdomain s) is rewritten in that order. `slot` (size n, all -1)
+// maps original indices to positions in `grp` while this runs and is left all -1; only
+// entries of subdomain s are touched, so subdomains may run on different threads.
+static void rcm_group(const ilu_csr* A, const int32_t* part, int32_t s, std::vector<int32_t>& grp,
+                      int32_t* slot) {
+    const int32_t m = (int32_t)grp.size();
+    if (m <= 1) return;
+    for (int32_t k = 0; k < m; k++) slot[grp[k]] = k;
+    // the edges of the symmetrised graph as sorted, unique (row << 32 | col) keys
+    std::vector<uint64_t> key;
+    for (int32_t k = 0; k < m; k++) {
+        const int32_t i = grp[k];
+        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+            if (part[A->colind[q]] != s) continue;
+            const int32_t t = slot[A->colind[q]];
+            if (t >= 0 && t != k) {
+                key.push_back(((uint64_t)(uint32_t)k << 32) | (uint32_t)t);
+                key.push_back(((uint64_t)(uint32_t)t << 32) | (uint32_t)k);
+            }
+        }
+    }
+    std::sort(key.begin(), key.end());
+    key.erase(std::unique(key.begin(), key.end()), key.end());
+    std::vector<int32_t> off(m + 1, 0), nb(key.size());
+    for (size_t e = 0; e < key.size(); e++) {
+        off[(key[e] >> 32) + 1]++;
+        nb[e] = (int32_t)(key[e] & 0xffffffffu);
+    }
+    for (int32_t k = 0; k < m; k++) off[k + 1] += off[k];
+    // labels follow the ascending original index, so (degree, label) orders like
+    // (degree, index)
+    auto before = [&](int32_t a, int32_t b) {
+        const int32_t da = off[a + 1] - off[a], db = off[b + 1] - off[b];
+        return da != db ? da < db : a < b;
+    };
+    std::vector<int32_t> roots(m);
+    for (int32_t k = 0; k < m; k++) roots[k] = k;
+    std::sort(roots.begin(), roots.end(), before);
+    std::vector<char> placed(m, 0);
+    std::vector<int32_t> seq;
+    seq.reserve(m);
+    std::vector<int32_t> fresh;
+    size_t next_root = 0;
+    while ((int32_t)seq.size() < m) {
+        while (placed[roots[next_root]]) next_root++;
+        placed[roots[next_root]] = 1;
+        seq.push_back(roots[next_root]);
+        for (size_t head = seq.size() - 1; head < seq.size(); head++) {
+            const int32_t u = seq[head];
+            fresh.clear();
+            for (int32_t e = off[u]; e < off[u + 1]; e++)
+                if (!placed[nb[e]]) {
+                    placed[nb[e]] = 1;
+                    fresh.push_back(nb[e]);
+                }
+            std::sort(fresh.begin(), fresh.end(), before);
+            seq.insert(seq.end(), fresh.begin(), fresh.end());
+        }
+    }
+    std::vector<int32_t> out(m);
+    for (int32_t k = 0; k < m; k++) out[k] = grp[seq[m - 1 - k]];
+    for (int32_t k = 0; k < m; k++) slot[grp[k]] = -1;
+    grp.swap(out);
+}
+
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
     ilu_status st = validate(A, part, p);
     if (st != ILU_OK) return st;
@@ -595,8 +665,9 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
 
     // ---- classification (Sec. 2.2.1): interface iff coupled to another subdomain in A
     //      or A^T (symmetrised pattern keeps B, E, F block diagonal for any pattern).
+    //      Block Jacobi factors each whole A_i (Sec. 2.1): it has no interface.
     h.iface.assign(n, 0);
-    for (int32_t i = 0; i < n; i++)
+    for (int32_t i = 0; i < n && h.variant != ILU_VARIANT_BJ; i++)
         for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
             const int32_t j = A->colind[q];
             if (part[j] != part[i]) {
@@ -626,6 +697,33 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
             h.perm[g] = i;
             h.iperm[i] = g;
         }
+    }
+
+    // ---- RCM inside each group (Sec. 3.1; Algorithm "Block Jacobi ILU on GPU"): block
+    //      Jacobi orders all of A_s, the two-level variants its interior nodes and its
+    //      interface nodes separately, so A_s keeps its [B F; E C] form
+    if (h.o.ordering == ILU_ORDER_RCM) {
+        std::vector<int32_t> slot(n, -1);
+        auto work = [&](int32_t s0, int32_t s1) {
+            std::vector<int32_t> grp;
+            for (int32_t s = s0; s < s1; s++)
+                for (int side = 0; side < 2; side++) {
+                    const int32_t g0 = side ? h.n1 + h.if_ptr[s] : h.int_ptr[s];
+                    const int32_t g1 = side ? h.n1 + h.if_ptr[s + 1] : h.int_ptr[s + 1];
+                    grp.assign(h.perm.begin() + g0, h.perm.begin() + g1);
+                    rcm_group(A, part, s, grp, slot.data());
+                    for (int32_t k = 0; k < g1 - g0; k++) {
+                        h.perm[g0 + k] = grp[k];
+                        h.iperm[grp[k]] = g0 + k;
+                    }
+                }
+        };
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        nt = std::min<unsigned>(nt, (unsigned)p);
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; t++)
+            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
+        for (auto& t : th) t.join();
     }
 
     // ---- Q order: subdomain s owns [qoff[s], qoff[s+1]) = [interior_s ; interface_s]

@@ -23,6 +23,10 @@ CFGS = [
     dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-2, ilut_p=3),
     dict(variant="bj", factor_B="ilut", factor_S="ilu0", ilut_tau=1e-3, ilut_p=5),
     dict(variant="rap", factor_B="ilu0", factor_S="milu0"),
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="rcm"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
+    dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10, local_order="rcm"),
+    dict(variant="rap", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
 ]
 
 

@@ -31,6 +31,8 @@ CFGS = [
     dict(variant="schur", factor_B="ilu0", factor_S="milu0"),
     dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
     dict(variant="rap", factor_B="ilu0", factor_S="milu0"),
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="rcm"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
 ]
 SKIP = 1 << 31
 BARRIER = 1 << 31
