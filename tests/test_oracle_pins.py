@@ -696,8 +696,11 @@ def test_paper_iteration_counts(case):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("case", _golden_cases(True), ids=lambda c: c["problem"])
+@pytest.mark.parametrize("case", _golden_cases(True),
+                         ids=lambda c: f'{c["problem"]}-p{c["p"]}-{c.get("local_order", "natural")}')
 def test_paper_iteration_counts_slow(case):
+    """Larger printed counts: 3D 128^3 at Np=1 (~65 s) and 2D 512^2 split into 4 blocks of
+    whole grid rows (~80 s; the multi-subdomain block Jacobi)."""
     assert _run_paper_case(case) == case["iters"]
 
 
