@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("factor_B", C.c_int), ("factor_S", C.c_int),
                 ("form", C.c_int), ("ilut_tau", C.c_double), ("ilut_p", C.c_int),
-                ("inner_iters", C.c_int), ("pivot_eps", C.c_double), ("local_order", C.c_int)]
+                ("inner_iters", C.c_int), ("pivot_eps", C.c_double), ("local_order", C.c_int),
+                ("fill_level", C.c_int)]
 
 
 _lib = None
@@ -68,6 +69,7 @@ def lib():
             "orc_classify": (I, [I, P, P, P, I, P]),
             "orc_permutation": (I, [I, P, I, P, P, P, P, P]),
             "orc_rcm": (I, [I, P, P, P]),
+            "orc_iluk_pattern": (P, [I, P, P, P, I, P]),
             "orc_opts_default": (None, [P]),
             "orc_setup": (P, [I, P, P, P, P, I, P, P]),
             "orc_free": (None, [P]),
@@ -177,6 +179,23 @@ def classify(n, rowptr, colind, part, p):
     return iface
 
 
+def iluk_pattern(n, rowptr, colind, val, k):
+    """Level-k fill pattern of ILU(k): (rowptr, colind, val) with A's values and zeros at
+    the fill positions."""
+    rowptr, colind, val = _i32(rowptr), _i32(colind), _f64(val)
+    st = C.c_int(0)
+    f = lib().orc_iluk_pattern(int(n), _p(rowptr), _p(colind), _p(val), int(k), C.byref(st))
+    if not f:
+        raise ValueError(f"iluk_pattern status {st.value}")
+    nnz = lib().orc_factor_nnz(f)
+    rp = np.empty(n + 1, np.int32)
+    ci = np.empty(nnz, np.int32)
+    v = np.empty(nnz)
+    lib().orc_factor_get(f, _p(rp), _p(ci), _p(v))
+    lib().orc_factor_free(f)
+    return rp, ci, v
+
+
 def rcm(n, rowptr, colind):
     """Reverse Cuthill-McKee order of the symmetrised graph of a square pattern:
     order[k] = the node placed k-th."""
@@ -219,7 +238,7 @@ class Oracle:
 
     def __init__(self, n, rowptr, colind, val, part, p, variant="schur", factor_B="ilu0",
                  factor_S="milu0", form="auto", ilut_tau=1e-3, ilut_p=10, inner_iters=3,
-                 pivot_eps=1e-8, local_order="natural"):
+                 pivot_eps=1e-8, local_order="natural", fill_level=0):
         self._keep = [_i32(rowptr), _i32(colind), _f64(val), _i32(part)]
         o = _Opts()
         lib().orc_opts_default(C.byref(o))
@@ -232,6 +251,7 @@ class Oracle:
         o.inner_iters = int(inner_iters)
         o.pivot_eps = pivot_eps
         o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM}[local_order]
+        o.fill_level = int(fill_level)
         self.opts = o
         st = C.c_int(0)
         rp, ci, v, pt = self._keep

@@ -228,6 +228,98 @@ typedef struct {
     int npert;
 } ilut_fact_t;
 
+static int int_cmp(const void* a, const void* b);
+
+/* Level-of-fill pattern of ILU(k) (the paper uses ILU(1) and ILU(2) in Sec. 4.2-4.4 without
+   defining them; standard sum rule). Stored entries have level 0. Row i is eliminated with
+   its pivots m < i in ascending order, fill included: each entry u_mj (j > m) kept in row m
+   gives position (i, j) the level lev(i,m) + lev(m,j) + 1, the smallest such level wins, and
+   positions of level <= k are kept. Rows: sorted columns, the diagonal stored. */
+static int iluk_symbolic(const csr_t* M, int k, csr_t* out) {
+    int n = M->nr, st = ORC_OK;
+    int* lev = (int*)malloc(((size_t)n + 1) * sizeof(int));   /* level of (i, j), -1 absent */
+    int* cols = (int*)malloc(((size_t)n + 1) * sizeof(int));  /* columns present in row i */
+    int* heap = (int*)malloc(((size_t)n + 1) * sizeof(int));  /* pending pivots m < i */
+    int* rp = (int*)calloc((size_t)n + 1, sizeof(int));
+    int cap = M->nnz + n + 16, nnz = 0;
+    int* ci = (int*)malloc((size_t)cap * sizeof(int));
+    int* lv = (int*)malloc((size_t)cap * sizeof(int));        /* level of each kept entry */
+    int* dg = (int*)malloc(((size_t)n + 1) * sizeof(int));    /* position of each diagonal */
+    if (!lev || !cols || !heap || !rp || !ci || !lv || !dg) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int j = 0; j < n; j++) lev[j] = -1;
+    for (int i = 0; i < n; i++) {
+        int nc = 0, hl = 0;
+        for (int q = M->rp[i]; q < M->rp[i + 1]; q++) {
+            int j = M->ci[q];
+            lev[j] = 0;
+            cols[nc++] = j;
+            if (j < i) heap_push(heap, &hl, j);
+        }
+        while (hl > 0) {
+            int m = heap_pop(heap, &hl);
+            int lim = lev[m];
+            for (int t = dg[m] + 1; t < rp[m + 1]; t++) {
+                int j = ci[t], nl = lim + lv[t] + 1;
+                if (nl > k) continue;
+                if (lev[j] < 0) {
+                    lev[j] = nl;
+                    cols[nc++] = j;
+                    if (j < i) heap_push(heap, &hl, j);
+                } else if (nl < lev[j]) {
+                    lev[j] = nl;
+                }
+            }
+        }
+        qsort(cols, (size_t)nc, sizeof(int), int_cmp);
+        if (nnz + nc > cap) {
+            while (nnz + nc > cap) cap *= 2;
+            int* c2 = (int*)realloc(ci, (size_t)cap * sizeof(int));
+            if (c2) ci = c2;
+            int* l2 = (int*)realloc(lv, (size_t)cap * sizeof(int));
+            if (l2) lv = l2;
+            if (!c2 || !l2) {
+                st = ORC_ERR_OOM;
+                goto done;
+            }
+        }
+        dg[i] = -1;
+        for (int t = 0; t < nc; t++) {
+            if (cols[t] == i) dg[i] = nnz;
+            ci[nnz] = cols[t];
+            lv[nnz++] = lev[cols[t]];
+            lev[cols[t]] = -1;
+        }
+        rp[i + 1] = nnz;
+        if (dg[i] < 0) {
+            st = ORC_ERR_CSR;
+            goto done;
+        }
+    }
+    st = csr_init(out, n, n, nnz);
+    if (st) goto done;
+    memcpy(out->rp, rp, ((size_t)n + 1) * sizeof(int));
+    memcpy(out->ci, ci, (size_t)nnz * sizeof(int));
+    for (int i = 0; i < n; i++) { /* A's values, zeros at the fill positions */
+        int q = M->rp[i];
+        for (int t = rp[i]; t < rp[i + 1]; t++) {
+            while (q < M->rp[i + 1] && M->ci[q] < ci[t]) q++;
+            out->v[t] = (q < M->rp[i + 1] && M->ci[q] == ci[t]) ? M->v[q] : 0.0;
+        }
+    }
+done:
+    free(lev);
+    free(cols);
+    free(heap);
+    free(rp);
+    free(ci);
+    free(lv);
+    free(dg);
+    return st;
+}
+
 static int ilut_factor(int n, const int* rp, const int* ci, const double* a, double tau,
                        int pkeep, double eps, csr_t* out, int* npert) {
     double* w = (double*)calloc((size_t)n + 1, sizeof(double));
@@ -388,6 +480,28 @@ void* orc_ilut_csr(int n, const int* rp, const int* ci, const double* val, doubl
         free(f);
         return NULL;
     }
+    return f;
+}
+
+void* orc_iluk_pattern(int n, const int* rp, const int* ci, const double* val, int k,
+                       int* status) {
+    int st = orc_csr_check(n, rp, ci);
+    ilut_fact_t* f = NULL;
+    if (!st && k < 0) st = ORC_ERR_ARG;
+    if (!st) {
+        f = (ilut_fact_t*)calloc(1, sizeof(ilut_fact_t));
+        if (!f) st = ORC_ERR_OOM;
+    }
+    if (!st) {
+        csr_t M = {n, n, rp[n], (int*)rp, (int*)ci, (double*)val};
+        st = iluk_symbolic(&M, k, &f->f);
+    }
+    if (st && f) {
+        csr_release(&f->f);
+        free(f);
+        f = NULL;
+    }
+    if (status) *status = st;
     return f;
 }
 
@@ -732,6 +846,7 @@ void orc_opts_default(orc_opts* o) {
     o->inner_iters = 3;
     o->pivot_eps = 1e-8;
     o->local_order = ORC_ORDER_NATURAL;
+    o->fill_level = 0;
 }
 
 static inline int nint_of(const orc_t* h, int s) { return h->int_ptr[s + 1] - h->int_ptr[s]; }
@@ -944,6 +1059,21 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
         }
         free(row);
         free(fill);
+    }
+
+    /* ILU(k) / MILU(k): each local block stored in its level-k pattern, so that ILU(0) /
+       MILU(0) of the stored block is ILU(k) / MILU(k) of A_s */
+    if (h->o.fill_level < 0 ||
+        (h->o.fill_level > 0 && (h->o.factor_B > ORC_MILU0 || h->o.factor_S > ORC_MILU0))) {
+        st = ORC_ERR_ARG;
+        goto fail;
+    }
+    for (int s = 0; s < p && h->o.fill_level > 0; s++) {
+        csr_t X;
+        st = iluk_symbolic(&h->Aloc[s], h->o.fill_level, &X);
+        if (st) goto fail;
+        csr_release(&h->Aloc[s]);
+        h->Aloc[s] = X;
     }
 
     /* factorisations (Sec. 3.1 / 3.2 / 2.3 / 3.3); readings:

@@ -62,6 +62,9 @@ typedef struct orc_opts {
                            whole subdomain (no interior / interface split, Sec. 2.1); the
                            two-level variants, the interior and the interface nodes of each
                            subdomain (Sec. 2.2.1) */
+    int fill_level;     /* k >= 0: ILU0 / MILU0 become ILU(k) / MILU(k) (Sec. 4.2-4.4): each
+                           local block is stored in its level-k fill pattern, explicit zeros
+                           at the fill positions; needs factor_B, factor_S in {ILU0, MILU0} */
 } orc_opts;
 
 /* ---- primitives on one CSR matrix ---- */
@@ -94,6 +97,11 @@ int orc_classify(int n, const int* rowptr, const int* colind, const int* part, i
 /* Reverse Cuthill-McKee order of the symmetrised graph of a square pattern (i ~ j when
    a_ij or a_ji is stored, i != j): order[k] = the node placed k-th. */
 int orc_rcm(int n, const int* rowptr, const int* colind, int* order);
+/* Level-k fill pattern of ILU(k) of a square CSR matrix with sorted rows and its diagonal
+   stored: returns the pattern as a new CSR (values: the matrix's, 0 at fill positions) via
+   orc_factor_* (opaque handle); NULL with *status set on error. */
+void* orc_iluk_pattern(int n, const int* rowptr, const int* colind, const double* val, int k,
+                       int* status);
 /* returns n1 (number of interior unknowns) */
 int orc_permutation(int n, const int* part, int p, const int* iface, int* perm, int* iperm,
                     int* int_ptr, int* if_ptr);

@@ -621,6 +621,131 @@ def test_two_level_rcm_orders_each_group_and_stays_exact(kind):
 
 
 # --------------------------------------------------------------------------------------
+# ILU(k) (level of fill; the paper runs ILU(1) and ILU(2) in Sec. 4.2-4.4)
+
+
+def _fill_path_levels(M, k):
+    """Brute force from the fill-path theorem (Hysom and Pothen): (i, j) has level l iff the
+    shortest directed path i -> j in the graph of A whose inner vertices are all below
+    min(i, j) has l + 1 edges. Returns the set of positions of level <= k."""
+    n = M.shape[0]
+    adj = [set(M.indices[M.indptr[i]:M.indptr[i + 1]]) - {i} for i in range(n)]
+    keep = set((i, i) for i in range(n))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            lo = min(i, j)
+            dist, frontier, seen = 0, {i}, {i}
+            found = None
+            while frontier and found is None and dist <= k:
+                dist += 1
+                nxt = set()
+                for u in frontier:
+                    for w in adj[u]:
+                        if w == j:
+                            found = dist
+                        elif w < lo and w not in seen:
+                            seen.add(w)
+                            nxt.add(w)
+                frontier = nxt
+            if found is not None and found - 1 <= k:
+                keep.add((i, j))
+    return keep
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_iluk_pattern_is_the_fill_path_closure(seed, k):
+    M = _rand_sparse(18, 0.09, seed=40 + seed)
+    rp, ci, _ = O.iluk_pattern(18, M.indptr, M.indices, M.data, k)
+    got = {(i, int(j)) for i in range(18) for j in ci[rp[i]:rp[i + 1]]}
+    assert got == _fill_path_levels(M, k)
+
+
+def test_iluk_of_the_5pt_grid_adds_the_two_textbook_diagonals():
+    """Natural order, 5-point grid nx x ny: ILU(1) adds exactly (i, i - nx + 1) and
+    (i, i + nx - 1) where both nodes exist (eliminating the south and west neighbours)."""
+    nx, ny = 7, 5
+    n, rp, ci, v = P.poisson2d_5pt(nx, ny)
+    r1, c1, v1 = O.iluk_pattern(n, rp, ci, v, 1)
+    base = {(i, int(j)) for i in range(n) for j in ci[rp[i]:rp[i + 1]]}
+    got = {(i, int(j)) for i in range(n) for j in c1[r1[i]:r1[i + 1]]}
+    want = set(base)
+    for i in range(n):
+        x, y = i % nx, i // nx
+        if y > 0 and x < nx - 1:
+            want.add((i, i - nx + 1))
+        if y < ny - 1 and x > 0:
+            want.add((i, i + nx - 1))
+    assert got == want
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    F = sp.csr_matrix((v1, c1, r1), shape=(n, n))
+    assert abs(F - A).max() == 0  # A's values, zeros at the fill
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("milu", [False, True])
+def test_iluk_factors_match_A_on_their_pattern(k, milu):
+    """ILU on a pattern P reproduces A on P: (LU)_ij = a_ij there; MILU(k) instead keeps
+    every row sum of A (the dropped updates go to the pivot)."""
+    M = _rand_sparse(120, 0.03, seed=3)
+    n = 120
+    part = np.zeros(n, np.int32)
+    kind = "milu0" if milu else "ilu0"
+    o = O.Oracle(*_mat_tuple(M), part, 1, variant="bj", factor_B=kind, factor_S=kind, fill_level=k)
+    rp, ci, _ = o.local_csr(0)
+    f = o.local_factor(0, 1)
+    L, U = _split_lu(n, rp, ci, f)
+    LU = (L @ U).toarray()
+    Ad = M.toarray()
+    if milu:
+        np.testing.assert_allclose(LU.sum(axis=1), Ad.sum(axis=1), rtol=1e-11, atol=1e-11)
+        mask = np.zeros((n, n), bool)
+        for i in range(n):
+            mask[i, ci[rp[i]:rp[i + 1]]] = True
+        np.fill_diagonal(mask, False)
+        np.testing.assert_allclose(LU[mask], Ad[mask], rtol=1e-11, atol=1e-11)
+    else:
+        for i in range(n):
+            cols = ci[rp[i]:rp[i + 1]]
+            np.testing.assert_allclose(LU[i, cols], Ad[i, cols], rtol=1e-11, atol=1e-11)
+    assert rp[-1] > M.nnz  # fill was added
+
+
+def test_iluk_with_a_large_level_is_exact_lu():
+    """With k >= n nothing is dropped: L U = A."""
+    M = _rand_sparse(60, 0.06, seed=8)
+    o = O.Oracle(*_mat_tuple(M), np.zeros(60, np.int32), 1, variant="bj", factor_B="ilu0",
+                 factor_S="ilu0", fill_level=60)
+    rp, ci, _ = o.local_csr(0)
+    L, U = _split_lu(60, rp, ci, o.local_factor(0, 1))
+    np.testing.assert_allclose((L @ U).toarray(), M.toarray(), rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "rand"])
+def test_two_level_with_exact_iluk_is_A_inverse(kind):
+    """ILU(k) with k >= n is exact on every local block, so with n2 inner steps the
+    two-level apply is A^{-1} (Eq. blockldusolve); the same with the RCM order."""
+    pr = _small_dd(kind)
+    n2 = O.Oracle.from_problem(pr).sizes().n2
+    r = np.random.default_rng(5).standard_normal(pr.n)
+    x = np.linalg.solve(pr.scipy().toarray(), r)
+    for order in ("natural", "rcm"):
+        o = O.Oracle.from_problem(pr, factor_B="ilu0", factor_S="ilu0", fill_level=pr.n,
+                                  inner_iters=max(n2, 1), local_order=order)
+        np.testing.assert_allclose(o.apply(r), x, rtol=1e-9, atol=1e-10)
+
+
+def test_fill_level_needs_level_based_factors():
+    pr = _small_dd("aniso2d")
+    with pytest.raises(RuntimeError):
+        O.Oracle.from_problem(pr, factor_B="ilut", fill_level=1)
+    with pytest.raises(RuntimeError):
+        O.Oracle.from_problem(pr, fill_level=-1)
+
+
+# --------------------------------------------------------------------------------------
 # FGMRES
 
 
