@@ -94,6 +94,12 @@ typedef struct {
                              cooperative launch for all inner steps when every subdomain's CTA
                              can be resident at once (else as 1; default), 1 = four launches
                              per inner step */
+    int32_t fill_level;   /* k >= 0: the ILU0 / MILU0 factor kinds become ILU(k) / MILU(k)
+                             (the paper runs ILU(1) and ILU(2), Sec. 4.2-4.4). Each local block
+                             is stored in its level-k fill pattern (level of a stored entry 0;
+                             eliminating pivot m of row i gives (i, j) the level
+                             lev(i,m) + lev(m,j) + 1, the least wins), zeros at the fill, and
+                             factorised in it. ILU_ERR_ARG with factor_B = ILUT. Default 0. */
 } ilu_opts;
 
 typedef struct {
@@ -179,6 +185,12 @@ ilu_status ilu_get_levels(void* h, int32_t which, int32_t* lev, int32_t* nlev);
    original index): fact = 1 the factor giving L_B, U_B, W, Z; fact = 2 the one giving
    L_S, U_S. ILU_ERR_ARG if that factor does not have the pattern of A_s (ILUT). */
 ilu_status ilu_get_local_factor(void* h, int32_t s, int32_t fact, double* val);
+
+/* Pattern of local block s as stored for the factorisation (A_s in the local order; with
+   fill_level k > 0 its level-k fill pattern): rowptr (host int32[rows of s + 1], from 0)
+   and colind (host int32[*nnz], local column indices, ascending in each row). Either array
+   may be NULL; *nnz (required) receives the entry count. Valid on analysis-only handles. */
+ilu_status ilu_get_local_pattern(void* h, int32_t s, int32_t* rowptr, int32_t* colind, int32_t* nnz);
 
 /* y = A x with the handle's FP64 CSR SpMV kernel (x, y DEVICE double[n], original
    ordering, no aliasing). Asynchronous on opts.stream. */

@@ -45,7 +45,8 @@ class ilu_opts(C.Structure):
                 ("inner_iters", C.c_int32), ("pc_precision", C.c_int32), ("ordering", C.c_int32),
                 ("pivot_eps", C.c_double), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
-                ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32)]
+                ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32),
+                ("fill_level", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -77,6 +78,7 @@ def lib():
             "ilu_get_perm": (I, [P, P, P, P, P, P]),
             "ilu_get_levels": (I, [P, I, P, P]),
             "ilu_get_local_factor": (I, [P, I, I, P]),
+            "ilu_get_local_pattern": (I, [P, I, P, P, P]),
             "ilu_spmv": (I, [P, P, P]),
             "ilu_inner_solve": (I, [P, P, P]),
             "ilu_profile": (I, [P, I]),
@@ -134,6 +136,7 @@ class Opts:
     kernel_path: str = "stream"     # "stream" (TMA-streamed level programs) or "generic"
     inner_launch: str = "single"    # inner Schur GMRES: "single" cooperative launch or "per_step"
     local_order: str = "natural"    # order inside each group of a subdomain: "natural" or "rcm"
+    fill_level: int = 0             # k > 0: ILU(k) / MILU(k) in the level-k fill pattern
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -154,6 +157,7 @@ class Opts:
         o.kernel_path = {"stream": 0, "generic": 1}[self.kernel_path]
         o.inner_launch = {"single": 0, "per_step": 1}[self.inner_launch]
         o.ordering = {"natural": 0, "rcm": 1}[self.local_order]
+        o.fill_level = int(self.fill_level)
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:
@@ -220,6 +224,18 @@ class Handle:
         _check(lib().ilu_get_levels(self.ptr, w, lev.ctypes.data_as(C.c_void_p), C.byref(nl)),
                "ilu_get_levels")
         return lev, nl.value
+
+    def local_pattern(self, s: int):
+        """(rowptr, colind) of local block s as stored for the factorisation."""
+        pm = self.perm()
+        rows = int(pm["int_ptr"][s + 1] - pm["int_ptr"][s] + pm["if_ptr"][s + 1] - pm["if_ptr"][s])
+        nnz = C.c_int32(0)
+        _check(lib().ilu_get_local_pattern(self.ptr, int(s), None, None, C.byref(nnz)), "ilu_get_local_pattern")
+        rp = np.empty(rows + 1, np.int32)
+        ci = np.empty(nnz.value, np.int32)
+        _check(lib().ilu_get_local_pattern(self.ptr, int(s), rp.ctypes.data_as(C.c_void_p),
+                                           ci.ctypes.data_as(C.c_void_p), C.byref(nnz)), "ilu_get_local_pattern")
+        return rp, ci
 
     def local_factor(self, s: int, fact: int, nnz: int) -> np.ndarray:
         v = np.empty(nnz)

@@ -426,7 +426,8 @@ void ilu_opts_default(ilu_opts* o) {
     o->ilut_p = 10;
     o->inner_iters = 3;
     o->pc_precision = ILU_PREC_FP32;
-    o->ordering = 0;
+    o->ordering = ILU_ORDER_NATURAL;
+    o->fill_level = 0;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -485,7 +486,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
         o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
-        (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM)) {
+        (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
+        (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT)) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -736,6 +738,19 @@ ilu_status ilu_get_local_factor(void* hp, int32_t s, int32_t fact, double* val) 
     const int32_t q0 = h->qoff[s], q1 = h->qoff[s + 1];
     const int64_t b = h->q_rp[q0], e = h->q_rp[q1];
     CK(cudaMemcpy(val, h->d_vals + F.base + b, (size_t)(e - b) * sizeof(double), cudaMemcpyDeviceToHost));
+    return ILU_OK;
+}
+
+ilu_status ilu_get_local_pattern(void* hp, int32_t s, int32_t* rowptr, int32_t* colind, int32_t* nnz) {
+    if (!hp || !nnz) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (s < 0 || s >= h->p) return ILU_ERR_ARG;
+    const int32_t q0 = h->qoff[s], q1 = h->qoff[s + 1];
+    const int32_t b = h->q_rp[q0];
+    *nnz = h->q_rp[q1] - b;
+    if (rowptr)
+        for (int32_t q = q0; q <= q1; q++) rowptr[q - q0] = h->q_rp[q] - b;
+    if (colind) std::memcpy(colind, h->q_ci.data() + b, (size_t)*nnz * sizeof(int32_t));
     return ILU_OK;
 }
 

@@ -654,6 +654,61 @@ static void rcm_group(const ilu_csr* A, const int32_t* part, int32_t s, std::vec
     grp.swap(out);
 }
 
+// Level-k fill pattern of ILU(k) of one local block: rows [q0, q0 + ns) of the Q-order CSR
+// (rp, ci; local column indices, sorted, diagonal stored). Stored entries have level 0;
+// row r is eliminated with its pivots m < r in ascending order, fill included, and every
+// entry u_mj (j > m) already kept in row m gives (r, j) the level lev(r, m) + lev(m, j) + 1;
+// the least level wins and levels <= k are kept. While a row is eliminated its columns sit
+// in a sorted singly linked list (head = ns), so fill is inserted in place. Output: local
+// CSR (orp, oci) and, for the values, the position of each kept entry in the input (-1 =
+// fill).
+static void iluk_block(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, int32_t q0, int32_t ns,
+                       int k, std::vector<int32_t>& orp, std::vector<int32_t>& oci, std::vector<int64_t>& osrc) {
+    const int32_t head = ns;
+    std::vector<int32_t> nxt(ns + 1, -1), lev(ns, -1), diag(ns, -1);
+    std::vector<int32_t> olev;
+    orp.assign(ns + 1, 0);
+    oci.clear();
+    osrc.clear();
+    for (int32_t r = 0; r < ns; r++) {
+        // stored entries, already ascending
+        int32_t tail = head;
+        for (int32_t q = rp[q0 + r]; q < rp[q0 + r + 1]; q++) {
+            const int32_t j = ci[q];
+            lev[j] = 0;
+            nxt[tail] = j;
+            tail = j;
+        }
+        nxt[tail] = ns;  // end marker: ns is never a column
+        for (int32_t m = nxt[head]; m < r; m = nxt[m]) {
+            const int32_t lm = lev[m];
+            int32_t at = m;  // insertion walk starts at the pivot: fill columns are > m
+            for (int32_t t = diag[m] + 1; t < orp[m + 1]; t++) {
+                const int32_t j = oci[t], l = lm + olev[t] + 1;
+                if (l > k) continue;
+                if (lev[j] >= 0) {
+                    lev[j] = std::min(lev[j], l);
+                    continue;
+                }
+                while (nxt[at] < j) at = nxt[at];
+                nxt[j] = nxt[at];
+                nxt[at] = j;
+                lev[j] = l;
+            }
+        }
+        int32_t q = rp[q0 + r];
+        for (int32_t j = nxt[head]; j < ns; j = nxt[j]) {
+            if (j == r) diag[r] = (int32_t)oci.size();
+            while (q < rp[q0 + r + 1] && ci[q] < j) q++;
+            osrc.push_back((q < rp[q0 + r + 1] && ci[q] == j) ? (int64_t)q : -1);
+            oci.push_back(j);
+            olev.push_back(lev[j]);
+            lev[j] = -1;
+        }
+        orp[r + 1] = (int32_t)oci.size();
+    }
+}
+
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
     ilu_status st = validate(A, part, p);
     if (st != ILU_OK) return st;
@@ -765,7 +820,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         if (h.iface[i]) h.coff_rp[h.iperm[i] - h.n1 + 1] = c_out;
     }
     for (int32_t r = 0; r < h.n2; r++) h.coff_rp[r + 1] += h.coff_rp[r];
-    const int64_t nnzQ = h.q_rp[n];
+    int64_t nnzQ = h.q_rp[n];
     h.q_ci.resize(nnzQ);
     h.q_v.resize(nnzQ);
     h.q_dpos.assign(n, -1);
@@ -809,6 +864,47 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 }
             }
         }
+    }
+
+    // ---- ILU(k) / MILU(k): every local block is stored in its level-k fill pattern with
+    //      zeros at the fill positions, so the device ILU(0) / MILU(0) of the stored block
+    //      is ILU(k) / MILU(k) of A_s
+    if (h.o.fill_level > 0) {
+        std::vector<std::vector<int32_t>> brp(p), bci(p);
+        std::vector<std::vector<int64_t>> bsrc(p);
+        auto work = [&](int32_t s0, int32_t s1) {
+            for (int32_t s = s0; s < s1; s++)
+                iluk_block(h.q_rp, h.q_ci, h.qoff[s], h.qoff[s + 1] - h.qoff[s], h.o.fill_level, brp[s], bci[s],
+                           bsrc[s]);
+        };
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        nt = std::min<unsigned>(nt, (unsigned)p);
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; t++)
+            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
+        for (auto& t : th) t.join();
+        int64_t tot = 0;
+        for (int32_t s = 0; s < p; s++) tot += (int64_t)bci[s].size();
+        if (tot >= (int64_t)INT32_MAX) return ILU_ERR_TOO_LARGE;
+        std::vector<int32_t> rp2(n + 1, 0), ci2;
+        std::vector<double> v2;
+        ci2.reserve(tot);
+        v2.reserve(tot);
+        for (int32_t s = 0; s < p; s++) {
+            const int32_t q0 = h.qoff[s], ns = h.qoff[s + 1] - q0;
+            for (int32_t r = 0; r < ns; r++) {
+                for (int32_t t = brp[s][r]; t < brp[s][r + 1]; t++) {
+                    if (bci[s][t] == r) h.q_dpos[q0 + r] = (int32_t)ci2.size();
+                    ci2.push_back(bci[s][t]);
+                    v2.push_back(bsrc[s][t] >= 0 ? h.q_v[bsrc[s][t]] : 0.0);
+                }
+                rp2[q0 + r + 1] = (int32_t)ci2.size();
+            }
+        }
+        h.q_rp.swap(rp2);
+        h.q_ci.swap(ci2);
+        h.q_v.swap(v2);
+        nnzQ = h.q_rp[n];
     }
 
     // ---- factor patterns and value regions [F1 | F2 | A_local]

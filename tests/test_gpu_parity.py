@@ -53,6 +53,9 @@ CONFIGS = [
     # RCM local order (Sec. 3.1): whole blocks for block Jacobi, each group for two-level
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="rcm"),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
+    # ILU(k) / MILU(k): local blocks stored in their level-k fill pattern
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
+    dict(variant="bj", factor_B="milu0", factor_S="milu0", fill_level=1),
 ]
 
 
@@ -122,7 +125,8 @@ def test_setup_structure_bit_exact(ilu, name, cfg):
 
 
 @pytest.mark.parametrize("name", list(PROBS))
-@pytest.mark.parametrize("cfg", [CONFIGS[0], CONFIGS[2], CONFIGS[4], CONFIGS[7], CONFIGS[8]], ids=_cid)
+@pytest.mark.parametrize("cfg", [CONFIGS[0], CONFIGS[2], CONFIGS[4], CONFIGS[7], CONFIGS[8], CONFIGS[9],
+                                 CONFIGS[10]], ids=_cid)
 def test_device_factors_bit_exact(ilu, name, cfg):
     pr, h, orc = _pair(ilu, name, cfg, "fp64")
     facts = [1] if cfg["variant"] == "bj" or cfg["factor_B"] == cfg["factor_S"] else [1, 2]
@@ -288,13 +292,13 @@ RAP = dict(variant="rap", factor_B="ilu0", factor_S="milu0")
 @pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "cuts3d", "rand", "p1", "dense_rows"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("k", [1, 3])
-@pytest.mark.parametrize("order", ["natural", "rcm"])
-def test_rap_apply_matches_oracle(ilu, name, prec, k, order):
+@pytest.mark.parametrize("extra", [{}, {"local_order": "rcm"}, {"fill_level": 1}], ids=["natural", "rcm", "iluk1"])
+def test_rap_apply_matches_oracle(ilu, name, prec, k, extra):
     """Multiplicative two-level apply (Algorithm "Multiplicative RAP-ILU on GPU"): ILU(0)
     smoother, R and P from MILU(0), k coarse GMRES steps preconditioned by L_S U_S."""
     pr = _prob(name)
-    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_iters=k, local_order=order, **RAP))
-    orc = O.Oracle.from_problem(pr, inner_iters=k, local_order=order, **RAP)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, inner_iters=k, **extra, **RAP))
+    orc = O.Oracle.from_problem(pr, inner_iters=k, **extra, **RAP)
     assert h.stats()["stream_path"]
     r = np.random.default_rng(19).standard_normal(pr.n)
     z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
@@ -467,6 +471,8 @@ def test_bad_vectors_are_rejected(ilu):
     ("conv3d", CONFIGS[5], "fp64", 10),
     ("aniso2d_ragged", CONFIGS[7], "fp64", 50),
     ("conv3d", CONFIGS[8], "fp32", 50),
+    ("conv3d", CONFIGS[9], "fp64", 30),
+    ("aniso2d_ragged", CONFIGS[9], "fp32", 50),
 ])
 @pytest.mark.parametrize("graphs", [True, False])
 def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):

@@ -27,6 +27,9 @@ CFGS = [
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
     dict(variant="schur", factor_B="ilut", factor_S="milu0", ilut_tau=1e-3, ilut_p=10, local_order="rcm"),
     dict(variant="rap", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0", fill_level=1),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
+    dict(variant="rap", factor_B="ilu0", factor_S="milu0", fill_level=1, local_order="rcm"),
 ]
 
 
@@ -54,7 +57,19 @@ def test_host_analysis_matches_oracle(ilu, name, cfg):
         lg, nlg = h.levels(w)
         lo, nlo = orc.levels(w)
         assert np.array_equal(lg, lo) and nlg == nlo, f"levels {w}"
+    for sd in range(pr.p):  # the stored local blocks (the level-k fill pattern if any)
+        rp, ci = h.local_pattern(sd)
+        orp, oci, _ = orc.local_csr(sd)
+        assert np.array_equal(rp, orp) and np.array_equal(ci, oci), f"pattern of block {sd}"
     h.close()
+
+
+def test_fill_level_option_is_validated(ilu):
+    pr = CASES["poisson64"]()
+    with pytest.raises(ilu.IluError):
+        ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, factor_B="ilut", fill_level=1))
+    with pytest.raises(ilu.IluError):
+        ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, fill_level=-1))
 
 
 def test_full_size_2d_workload_structure(ilu):

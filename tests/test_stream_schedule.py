@@ -33,6 +33,7 @@ CFGS = [
     dict(variant="rap", factor_B="ilu0", factor_S="milu0"),
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="rcm"),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
 ]
 SKIP = 1 << 31
 BARRIER = 1 << 31
