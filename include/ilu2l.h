@@ -143,7 +143,8 @@ ilu_status ilu_apply(void* h, const double* r, double* z);
    ||b - A x|| <= rtol ||b|| (checked at the end of every cycle; a cycle ends early when
    the Givens estimate meets the same bound) or after maxit Arnoldi steps.
    Synchronises the stream at every cycle end and fills *info (may be NULL).
-   restart in [1, 64] (the Gram-Schmidt kernels keep a row of the basis in registers).
+   restart in [1, 256] (the Gram-Schmidt kernels keep one coefficient per basis vector in
+   shared memory; the paper runs restarts of 50 and 100).
    Returns ILU_OK, ILU_ERR_NOT_CONVERGED (x = last iterate), ILU_ERR_TIMEOUT, ILU_ERR_ARG,
    ILU_ERR_OOM, ILU_ERR_CUDA. ||b|| = 0 gives x = 0. */
 ilu_status gmres_solve(void* h, const double* b, double* x, double rtol, int32_t restart,

@@ -22,7 +22,7 @@ namespace ilu2l {
 
 constexpr int kMaxInner = 32;   // inner GMRES steps supported on the device
 constexpr int kMaxRestart = 400;
-constexpr int kMaxRestartGS = 64;  // restart limit of gmres_solve (register-resident Gram-Schmidt)
+constexpr int kMaxRestartGS = 256;  // restart limit of gmres_solve (the Gram-Schmidt kernels' shared arrays)
 
 // ---- a level program: rows of every subdomain scheduled level by level --------------
 // Rows of subdomain s are processed in levels [sub_lvl[s], sub_lvl[s+1]); level e covers

@@ -19,7 +19,7 @@
 
 namespace ilu2l {
 
-constexpr int kMaxJ = 63;  // basis vectors a Gram-Schmidt kernel handles (restart <= 64)
+constexpr int kMaxJ = 255;  // basis vectors a Gram-Schmidt kernel handles (restart <= 256)
 
 // CTA row slices: multiples of 64 rows, so every slice starts 512-byte aligned in a
 // basis vector (leading dimension a multiple of 64) and pairs of rows load as 128 bits.
@@ -159,7 +159,8 @@ __global__ void k_fg_scale0(FgDev f, int n) {
 //    one partial; the sub-slice partials of a vector are added in order.
 //  * Updates w -= V h: one row pair per thread, eight basis vectors in flight, the terms
 //    subtracted in the order i = 0..j.
-constexpr int kMaxTasks = 8 * (kMaxJ + 1);
+// dot tasks per CTA: (j + 1) * max(1, nw / (j + 1)) <= max(j + 1, nw), nw <= 8 warps
+constexpr int kMaxTasks = (kMaxJ + 1 > 8) ? kMaxJ + 1 : 8;
 
 // spart[i] (i <= j, shared) = sum over the CTA's rows of V_i[r] w[r]
 __device__ __forceinline__ void cta_dots(const double* __restrict__ V, int64_t ld, const double* w, int r0, int r1,

@@ -473,6 +473,9 @@ def test_bad_vectors_are_rejected(ilu):
     ("conv3d", CONFIGS[8], "fp32", 50),
     ("conv3d", CONFIGS[9], "fp64", 30),
     ("aniso2d_ragged", CONFIGS[9], "fp32", 50),
+    # restarts the paper uses beyond 64 (FGMRES(100), Sec. 4.2-4.4) and the limit 256
+    ("aniso2d_ragged", CONFIGS[0], "fp64", 100),
+    ("poisson64", CONFIGS[0], "fp64", 256),
 ])
 @pytest.mark.parametrize("graphs", [True, False])
 def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):
@@ -499,6 +502,18 @@ def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):
     x.fill_(3.0)
     info3 = ilu.gmres_solve(h, torch.zeros_like(b), x, rtol=1e-8, restart=restart)
     assert info3["status"] == 0 and not x.any()
+    h.close()
+
+
+def test_restart_limit(ilu):
+    pr = _prob("poisson64")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp64", **CONFIGS[0]))
+    b = _dev(pr.b)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(ilu.IluError):
+        ilu.gmres_solve(h, b, x, rtol=1e-8, restart=257, maxit=100)
+    info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=256, maxit=5000)
+    assert info["status"] == 0 and info["rel_res_true"] <= 1e-8
     h.close()
 
 
