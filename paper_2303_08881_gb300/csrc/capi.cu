@@ -78,8 +78,8 @@ static void ctl_give(FgCtl* c) {
     g_ctl_free.push_back(c);
 }
 
-template <class T>
-cudaError_t upload(Handle& h, T** dst, const std::vector<T>& src) {
+template <class T, class A>
+cudaError_t upload(Handle& h, T** dst, const std::vector<T, A>& src) {
     cudaError_t e = cudaSuccess;
     *dst = h.alloc<T>(src.size(), &e);
     if (!*dst) return e;
@@ -175,11 +175,11 @@ ilu_status device_setup_t(Handle& h) {
             CK(launch_pack_stream<T>(S, dvoff, dvsrc, ddoff, ddsrc, h.d_vals, B.blob, h.st));
             CK(cudaStreamSynchronize(h.st));
             for (void* q : {(void*)dvoff, (void*)dvsrc, (void*)ddoff, (void*)ddsrc}) h.release(q);
-            std::vector<uint8_t>().swap(S.blob);
-            std::vector<int64_t>().swap(S.voff);
-            std::vector<int64_t>().swap(S.doff);
-            std::vector<int32_t>().swap(S.vsrc);
-            std::vector<int32_t>().swap(S.dsrc);
+            decltype(S.blob)().swap(S.blob);
+            decltype(S.voff)().swap(S.voff);
+            decltype(S.doff)().swap(S.doff);
+            decltype(S.vsrc)().swap(S.vsrc);
+            decltype(S.dsrc)().swap(S.dsrc);
         }
     }
     if (h.variant == ILU_VARIANT_BJ) {

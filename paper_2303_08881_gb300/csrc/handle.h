@@ -15,17 +15,23 @@ enum ProgId { PR_BJ = 0, PR_FWD = 1, PR_S = 2, PR_BWD = 3, PR_FWDS = 4, PR_COUNT
 
 // A factor's sparsity pattern over all Q rows (rows outside the factor are empty).
 // Values live in the handle's value array at [base + k] for pattern entry k.
+// A factor pattern in Q order, as a view: rp[n + 1], ci[nnz] (local columns), dpos[n]
+// (diagonal entry or -1) point into arrays the handle owns (the local blocks' own q_*
+// arrays, or the host ILUT pattern); base = offset of its values in the value array.
 struct FPat {
-    std::vector<int32_t> rp, ci, dpos;  // ci: local column; dpos: diagonal entry or -1
+    const int32_t* rp = nullptr;
+    const int32_t* ci = nullptr;
+    const int32_t* dpos = nullptr;
+    int64_t nnz = 0;
     int64_t base = 0;
 };
 
 // A level program laid out as TMA chunks (stream_layout.h) for one index width.
 struct StreamHost {
-    std::vector<uint8_t> blob;        // chunks of every subdomain, kChunk bytes each
-    std::vector<int32_t> ch0;         // p+1: subdomain s owns chunks [ch0[s], ch0[s+1])
-    std::vector<int64_t> voff, doff;  // byte offsets of value / pivot-inverse slots
-    std::vector<int32_t> vsrc, dsrc;  // their sources in the value array
+    rawvec<uint8_t> blob;        // chunks of every subdomain, kChunk bytes each
+    std::vector<int32_t> ch0;    // p+1: subdomain s owns chunks [ch0[s], ch0[s+1])
+    rawvec<int64_t> voff, doff;  // byte offsets of value / pivot-inverse slots
+    rawvec<int32_t> vsrc, dsrc;  // their sources in the value array
     uint32_t chunk = 8192;
     int idx_bytes = 2, val_bytes = 4;
     int rw = 4;                       // entries per row record (compile-time width on the device)
@@ -91,6 +97,7 @@ struct Handle {
     FPat apat;             // pattern of the local blocks A_s themselves
     bool lev_ready = false;  // lev / nlev computed (on the first introspection call)
     std::vector<double> f1_host_vals;  // ILUT values (host-computed factor F1)
+    std::vector<int32_t> f1_rp, f1_ci, f1_dpos;  // its pattern (f1 views it)
     int64_t a_base = 0;    // region of the original local values in the value array
     int64_t nvals = 0;
     ProgHost prog[PR_COUNT];

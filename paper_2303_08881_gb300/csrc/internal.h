@@ -13,7 +13,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ilu2l.h"
@@ -29,8 +31,32 @@ constexpr int kMaxRestartGS = 256;  // restart limit of gmres_solve (the Gram-Sc
 // packed rows [lvl_ptr[e], lvl_ptr[e+1]); packed row k updates x[prow[k]] =
 // (x[prow[k]] - sum_q pval[q] * x[pcol[q]]) * pdinv[k] over q in [pptr[k], pptr[k+1]).
 // Indices are local to the subdomain's working vector (offset by the program's base).
+// std::allocator whose value-less construct leaves the element uninitialised: resize()
+// then does not write the memory, and the threads that fill a large array fault its pages
+// in themselves, in parallel
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... Args>
+    void construct(U* p, Args&&... args) {
+        ::new ((void*)p) U(std::forward<Args>(args)...);
+    }
+};
+template <class T>
+using rawvec = std::vector<T, NoInitAlloc<T>>;
+
 struct ProgHost {
-    std::vector<int32_t> sub_lvl, lvl_ptr, prow, pptr, pcol, psrc, pdsrc;
+    rawvec<int32_t> sub_lvl, lvl_ptr, prow, pptr, pcol, psrc, pdsrc;
     int32_t max_level_rows = 0, max_levels = 0;
     int64_t nnz() const { return (int64_t)pcol.size(); }
 };

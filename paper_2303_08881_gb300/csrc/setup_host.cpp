@@ -6,6 +6,7 @@
 // scheduling analysis, L\U stored in the pattern), Sec. 3.2 (local blocks Eq. localA,
 // factor extraction L_B, U_B, L_S, U_S, W, Z, the off-diagonal blocks of S, Eq. SS).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -94,6 +95,57 @@ void prog_close_level(ProgHost& P) {
     const int32_t rows = (int32_t)P.prow.size() - P.lvl_ptr.back();
     P.max_level_rows = std::max(P.max_level_rows, rows);
     P.lvl_ptr.push_back((int32_t)P.prow.size());
+}
+
+// fn(t, s0, s1) on up to 16 host threads, thread t taking the contiguous subdomains
+// [s0, s1); returns the number of ranges used
+template <class Fn>
+int for_ranges(int32_t p, Fn fn) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    nt = std::max(1u, std::min<unsigned>(nt, (unsigned)std::max(p, 1)));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; t++)
+        th.emplace_back(fn, (int)t, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
+    for (auto& t : th) t.join();
+    return (int)nt;
+}
+
+// D = the fragments fr[0..nf) (each from prog_init over consecutive subdomain ranges)
+// one after the other, their level, row and entry indices shifted; the arrays are sized
+// once and every fragment is copied by its own host thread
+void prog_concat(ProgHost& D, const std::vector<const ProgHost*>& fr) {
+    const size_t nf = fr.size();
+    std::vector<size_t> sb(nf + 1, 0), lv(nf + 1, 0), rw(nf + 1, 0), en(nf + 1, 0);
+    for (size_t t = 0; t < nf; t++) {
+        sb[t + 1] = sb[t] + fr[t]->sub_lvl.size() - 1;
+        lv[t + 1] = lv[t] + fr[t]->lvl_ptr.size() - 1;
+        rw[t + 1] = rw[t] + fr[t]->prow.size();
+        en[t + 1] = en[t] + fr[t]->pcol.size();
+    }
+    prog_init(D);
+    D.sub_lvl.resize(sb[nf] + 1);
+    D.lvl_ptr.resize(lv[nf] + 1);
+    D.pptr.resize(rw[nf] + 1);
+    D.prow.resize(rw[nf]);
+    D.pdsrc.resize(rw[nf]);
+    D.pcol.resize(en[nf]);
+    D.psrc.resize(en[nf]);
+    for_ranges((int32_t)nf, [&](int, int32_t t0, int32_t t1) {
+        for (int32_t t = t0; t < t1; t++) {
+            const ProgHost& F = *fr[t];
+            for (size_t i = 1; i < F.sub_lvl.size(); i++) D.sub_lvl[sb[t] + i] = F.sub_lvl[i] + (int32_t)lv[t];
+            for (size_t i = 1; i < F.lvl_ptr.size(); i++) D.lvl_ptr[lv[t] + i] = F.lvl_ptr[i] + (int32_t)rw[t];
+            for (size_t i = 1; i < F.pptr.size(); i++) D.pptr[rw[t] + i] = F.pptr[i] + (int32_t)en[t];
+            std::copy(F.prow.begin(), F.prow.end(), D.prow.begin() + rw[t]);
+            std::copy(F.pdsrc.begin(), F.pdsrc.end(), D.pdsrc.begin() + rw[t]);
+            std::copy(F.pcol.begin(), F.pcol.end(), D.pcol.begin() + en[t]);
+            std::copy(F.psrc.begin(), F.psrc.end(), D.psrc.begin() + en[t]);
+        }
+    });
+    for (size_t t = 0; t < nf; t++) {
+        D.max_level_rows = std::max(D.max_level_rows, fr[t]->max_level_rows);
+        D.max_levels = std::max(D.max_levels, fr[t]->max_levels);
+    }
 }
 
 void prog_push_row(ProgHost& P, const FPat& F, int32_t q0, int32_t r, int32_t clo, int32_t chi,
@@ -323,12 +375,6 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     if (nt_fit < 32 || chunk > (1u << 20)) return false;
     S.nt = std::min(S.nt, std::min(nt_fit, kMaxConsumers));
     const uint32_t nt = (uint32_t)S.nt;
-    auto put = [&](size_t off, uint32_t v, int bytes) {  // little-endian, like the device
-        if (bytes == 4)
-            std::memcpy(&S.blob[off], &v, 4);
-        else
-            for (int b = 0; b < bytes; b++) S.blob[off + b] = (uint8_t)(v >> (8 * b));
-    };
     struct Piece {
         int32_t k;      // packed row (-1: skip record, a hole in a merged wave)
         int32_t q0, n;  // entries [q0, q0+n) of the row
@@ -352,197 +398,247 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     int32_t maxpos = 0;
     for (int32_t r : P.prow) maxpos = std::max(maxpos, r);
     for (int32_t c : P.pcol) maxpos = std::max(maxpos, c);
-    // per slot, within the current stretch: writer thread, reader thread (-2: several)
-    std::vector<int32_t> wep((size_t)maxpos + 1, -1), wth((size_t)maxpos + 1, -1);
-    std::vector<int32_t> rep((size_t)maxpos + 1, -1), rth((size_t)maxpos + 1, -1);
-    std::vector<int32_t> used(nt), assign;
-    int32_t epoch = 0;
-    std::vector<Piece> pieces;
-    std::vector<Wave> waves;
-    std::vector<Piece> sub;
-    int64_t nchunks = 0;
-    S.waves = 0;
-    S.segments = 0;
-    S.records = 0;
-    S.skips = 0;
-    S.max_barriers = 0;
-    S.max_levels_sub = 0;
-    auto mark = [&](const Piece& pc, int32_t t) {
-        auto rd = [&](int32_t pos) {
-            if (rep[pos] != epoch) {
-                rep[pos] = epoch;
-                rth[pos] = t;
-            } else if (rth[pos] != t) {
-                rth[pos] = -2;
-            }
-        };
-        for (int32_t q = 0; q < pc.n; q++) rd(P.pcol[P.pptr[pc.k] + pc.q0 + q]);
-        const int32_t w = P.prow[pc.k];
-        rd(w);
-        wep[w] = epoch;
-        wth[w] = t;
+    // Subdomains are independent: host threads pack contiguous ranges of them into
+    // fragments (offsets relative to the fragment), appended in subdomain order below.
+    struct Frag {
+        rawvec<uint8_t> blob;
+        std::vector<int32_t> nch;  // chunks of each subdomain of the range
+        rawvec<int64_t> voff, doff;
+        rawvec<int32_t> vsrc, dsrc;
+        int64_t waves = 0, segments = 0, records = 0, skips = 0, max_barriers = 0, max_levels_sub = 0;
+        bool ok = true;
     };
-    for (int32_t s = 0; s < p; s++) {
-        // pieces and waves of this subdomain, in program order
-        pieces.clear();
-        waves.clear();
-        epoch++;
-        S.max_levels_sub = std::max<int64_t>(S.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
-        for (int32_t e = P.sub_lvl[s]; e < P.sub_lvl[s + 1]; e++) {
-            const int32_t k0 = P.lvl_ptr[e], k1 = P.lvl_ptr[e + 1];
-            int32_t np = 1;
-            for (int32_t k = k0; k < k1; k++) np = std::max(np, (P.pptr[k + 1] - P.pptr[k] + RW - 1) / RW);
-            for (int32_t j = 0; j < np; j++) {  // sub-level j: piece j of every row that has one
-                sub.clear();
-                for (int32_t k = k0; k < k1; k++) {
-                    const int32_t n = P.pptr[k + 1] - P.pptr[k];
-                    const int32_t npk = std::max(1, (n + RW - 1) / RW);
-                    if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1});
-                }
-                bool merge = !waves.empty() && sub.size() <= nt;
-                if (merge) {
-                    std::fill(used.begin(), used.end(), -1);
-                    assign.assign(sub.size(), -1);
-                    for (size_t i = 0; i < sub.size() && merge; i++) {
-                        const Piece& pc = sub[i];
-                        int32_t t = -1;
-                        auto need = [&](int32_t u) {
-                            if (u == -2 || (t >= 0 && t != u)) merge = false;
-                            t = u;
-                        };
-                        for (int32_t q = 0; q < pc.n; q++) {
-                            const int32_t c = P.pcol[P.pptr[pc.k] + pc.q0 + q];
-                            if (wep[c] == epoch) need(wth[c]);
-                        }
-                        const int32_t w = P.prow[pc.k];
-                        if (wep[w] == epoch) need(wth[w]);
-                        if (rep[w] == epoch) need(rth[w]);
-                        if (!merge) break;
-                        if (t >= 0) {
-                            if (used[t] >= 0) {
-                                merge = false;
-                                break;
-                            }
-                            used[t] = (int32_t)i;
-                            assign[i] = t;
-                        }
-                    }
-                    if (merge) {  // free pieces onto the lowest idle threads
-                        uint32_t t = 0;
-                        for (size_t i = 0; i < sub.size(); i++) {
-                            if (assign[i] >= 0) continue;
-                            while (used[t] >= 0) t++;
-                            used[t] = (int32_t)i;
-                            assign[i] = (int32_t)t;
-                        }
-                    }
-                }
-                if (merge) {
-                    uint32_t width = 0;
-                    for (int32_t a : assign) width = std::max(width, (uint32_t)a + 1);
-                    const size_t p0 = pieces.size();
-                    for (uint32_t t = 0; t < width; t++) {
-                        if (used[t] >= 0) {
-                            const Piece& pc = sub[(size_t)used[t]];
-                            pieces.push_back(pc);
-                            mark(pc, (int32_t)t);
-                        } else {
-                            pieces.push_back({-1, 0, 0, false});
-                        }
-                    }
-                    waves.push_back({p0, pieces.size(), false});
-                } else {
-                    if (!waves.empty()) waves.back().sync = true;
-                    epoch++;
-                    for (size_t t = 0; t < sub.size(); t += nt) {
-                        const size_t t1 = std::min(sub.size(), t + nt);
-                        waves.push_back({pieces.size() + t, pieces.size() + t1, false});
-                    }
-                    for (size_t i = 0; i < sub.size(); i++) mark(sub[i], (int32_t)(i % nt));
-                    pieces.insert(pieces.end(), sub.begin(), sub.end());
-                }
-            }
-        }
-        if (!waves.empty()) waves.back().sync = true;
-        int64_t barriers = 0;
-        for (const Wave& W : waves) barriers += W.sync;
-        S.max_barriers = std::max(S.max_barriers, barriers);
-        S.waves += (int64_t)waves.size();
-        // Pack the waves into chunks as segments: runs of consecutive waves of one width
-        // (a narrower wave joins when the padding at most doubles it), never crossing a
-        // barrier or a chunk.
-        struct Seg {
-            size_t w0, w1;
-            uint32_t width;
-            bool barrier;
+    std::vector<Frag> frag(16);
+    const int nfrag = for_ranges(p, [&](int ti, int32_t s0, int32_t s1) {
+        Frag& F = frag[ti];
+        auto put = [&](size_t off, uint32_t v, int bytes) {  // little-endian, like the device
+            if (bytes == 4)
+                std::memcpy(&F.blob[off], &v, 4);
+            else
+                for (int b = 0; b < bytes; b++) F.blob[off + b] = (uint8_t)(v >> (8 * b));
         };
-        std::vector<Seg> segs;
-        size_t wi = 0;
-        while (wi < waves.size()) {
-            segs.clear();
-            size_t recs = 0;
-            auto fits = [&](size_t nseg, size_t nrec) {
-                return kChunkHdr + al((uint32_t)(kSegEntry * nseg), 16) + nrec * RL.bytes <= chunk;
-            };
-            while (wi < waves.size()) {
-                const uint32_t ww = (uint32_t)(waves[wi].p1 - waves[wi].p0);
-                const bool join = !segs.empty() && !segs.back().barrier && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
-                                  (ww == segs.back().width || (ww < segs.back().width && segs.back().width <= 2 * ww));
-                if (join) {
-                    if (!fits(segs.size(), recs + segs.back().width)) break;
-                    segs.back().w1 = wi + 1;
-                    recs += segs.back().width;
-                } else {
-                    if (!fits(segs.size() + 1, recs + ww)) break;
-                    segs.push_back({wi, wi + 1, ww, false});
-                    recs += ww;
+        // per slot, within the current stretch: writer thread, reader thread (-2: several)
+        std::vector<int32_t> wep((size_t)maxpos + 1, -1), wth((size_t)maxpos + 1, -1);
+        std::vector<int32_t> rep((size_t)maxpos + 1, -1), rth((size_t)maxpos + 1, -1);
+        std::vector<int32_t> used(nt), assign;
+        int32_t epoch = 0;
+        std::vector<Piece> pieces;
+        std::vector<Wave> waves;
+        std::vector<Piece> sub;
+        auto mark = [&](const Piece& pc, int32_t t) {
+            auto rd = [&](int32_t pos) {
+                if (rep[pos] != epoch) {
+                    rep[pos] = epoch;
+                    rth[pos] = t;
+                } else if (rth[pos] != t) {
+                    rth[pos] = -2;
                 }
-                if (waves[wi].sync) segs.back().barrier = true;
-                wi++;
-            }
-            if (segs.empty()) return false;  // a wave wider than a chunk (excluded by nt_fit)
-            const size_t cb = S.blob.size();
-            S.blob.resize(cb + chunk, 0);
-            nchunks++;
-            S.segments += (int64_t)segs.size();
-            put(cb, (uint32_t)segs.size(), 4);
-            size_t roff = kChunkHdr + al((uint32_t)(kSegEntry * segs.size()), 16);
-            for (size_t g = 0; g < segs.size(); g++) {
-                const Seg& G = segs[g];
-                put(cb + kChunkHdr + kSegEntry * g, (uint32_t)(roff / 16) | (G.width << 16), 4);
-                put(cb + kChunkHdr + kSegEntry * g + 4, (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u), 4);
-                for (size_t w = G.w0; w < G.w1; w++) {
-                    const Wave& W = waves[w];
-                    for (uint32_t t = 0; t < G.width; t++) {
-                        const size_t rb = cb + roff;
-                        roff += RL.bytes;
-                        S.records++;
-                        const Piece* pc = (W.p0 + t < W.p1) ? &pieces[W.p0 + t] : nullptr;
-                        if (!pc || pc->k < 0) {  // skip record: reads slot 0, stores nothing
-                            S.skips++;
-                            put(rb, kRecSkip, 4);
-                            continue;
+            };
+            for (int32_t q = 0; q < pc.n; q++) rd(P.pcol[P.pptr[pc.k] + pc.q0 + q]);
+            const int32_t w = P.prow[pc.k];
+            rd(w);
+            wep[w] = epoch;
+            wth[w] = t;
+        };
+        for (int32_t s = s0; s < s1; s++) {
+            // pieces and waves of this subdomain, in program order
+            pieces.clear();
+            waves.clear();
+            epoch++;
+            int64_t nchunks = 0;
+            F.max_levels_sub = std::max<int64_t>(F.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
+            for (int32_t e = P.sub_lvl[s]; e < P.sub_lvl[s + 1]; e++) {
+                const int32_t k0 = P.lvl_ptr[e], k1 = P.lvl_ptr[e + 1];
+                int32_t np = 1;
+                for (int32_t k = k0; k < k1; k++) np = std::max(np, (P.pptr[k + 1] - P.pptr[k] + RW - 1) / RW);
+                for (int32_t j = 0; j < np; j++) {  // sub-level j: piece j of every row that has one
+                    sub.clear();
+                    for (int32_t k = k0; k < k1; k++) {
+                        const int32_t n = P.pptr[k + 1] - P.pptr[k];
+                        const int32_t npk = std::max(1, (n + RW - 1) / RW);
+                        if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1});
+                    }
+                    bool merge = !waves.empty() && sub.size() <= nt;
+                    if (merge) {
+                        std::fill(used.begin(), used.end(), -1);
+                        assign.assign(sub.size(), -1);
+                        for (size_t i = 0; i < sub.size() && merge; i++) {
+                            const Piece& pc = sub[i];
+                            int32_t t = -1;
+                            auto need = [&](int32_t u) {
+                                if (u == -2 || (t >= 0 && t != u)) merge = false;
+                                t = u;
+                            };
+                            for (int32_t q = 0; q < pc.n; q++) {
+                                const int32_t c = P.pcol[P.pptr[pc.k] + pc.q0 + q];
+                                if (wep[c] == epoch) need(wth[c]);
+                            }
+                            const int32_t w = P.prow[pc.k];
+                            if (wep[w] == epoch) need(wth[w]);
+                            if (rep[w] == epoch) need(rth[w]);
+                            if (!merge) break;
+                            if (t >= 0) {
+                                if (used[t] >= 0) {
+                                    merge = false;
+                                    break;
+                                }
+                                used[t] = (int32_t)i;
+                                assign[i] = t;
+                            }
                         }
-                        const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)val_bytes;
-                        put(rb, row_off | ((uint32_t)pc->n << 24), 4);
-                        S.doff.push_back((int64_t)(rb + RL.dinv));
-                        S.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
-                        for (int32_t q = 0; q < RW; q++) {
-                            if (q >= pc->n) {  // unused entry: the row's own slot times a zero value
-                                put(rb + RL.col + (size_t)q * 4, row_off, 4);
+                        if (merge) {  // free pieces onto the lowest idle threads
+                            uint32_t t = 0;
+                            for (size_t i = 0; i < sub.size(); i++) {
+                                if (assign[i] >= 0) continue;
+                                while (used[t] >= 0) t++;
+                                used[t] = (int32_t)i;
+                                assign[i] = (int32_t)t;
+                            }
+                        }
+                    }
+                    if (merge) {
+                        uint32_t width = 0;
+                        for (int32_t a : assign) width = std::max(width, (uint32_t)a + 1);
+                        const size_t p0 = pieces.size();
+                        for (uint32_t t = 0; t < width; t++) {
+                            if (used[t] >= 0) {
+                                const Piece& pc = sub[(size_t)used[t]];
+                                pieces.push_back(pc);
+                                mark(pc, (int32_t)t);
+                            } else {
+                                pieces.push_back({-1, 0, 0, false});
+                            }
+                        }
+                        waves.push_back({p0, pieces.size(), false});
+                    } else {
+                        if (!waves.empty()) waves.back().sync = true;
+                        epoch++;
+                        for (size_t t = 0; t < sub.size(); t += nt) {
+                            const size_t t1 = std::min(sub.size(), t + nt);
+                            waves.push_back({pieces.size() + t, pieces.size() + t1, false});
+                        }
+                        for (size_t i = 0; i < sub.size(); i++) mark(sub[i], (int32_t)(i % nt));
+                        pieces.insert(pieces.end(), sub.begin(), sub.end());
+                    }
+                }
+            }
+            if (!waves.empty()) waves.back().sync = true;
+            int64_t barriers = 0;
+            for (const Wave& W : waves) barriers += W.sync;
+            F.max_barriers = std::max(F.max_barriers, barriers);
+            F.waves += (int64_t)waves.size();
+            // Pack the waves into chunks as segments: runs of consecutive waves of one width
+            // (a narrower wave joins when the padding at most doubles it), never crossing a
+            // barrier or a chunk.
+            struct Seg {
+                size_t w0, w1;
+                uint32_t width;
+                bool barrier;
+            };
+            std::vector<Seg> segs;
+            size_t wi = 0;
+            while (wi < waves.size()) {
+                segs.clear();
+                size_t recs = 0;
+                auto fits = [&](size_t nseg, size_t nrec) {
+                    return kChunkHdr + al((uint32_t)(kSegEntry * nseg), 16) + nrec * RL.bytes <= chunk;
+                };
+                while (wi < waves.size()) {
+                    const uint32_t ww = (uint32_t)(waves[wi].p1 - waves[wi].p0);
+                    const bool join = !segs.empty() && !segs.back().barrier && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
+                                      (ww == segs.back().width || (ww < segs.back().width && segs.back().width <= 2 * ww));
+                    if (join) {
+                        if (!fits(segs.size(), recs + segs.back().width)) break;
+                        segs.back().w1 = wi + 1;
+                        recs += segs.back().width;
+                    } else {
+                        if (!fits(segs.size() + 1, recs + ww)) break;
+                        segs.push_back({wi, wi + 1, ww, false});
+                        recs += ww;
+                    }
+                    if (waves[wi].sync) segs.back().barrier = true;
+                    wi++;
+                }
+                if (segs.empty()) {  // a wave wider than a chunk (excluded by nt_fit)
+                    F.ok = false;
+                    return;
+                }
+                const size_t cb = F.blob.size();
+                F.blob.resize(cb + chunk, 0);
+                nchunks++;
+                F.segments += (int64_t)segs.size();
+                put(cb, (uint32_t)segs.size(), 4);
+                size_t roff = kChunkHdr + al((uint32_t)(kSegEntry * segs.size()), 16);
+                for (size_t g = 0; g < segs.size(); g++) {
+                    const Seg& G = segs[g];
+                    put(cb + kChunkHdr + kSegEntry * g, (uint32_t)(roff / 16) | (G.width << 16), 4);
+                    put(cb + kChunkHdr + kSegEntry * g + 4, (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u), 4);
+                    for (size_t w = G.w0; w < G.w1; w++) {
+                        const Wave& W = waves[w];
+                        for (uint32_t t = 0; t < G.width; t++) {
+                            const size_t rb = cb + roff;
+                            roff += RL.bytes;
+                            F.records++;
+                            const Piece* pc = (W.p0 + t < W.p1) ? &pieces[W.p0 + t] : nullptr;
+                            if (!pc || pc->k < 0) {  // skip record: reads slot 0, stores nothing
+                                F.skips++;
+                                put(rb, kRecSkip, 4);
                                 continue;
                             }
-                            const int32_t src = P.pptr[pc->k] + pc->q0 + q;
-                            put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
-                            S.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
-                            S.vsrc.push_back(P.psrc[src]);
+                            const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)val_bytes;
+                            put(rb, row_off | ((uint32_t)pc->n << 24), 4);
+                            F.doff.push_back((int64_t)(rb + RL.dinv));
+                            F.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
+                            for (int32_t q = 0; q < RW; q++) {
+                                if (q >= pc->n) {  // unused entry: the row's own slot times a zero value
+                                    put(rb + RL.col + (size_t)q * 4, row_off, 4);
+                                    continue;
+                                }
+                                const int32_t src = P.pptr[pc->k] + pc->q0 + q;
+                                put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
+                                F.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
+                                F.vsrc.push_back(P.psrc[src]);
+                            }
                         }
                     }
                 }
             }
+            F.nch.push_back((int32_t)nchunks);
         }
-        S.ch0.push_back((int32_t)nchunks);
+    });
+    // the fragments one after the other: arrays sized once, one host thread per fragment
+    S.waves = S.segments = S.records = S.skips = S.max_barriers = S.max_levels_sub = 0;
+    std::vector<size_t> nb(nfrag + 1, 0), nv(nfrag + 1, 0), nd(nfrag + 1, 0);
+    for (int t = 0; t < nfrag; t++) {
+        const Frag& F = frag[t];
+        if (!F.ok) return false;
+        nb[t + 1] = nb[t] + F.blob.size();
+        nv[t + 1] = nv[t] + F.voff.size();
+        nd[t + 1] = nd[t] + F.doff.size();
+        for (int32_t c : F.nch) S.ch0.push_back(S.ch0.back() + c);
+        S.waves += F.waves;
+        S.segments += F.segments;
+        S.records += F.records;
+        S.skips += F.skips;
+        S.max_barriers = std::max(S.max_barriers, F.max_barriers);
+        S.max_levels_sub = std::max(S.max_levels_sub, F.max_levels_sub);
     }
+    S.blob.resize(nb[nfrag]);
+    S.voff.resize(nv[nfrag]);
+    S.vsrc.resize(nv[nfrag]);
+    S.doff.resize(nd[nfrag]);
+    S.dsrc.resize(nd[nfrag]);
+    for_ranges(nfrag, [&](int, int32_t t0, int32_t t1) {
+        for (int32_t t = t0; t < t1; t++) {
+            const Frag& F = frag[t];
+            const int64_t base = (int64_t)nb[t];
+            std::copy(F.blob.begin(), F.blob.end(), S.blob.begin() + nb[t]);
+            for (size_t i = 0; i < F.voff.size(); i++) S.voff[nv[t] + i] = F.voff[i] + base;
+            std::copy(F.vsrc.begin(), F.vsrc.end(), S.vsrc.begin() + nv[t]);
+            for (size_t i = 0; i < F.doff.size(); i++) S.doff[nd[t] + i] = F.doff[i] + base;
+            std::copy(F.dsrc.begin(), F.dsrc.end(), S.dsrc.begin() + nd[t]);
+        }
+    });
     if (S.blob.empty()) S.blob.resize(16, 0);
     return true;
 }
@@ -773,12 +869,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                     }
                 }
         };
-        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        nt = std::min<unsigned>(nt, (unsigned)p);
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nt; t++)
-            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
-        for (auto& t : th) t.join();
+        for_ranges(p, [&](int, int32_t s0, int32_t s1) { work(s0, s1); });
     }
 
     // ---- Q order: subdomain s owns [qoff[s], qoff[s+1]) = [interior_s ; interface_s]
@@ -827,9 +918,10 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     h.coff_ci.resize(h.coff_rp[h.n2]);
     h.coff_v.resize(h.coff_rp[h.n2]);
     h.nnz_coff = h.coff_rp[h.n2];
-    {
+    // rows are independent from here: host threads fill contiguous row ranges
+    for_ranges(n, [&](int, int32_t qa, int32_t qb) {
         std::vector<std::pair<int32_t, double>> row;
-        for (int32_t q = 0; q < n; q++) {
+        for (int32_t q = qa; q < qb; q++) {
             const int32_t i = h.q_orig[q];
             row.clear();
             for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
@@ -864,7 +956,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 }
             }
         }
-    }
+    });
 
     // ---- ILU(k) / MILU(k): every local block is stored in its level-k fill pattern with
     //      zeros at the fill positions, so the device ILU(0) / MILU(0) of the stored block
@@ -877,12 +969,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 iluk_block(h.q_rp, h.q_ci, h.qoff[s], h.qoff[s + 1] - h.qoff[s], h.o.fill_level, brp[s], bci[s],
                            bsrc[s]);
         };
-        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        nt = std::min<unsigned>(nt, (unsigned)p);
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nt; t++)
-            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
-        for (auto& t : th) t.join();
+        for_ranges(p, [&](int, int32_t s0, int32_t s1) { work(s0, s1); });
         int64_t tot = 0;
         for (int32_t s = 0; s < p; s++) tot += (int64_t)bci[s].size();
         if (tot >= (int64_t)INT32_MAX) return ILU_ERR_TOO_LARGE;
@@ -908,10 +995,11 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     }
 
     // ---- factor patterns and value regions [F1 | F2 | A_local]
-    FPat apat;
-    apat.rp = h.q_rp;
-    apat.ci = h.q_ci;
-    apat.dpos = h.q_dpos;
+    FPat apat;  // views of the local blocks' arrays, final from here on
+    apat.rp = h.q_rp.data();
+    apat.ci = h.q_ci.data();
+    apat.dpos = h.q_dpos.data();
+    apat.nnz = nnzQ;
     const bool schur = (h.variant != ILU_VARIANT_BJ);  // two-level structure (SCHUR, RAP)
     const bool rap = (h.variant == ILU_VARIANT_RAP);
     const bool f1_ilut = (h.kB == ILU_FACT_ILUT);
@@ -947,19 +1035,14 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                                      &pert[s]);
             }
         };
-        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        nt = std::min<unsigned>(nt, (unsigned)p);
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nt; t++)
-            th.emplace_back(work, (int32_t)((int64_t)p * t / nt), (int32_t)((int64_t)p * (t + 1) / nt));
-        for (auto& t : th) t.join();
+        for_ranges(p, [&](int, int32_t s0, int32_t s1) { work(s0, s1); });
         for (int32_t s = 0; s < p; s++) {
             if (stat[s] != ILU_OK) return (ilu_status)stat[s];
             h.npert += pert[s];
         }
-        h.f1.rp.assign(n + 1, 0);
-        h.f1.dpos.assign(n, -1);
-        h.f1.ci.clear();
+        h.f1_rp.assign(n + 1, 0);
+        h.f1_dpos.assign(n, -1);
+        h.f1_ci.clear();
         h.f1_host_vals.clear();
         for (int32_t s = 0; s < p; s++) {
             const int32_t q0 = h.qoff[s];
@@ -969,17 +1052,21 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 if (r < (int32_t)res[s].size()) {
                     const IlutRow& ro = res[s][r];
                     for (size_t t = 0; t < ro.ci.size(); t++) {
-                        if (ro.ci[t] == r) h.f1.dpos[q] = (int32_t)h.f1.ci.size();
-                        h.f1.ci.push_back(ro.ci[t]);
+                        if (ro.ci[t] == r) h.f1_dpos[q] = (int32_t)h.f1_ci.size();
+                        h.f1_ci.push_back(ro.ci[t]);
                         h.f1_host_vals.push_back(ro.v[t]);
                     }
                 }
-                h.f1.rp[q + 1] = (int32_t)h.f1.ci.size();
+                h.f1_rp[q + 1] = (int32_t)h.f1_ci.size();
             }
         }
+        h.f1.rp = h.f1_rp.data();
+        h.f1.ci = h.f1_ci.data();
+        h.f1.dpos = h.f1_dpos.data();
+        h.f1.nnz = (int64_t)h.f1_ci.size();
         h.f1.base = 0;
     }
-    const int64_t nnz1 = (int64_t)h.f1.ci.size();
+    const int64_t nnz1 = h.f1.nnz;
     h.f2_alias = !(schur && (f1_ilut || h.kS != h.kB));
     if (h.f2_alias) {
         h.f2 = h.f1;
@@ -998,85 +1085,98 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     h.lev_ready = false;
     for (int pr = 0; pr < PR_COUNT; pr++) prog_init(h.prog[pr]);
     prog_init(h.numprog);
-    std::vector<int32_t> lev(h.max_ns + 1, 0);
     const bool wz = (h.form == ILU_FORM_WZ);
-    for (int32_t s = 0; s < p; s++) {
-        const int32_t q0 = h.qoff[s];
-        const int32_t ni = h.nint[s];
-        const int32_t ns = h.qoff[s + 1] - q0;
-        // numeric factorisation schedule: L levels of the pattern of A_s (all local rows)
-        {
-            ProgHost& N = h.numprog;
-            const int nl = window_levels(apat, q0, 0, ns, 0, ns, false, lev);
-            std::vector<std::vector<int32_t>> byl(nl);
-            for (int32_t r = 0; r < ns; r++) byl[lev[r]].push_back(r);
-            for (int l = 0; l < nl; l++) {
-                for (int32_t r : byl[l]) N.prow.push_back(r);
-                prog_close_level(N);
+    // each thread builds the programs of a contiguous range of subdomains; the fragments
+    // are appended in subdomain order, so the result equals a sequential build
+    std::vector<std::array<ProgHost, PR_COUNT + 1>> frag(16);
+    const int nfrag = for_ranges(p, [&](int t, int32_t s0, int32_t s1) {
+        std::array<ProgHost, PR_COUNT + 1>& G = frag[t];
+        for (auto& P : G) prog_init(P);
+        std::vector<int32_t> lev(h.max_ns + 1, 0);
+        for (int32_t s = s0; s < s1; s++) {
+            const int32_t q0 = h.qoff[s];
+            const int32_t ni = h.nint[s];
+            const int32_t ns = h.qoff[s + 1] - q0;
+            // numeric factorisation schedule: L levels of the pattern of A_s (all local rows)
+            {
+                ProgHost& N = G[PR_COUNT];
+                const int nl = window_levels(apat, q0, 0, ns, 0, ns, false, lev);
+                std::vector<std::vector<int32_t>> byl(nl);
+                for (int32_t r = 0; r < ns; r++) byl[lev[r]].push_back(r);
+                for (int l = 0; l < nl; l++) {
+                    for (int32_t r : byl[l]) N.prow.push_back(r);
+                    prog_close_level(N);
+                }
+                N.sub_lvl.push_back((int32_t)N.lvl_ptr.size() - 1);
+                N.max_levels = std::max(N.max_levels, nl);
             }
-            N.sub_lvl.push_back((int32_t)N.lvl_ptr.size() - 1);
-            N.max_levels = std::max(N.max_levels, nl);
-        }
-        if (!schur || rap) {  // block Jacobi, or the smoother of the multiplicative variant
-            ProgHost& P = h.prog[PR_BJ];
-            int a = prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, false, 0, lev);
-            a += prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, true, 0, lev);
-            P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-            P.max_levels = std::max(P.max_levels, a);
-        }
-        if (schur) {
-            // the B parts (L_B, U_B, W, Z): factor_B's factorisation for SCHUR; for RAP the
-            // factorisation that defines R and P (Eq. wzinmilu), factor_S's
-            const FPat& fb = rap ? h.f2 : h.f1;
-            {   // forward: f' = L_B^{-1} f then g' = g - W f'   (W/Z)
-                //          t = U_B^{-1} L_B^{-1} f then g' = g - E t   (E/F)
-                ProgHost& P = h.prog[PR_FWD];
-                int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
-                if (wz) {
-                    a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
-                } else {
+            if (!schur || rap) {  // block Jacobi, or the smoother of the multiplicative variant
+                ProgHost& P = G[PR_BJ];
+                int a = prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, false, 0, lev);
+                a += prog_add_tri(P, h.f1, q0, 0, ns, 0, ns, true, 0, lev);
+                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                P.max_levels = std::max(P.max_levels, a);
+            }
+            if (schur) {
+                // the B parts (L_B, U_B, W, Z): factor_B's factorisation for SCHUR; for RAP the
+                // factorisation that defines R and P (Eq. wzinmilu), factor_S's
+                const FPat& fb = rap ? h.f2 : h.f1;
+                {   // forward: f' = L_B^{-1} f then g' = g - W f'   (W/Z)
+                    //          t = U_B^{-1} L_B^{-1} f then g' = g - E t   (E/F)
+                    ProgHost& P = G[PR_FWD];
+                    int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
+                    if (wz) {
+                        a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
+                    } else {
+                        a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
+                        a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                    }
+                    P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                    P.max_levels = std::max(P.max_levels, a);
+                }
+                {   // forward and the first local Schur solve in one program (base 0)
+                    ProgHost& P = G[PR_FWDS];
+                    int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
+                    if (wz) {
+                        a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
+                    } else {
+                        a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
+                        a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                    }
+                    a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
+                    a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, 0, lev);
+                    P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                    P.max_levels = std::max(P.max_levels, a);
+                }
+                {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni)
+                    ProgHost& P = G[PR_S];
+                    int a = prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, ni, lev);
+                    a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, ni, lev);
+                    P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                    P.max_levels = std::max(P.max_levels, a);
+                }
+                {   // backward: u = U_B^{-1}(f' - Z y)  (W/Z);  u = U_B^{-1} L_B^{-1}(f - F y) (E/F)
+                    ProgHost& P = G[PR_BWD];
+                    int a = 0;
+                    if (wz) {
+                        a += prog_add_single(P, fb, q0, 0, ni, ni, ns, 0);
+                    } else {
+                        a += prog_add_single(P, apat, q0, 0, ni, ni, ns, 0);
+                        a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
+                    }
                     a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
-                    a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                    P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                    P.max_levels = std::max(P.max_levels, a);
                 }
-                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-                P.max_levels = std::max(P.max_levels, a);
-            }
-            {   // forward and the first local Schur solve in one program (base 0)
-                ProgHost& P = h.prog[PR_FWDS];
-                int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
-                if (wz) {
-                    a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
-                } else {
-                    a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
-                    a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
-                }
-                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
-                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, 0, lev);
-                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-                P.max_levels = std::max(P.max_levels, a);
-            }
-            {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni)
-                ProgHost& P = h.prog[PR_S];
-                int a = prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, ni, lev);
-                a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, ni, lev);
-                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-                P.max_levels = std::max(P.max_levels, a);
-            }
-            {   // backward: u = U_B^{-1}(f' - Z y)  (W/Z);  u = U_B^{-1} L_B^{-1}(f - F y) (E/F)
-                ProgHost& P = h.prog[PR_BWD];
-                int a = 0;
-                if (wz) {
-                    a += prog_add_single(P, fb, q0, 0, ni, ni, ns, 0);
-                } else {
-                    a += prog_add_single(P, apat, q0, 0, ni, ni, ns, 0);
-                    a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
-                }
-                a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
-                P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-                P.max_levels = std::max(P.max_levels, a);
             }
         }
+    });
+    for (int pr = 0; pr <= PR_COUNT; pr++) {
+        std::vector<const ProgHost*> fr;
+        for (int t = 0; t < nfrag; t++) fr.push_back(&frag[t][pr]);
+        prog_concat((pr == PR_COUNT) ? h.numprog : h.prog[pr], fr);
     }
+
     // ---- chunked streams of the programs the apply runs (TMA fast path)
     if (h.stream_path) {
         h.idx_bytes = 4;
