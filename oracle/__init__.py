@@ -42,7 +42,7 @@ class _Opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("factor_B", C.c_int), ("factor_S", C.c_int),
                 ("form", C.c_int), ("ilut_tau", C.c_double), ("ilut_p", C.c_int),
                 ("inner_iters", C.c_int), ("pivot_eps", C.c_double), ("local_order", C.c_int),
-                ("fill_level", C.c_int)]
+                ("fill_level", C.c_int), ("l1_block", C.c_int)]
 
 
 _lib = None
@@ -238,7 +238,7 @@ class Oracle:
 
     def __init__(self, n, rowptr, colind, val, part, p, variant="schur", factor_B="ilu0",
                  factor_S="milu0", form="auto", ilut_tau=1e-3, ilut_p=10, inner_iters=3,
-                 pivot_eps=1e-8, local_order="natural", fill_level=0):
+                 pivot_eps=1e-8, local_order="natural", fill_level=0, l1_block=False):
         self._keep = [_i32(rowptr), _i32(colind), _f64(val), _i32(part)]
         o = _Opts()
         lib().orc_opts_default(C.byref(o))
@@ -252,6 +252,7 @@ class Oracle:
         o.pivot_eps = pivot_eps
         o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM}[local_order]
         o.fill_level = int(fill_level)
+        o.l1_block = int(bool(l1_block))
         self.opts = o
         st = C.c_int(0)
         rp, ci, v, pt = self._keep

@@ -847,6 +847,7 @@ void orc_opts_default(orc_opts* o) {
     o->pivot_eps = 1e-8;
     o->local_order = ORC_ORDER_NATURAL;
     o->fill_level = 0;
+    o->l1_block = 0;
 }
 
 static inline int nint_of(const orc_t* h, int s) { return h->int_ptr[s + 1] - h->int_ptr[s]; }
@@ -1059,6 +1060,22 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
         }
         free(row);
         free(fill);
+    }
+
+    /* l1-BJ (Sec. 4.3): the diagonal of each row of A_s gains the absolute values of the
+       row's entries in the off-diagonal blocks; then the usual factorisation of A_s */
+    if (h->o.l1_block != 0 && (h->o.l1_block != 1 || h->o.variant != ORC_BJ)) {
+        st = ORC_ERR_ARG;
+        goto fail;
+    }
+    for (int g = 0; g < n && h->o.l1_block; g++) {
+        int i = h->perm[g], s = part[i], l = g - h->int_ptr[s];
+        double add = 0.0;
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+            if (part[ci[q]] != s) add += fabs(val[q]);
+        csr_t* M = &h->Aloc[s];
+        for (int q = M->rp[l]; q < M->rp[l + 1]; q++)
+            if (M->ci[q] == l) M->v[q] += add;
     }
 
     /* ILU(k) / MILU(k): each local block stored in its level-k pattern, so that ILU(0) /

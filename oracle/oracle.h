@@ -65,6 +65,8 @@ typedef struct orc_opts {
     int fill_level;     /* k >= 0: ILU0 / MILU0 become ILU(k) / MILU(k) (Sec. 4.2-4.4): each
                            local block is stored in its level-k fill pattern, explicit zeros
                            at the fill positions; needs factor_B, factor_S in {ILU0, MILU0} */
+    int l1_block;       /* block Jacobi only: 1 = l1-BJ (Sec. 4.3), every diagonal entry of A_s
+                           increased by the sum of |a_ij| over the columns of other subdomains */
 } orc_opts;
 
 /* ---- primitives on one CSR matrix ---- */
