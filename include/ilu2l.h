@@ -100,6 +100,9 @@ typedef struct {
                              eliminating pivot m of row i gives (i, j) the level
                              lev(i,m) + lev(m,j) + 1, the least wins), zeros at the fill, and
                              factorised in it. ILU_ERR_ARG with factor_B = ILUT. Default 0. */
+    int32_t l1_block;     /* block Jacobi only (else ILU_ERR_ARG): 1 = l1-BJ (Sec. 4.3), every
+                             diagonal entry of A_i increased by the sum of |a_ij| over the columns
+                             of other subdomains before the factorisation. Default 0. */
 } ilu_opts;
 
 typedef struct {

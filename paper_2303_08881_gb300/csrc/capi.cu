@@ -428,6 +428,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->pc_precision = ILU_PREC_FP32;
     o->ordering = ILU_ORDER_NATURAL;
     o->fill_level = 0;
+    o->l1_block = 0;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -487,7 +488,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
         o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
         (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
-        (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT)) {
+        (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
+        (o.l1_block && o.variant != ILU_VARIANT_BJ)) {
         delete h;
         return ILU_ERR_ARG;
     }

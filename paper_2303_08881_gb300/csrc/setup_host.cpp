@@ -924,9 +924,13 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         for (int32_t q = qa; q < qb; q++) {
             const int32_t i = h.q_orig[q];
             row.clear();
+            double l1 = 0.0;  // l1-BJ (Sec. 4.3): |a_ij| over the other subdomains' columns
             for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
                 const int32_t j = A->colind[k];
-                if (part[j] == part[i]) row.emplace_back(loc[j], A->val[k]);
+                if (part[j] == part[i])
+                    row.emplace_back(loc[j], A->val[k]);
+                else
+                    l1 += std::fabs(A->val[k]);
             }
             std::sort(row.begin(), row.end(),
                       [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
@@ -940,6 +944,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 h.q_ci[at] = e.first;
                 h.q_v[at++] = e.second;
             }
+            if (h.o.l1_block) h.q_v[h.q_dpos[q]] += l1;
             if (h.iface[i]) {
                 row.clear();
                 for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {

@@ -30,6 +30,7 @@ CFGS = [
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", fill_level=1),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
     dict(variant="rap", factor_B="ilu0", factor_S="milu0", fill_level=1, local_order="rcm"),
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0", l1_block=True, local_order="rcm"),
 ]
 
 
@@ -70,6 +71,8 @@ def test_fill_level_option_is_validated(ilu):
         ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, factor_B="ilut", fill_level=1))
     with pytest.raises(ilu.IluError):
         ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, fill_level=-1))
+    with pytest.raises(ilu.IluError):
+        ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, variant="schur", l1_block=True))
 
 
 def test_full_size_2d_workload_structure(ilu):
