@@ -6,6 +6,7 @@
 // scheduling analysis, L\U stored in the pattern), Sec. 3.2 (local blocks Eq. localA,
 // factor extraction L_B, U_B, L_S, U_S, W, Z, the off-diagonal blocks of S, Eq. SS).
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -97,11 +98,22 @@ void prog_close_level(ProgHost& P) {
     P.lvl_ptr.push_back((int32_t)P.prow.size());
 }
 
-// fn(t, s0, s1) on up to 16 host threads, thread t taking the contiguous subdomains
-// [s0, s1); returns the number of ranges used
+// Host setups running in this process; each takes its share of the hardware threads, so
+// that concurrent setups (several requests being served) do not oversubscribe the cores.
+std::atomic<int> g_setups{0};
+
+struct SetupCount {
+    SetupCount() { g_setups.fetch_add(1); }
+    ~SetupCount() { g_setups.fetch_sub(1); }
+};
+
+// fn(t, s0, s1) on up to 16 host threads (fewer while other setups run), thread t taking
+// the contiguous subdomains [s0, s1); returns the number of ranges used
 template <class Fn>
 int for_ranges(int32_t p, Fn fn) {
-    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned share = std::max(1u, hw / (unsigned)std::max(1, g_setups.load()));
+    unsigned nt = std::max(1u, std::min(16u, share));
     nt = std::max(1u, std::min<unsigned>(nt, (unsigned)std::max(p, 1)));
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nt; t++)
@@ -806,6 +818,7 @@ static void iluk_block(const std::vector<int32_t>& rp, const std::vector<int32_t
 }
 
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p) {
+    SetupCount running;
     ilu_status st = validate(A, part, p);
     if (st != ILU_OK) return st;
     const int32_t n = A->n;
