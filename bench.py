@@ -50,6 +50,16 @@ def prog_bytes(prog, sv):
     return prog["entries"] * (4 + sv) + prog["rows"] * (8 + sv) + prog["levels"] * 4
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over every
+# launch of the timed solve) from the ncu capture summarised in
+# profiles/k_fg_cgs_dram_aniso2d_1024_p64.md; valid for that workload and for the kernel as
+# captured there (set to None when the kernel changes)
+MEASURED_TRAFFIC = {
+    ("aniso2d_boxes_side1024_boxes8_schur_ilu0+milu0_fp32pc_fgmres50_rtol1e-8", "schur", "ilu0+milu0", "fp32",
+     "fg_cgs"): 409.0e6,
+}
+
+
 def class_bytes(sz, prec, iters, m, k):
     """Algorithmic bytes summed over the working launches of every kernel class of one
     solve with `iters` Arnoldi steps in cycles of m, inner GMRES of k steps."""
@@ -454,8 +464,15 @@ def main():
     dom = max(classes, key=lambda k: classes[k]["ms"])
     total_prof = sum(c["ms"] for c in classes.values())
     d = classes[dom]
+    traffic = MEASURED_TRAFFIC.get((workload_name(cfg), sol["variant"], f'{sol["factor_B"]}+{sol["factor_S"]}',
+                                    prec, dom))
+    alg_bytes = cbytes.get(dom) / d["launches"] if cbytes.get(dom) else None
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
-                "unit": d["unit"], "frac": d["frac"], "traffic": None, "arith": d.get("arith"),
+                "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu, see profiles/)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic_per_algorithmic": (traffic / alg_bytes) if (traffic and alg_bytes) else None,
+                "arith": d.get("arith"),
                 "share": d["ms"] / total_prof,
                 "peak_kind": "derived: 2 FP64 FMA/SM/clock x 152 SMs x 2.07 GHz" if d["bound"] == "alu"
                 else peak_kind,
