@@ -209,6 +209,24 @@ def cpu_baseline(cfg, sample_cycles=1):
                 time_to_rtol_s=est, setup_s=t1 - t0, iters=iters)
 
 
+def max_over_ranks(v, world, device):
+    """The largest of every rank's v (collective over the default process group)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(t_ms_local, steps, world, device):
+    """N independent replicas, each timing `steps` solves: whole-job solves per second = the
+    solves of all ranks over the slowest rank's time. Returns (value, slowest ms)."""
+    t_ms = max_over_ranks(t_ms_local, world, device)
+    return world * steps / (t_ms / 1000.0), t_ms
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -352,12 +370,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     if args.mode == "serve":
         if rank == 0:
@@ -406,15 +418,13 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         barrier()
-    t_ms = ev0.elapsed_time(ev1)
-    t_ms = max_over_ranks(t_ms)
+    value, t_ms = replica_value(ev0.elapsed_time(ev1), args.steps, world, dev)
     launches = h.stats()["kernel_launches"] - launches0
     info = infos[-1]
     xs = x.cpu().numpy()
     relres = float(np.linalg.norm(pr.b - pr.scipy() @ xs) / np.linalg.norm(pr.b))
     err_true = float(np.linalg.norm(xs - pr.x_true) / np.linalg.norm(pr.x_true))
     time_to_rtol = t_ms / 1000.0 / args.steps
-    value = world * args.steps / (t_ms / 1000.0)
 
     # ---- preconditioner apply bandwidth (standalone applies, events on the same stream)
     sz = h.sizes()
@@ -519,7 +529,7 @@ def main():
             x_host.copy_(xd, non_blocking=True)
             torch.cuda.synchronize()
             he.close()
-        te = max_over_ranks((time.perf_counter() - t0) / ne2e)
+        te = max_over_ranks((time.perf_counter() - t0) / ne2e, world, dev)
         h2d = pr.rowptr.nbytes + pr.colind.nbytes + pr.val.nbytes + pr.part.nbytes + pr.b.nbytes
         e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * pr.n),
                "time_s": te, "includes": "ilu_setup from host CSR + H2D b + gmres_solve + D2H x + ilu_free"}
