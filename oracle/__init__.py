@@ -42,7 +42,7 @@ class _Opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("factor_B", C.c_int), ("factor_S", C.c_int),
                 ("form", C.c_int), ("ilut_tau", C.c_double), ("ilut_p", C.c_int),
                 ("inner_iters", C.c_int), ("pivot_eps", C.c_double), ("local_order", C.c_int),
-                ("fill_level", C.c_int), ("l1_block", C.c_int)]
+                ("fill_level", C.c_int), ("l1_block", C.c_int), ("store_bf16", C.c_int)]
 
 
 _lib = None
@@ -69,6 +69,7 @@ def lib():
             "orc_classify": (I, [I, P, P, P, I, P]),
             "orc_permutation": (I, [I, P, I, P, P, P, P, P]),
             "orc_rcm": (I, [I, P, P, P]),
+            "orc_round_bf16": (D, [D]),
             "orc_iluk_pattern": (P, [I, P, P, P, I, P]),
             "orc_opts_default": (None, [P]),
             "orc_setup": (P, [I, P, P, P, P, I, P, P]),
@@ -196,6 +197,11 @@ def iluk_pattern(n, rowptr, colind, val, k):
     return rp, ci, v
 
 
+def round_bf16(x: float) -> float:
+    """x rounded to the nearest bfloat16 value, ties to even."""
+    return lib().orc_round_bf16(float(x))
+
+
 def rcm(n, rowptr, colind):
     """Reverse Cuthill-McKee order of the symmetrised graph of a square pattern:
     order[k] = the node placed k-th."""
@@ -238,7 +244,8 @@ class Oracle:
 
     def __init__(self, n, rowptr, colind, val, part, p, variant="schur", factor_B="ilu0",
                  factor_S="milu0", form="auto", ilut_tau=1e-3, ilut_p=10, inner_iters=3,
-                 pivot_eps=1e-8, local_order="natural", fill_level=0, l1_block=False):
+                 pivot_eps=1e-8, local_order="natural", fill_level=0, l1_block=False,
+                 store_bf16=False):
         self._keep = [_i32(rowptr), _i32(colind), _f64(val), _i32(part)]
         o = _Opts()
         lib().orc_opts_default(C.byref(o))
@@ -253,6 +260,7 @@ class Oracle:
         o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM}[local_order]
         o.fill_level = int(fill_level)
         o.l1_block = int(bool(l1_block))
+        o.store_bf16 = int(bool(store_bf16))
         self.opts = o
         st = C.c_int(0)
         rp, ci, v, pt = self._keep

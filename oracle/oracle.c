@@ -230,6 +230,24 @@ typedef struct {
 
 static int int_cmp(const void* a, const void* b);
 
+/* bfloat16: 1 sign bit, 8 exponent bits (bias 127, like IEEE single), 7 stored significand
+   bits. Normal values keep 8 significant bits; below 2^-126 the spacing is 2^-133; at or
+   above 2^128 (1 - 2^-9) the value rounds to infinity. nearbyint rounds half to even in
+   the default rounding mode. */
+double orc_round_bf16(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    double a = fabs(x), r;
+    if (a < ldexp(1.0, -126)) {
+        r = ldexp(nearbyint(ldexp(a, 133)), -133);
+    } else {
+        int e;
+        double m = frexp(a, &e);                       /* a = m 2^e, m in [0.5, 1) */
+        r = ldexp(nearbyint(ldexp(m, 8)), e - 8);      /* 8 significant bits */
+        if (r >= ldexp(1.0, 128)) r = INFINITY;
+    }
+    return copysign(r, x);
+}
+
 /* Level-of-fill pattern of ILU(k) (the paper uses ILU(1) and ILU(2) in Sec. 4.2-4.4 without
    defining them; standard sum rule). Stored entries have level 0. Row i is eliminated with
    its pivots m < i in ascending order, fill included: each entry u_mj (j > m) kept in row m
@@ -848,6 +866,7 @@ void orc_opts_default(orc_opts* o) {
     o->local_order = ORC_ORDER_NATURAL;
     o->fill_level = 0;
     o->l1_block = 0;
+    o->store_bf16 = 0;
 }
 
 static inline int nint_of(const orc_t* h, int s) { return h->int_ptr[s + 1] - h->int_ptr[s]; }
@@ -1140,6 +1159,21 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
         } else {
             h->F2 = h->F1;
             h->f2_alias = 1;
+        }
+    }
+    /* bfloat16 storage of the factors the applies read: every off-diagonal entry of F1 and
+       F2 (L, U, and the W and Z blocks) rounded, the pivots kept */
+    if (h->o.store_bf16) {
+        if (h->o.store_bf16 != 1 || h->form != ORC_FORM_WZ || h->o.factor_B > ORC_MILU0) {
+            st = ORC_ERR_ARG;
+            goto fail;
+        }
+        for (int pass = 0; pass < (h->f2_alias ? 1 : 2); pass++) {
+            csr_t* F = pass ? h->F2 : h->F1;
+            for (int s = 0; s < p; s++)
+                for (int r = 0; r < F[s].nr; r++)
+                    for (int q = F[s].rp[r]; q < F[s].rp[r + 1]; q++)
+                        if (F[s].ci[q] != r) F[s].v[q] = orc_round_bf16(F[s].v[q]);
         }
     }
     if (status) *status = ORC_OK;

@@ -67,6 +67,9 @@ typedef struct orc_opts {
                            at the fill positions; needs factor_B, factor_S in {ILU0, MILU0} */
     int l1_block;       /* block Jacobi only: 1 = l1-BJ (Sec. 4.3), every diagonal entry of A_s
                            increased by the sum of |a_ij| over the columns of other subdomains */
+    int store_bf16;     /* 1: every off-diagonal factor entry rounded to bfloat16 (nearest,
+                           ties to even, straight from the double), the pivots u_ii kept;
+                           the applies then run in double on those values. W/Z form only */
 } orc_opts;
 
 /* ---- primitives on one CSR matrix ---- */
@@ -96,6 +99,9 @@ int orc_levels_csr(int n, const int* rowptr, const int* colind, int upper, int* 
 /* ---- domain decomposition ---- */
 int orc_classify(int n, const int* rowptr, const int* colind, const int* part, int p,
                  int* iface);
+/* x rounded to the nearest bfloat16 value (8 significant bits, the exponent range of
+   IEEE single), ties to even; zero, infinities and NaN unchanged. */
+double orc_round_bf16(double x);
 /* Reverse Cuthill-McKee order of the symmetrised graph of a square pattern (i ~ j when
    a_ij or a_ji is stored, i != j): order[k] = the node placed k-th. */
 int orc_rcm(int n, const int* rowptr, const int* colind, int* order);

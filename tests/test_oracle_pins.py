@@ -809,6 +809,73 @@ def test_l1_block_jacobi_apply_is_blockwise_ilu0_of_the_augmented_blocks():
 
 
 # --------------------------------------------------------------------------------------
+# bfloat16 factor storage
+
+
+def _bf16_bits(x):
+    """Round-to-nearest-even to 8 significant bits on the float64 bit pattern (normal
+    bfloat16 range): drop the low 45 significand bits, adding half an ulp minus one plus the
+    kept lowest bit first."""
+    b = np.asarray(x, dtype=np.float64).view(np.uint64)
+    keep = (b >> np.uint64(45)) & np.uint64(1)
+    r = (b + np.uint64((1 << 44) - 1) + keep) >> np.uint64(45) << np.uint64(45)
+    return r.view(np.float64)
+
+
+def test_round_bf16_matches_the_bit_level_definition():
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(4000) * 10.0 ** rng.uniform(-30, 30, 4000)
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(2.0 + 2.0 ** -7), 3.0 * 2.0 ** -9])
+    for v in np.concatenate([x, ties]):
+        assert O.round_bf16(v) == _bf16_bits(v), v
+    assert O.round_bf16(1.0 + 2.0 ** -8) == 1.0 and O.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    # below 2^-126 the spacing is 2^-133 (np.round: half to even)
+    for v in rng.uniform(-1, 1, 200) * 2.0 ** -126:
+        assert O.round_bf16(v) == np.round(v * 2.0 ** 133) * 2.0 ** -133
+    assert O.round_bf16(3.4e38) == np.inf and O.round_bf16(3.38e38) < np.inf
+
+
+@pytest.mark.parametrize("variant", ["bj", "schur", "rap"])
+def test_bf16_storage_rounds_the_off_diagonal_factor_entries(variant):
+    pr = _small_dd("aniso2d")
+    kw = dict(variant=variant, factor_B="ilu0", factor_S="milu0")
+    o, ob = O.Oracle.from_problem(pr, **kw), O.Oracle.from_problem(pr, store_bf16=True, **kw)
+    facts = [1] if variant == "bj" else [1, 2]
+    for sd in range(pr.p):
+        rp, ci, _ = o.local_csr(sd)
+        diag = np.zeros(ci.size, bool)
+        for r in range(rp.size - 1):
+            diag[rp[r]:rp[r + 1]] = ci[rp[r]:rp[r + 1]] == r
+        for f in facts:
+            v, vb = o.local_factor(sd, f), ob.local_factor(sd, f)
+            assert np.array_equal(vb[diag], v[diag])
+            assert np.array_equal(vb[~diag], _bf16_bits(v[~diag]))
+
+
+def test_bf16_block_jacobi_apply_uses_the_rounded_factors():
+    pr = P.convdiff3d_boxes(8, 2)
+    ob = O.Oracle.from_problem(pr, variant="bj", factor_B="ilu0", store_bf16=True)
+    r = np.random.default_rng(4).standard_normal(pr.n)
+    A = pr.scipy()
+    zz = np.zeros(pr.n)
+    for sd in range(pr.p):
+        idx = np.nonzero(pr.part == sd)[0]
+        Ai = A[idx][:, idx].tocsr()
+        Ai.sort_indices()
+        f, _, _ = O.ilu0(idx.size, Ai.indptr, Ai.indices, Ai.data)
+        F = sp.csr_matrix((f, Ai.indices, Ai.indptr), shape=Ai.shape)
+        off = F - sp.diags(F.diagonal())
+        off.data = _bf16_bits(off.data)
+        F = (off + sp.diags(F.diagonal())).tocsr()
+        L = (sp.tril(F, -1) + sp.identity(idx.size)).tocsr()
+        U = sp.triu(F).tocsr()
+        zz[idx] = spla.spsolve_triangular(U, spla.spsolve_triangular(L, r[idx], lower=True), lower=False)
+    np.testing.assert_allclose(ob.apply(r), zz, rtol=1e-12, atol=1e-13)
+    with pytest.raises(RuntimeError):
+        O.Oracle.from_problem(pr, variant="schur", factor_B="ilut", store_bf16=True)
+
+
+# --------------------------------------------------------------------------------------
 # FGMRES
 
 
