@@ -46,8 +46,10 @@ def _peaks():
 # algorithmic bytes (each array read or written once per pass; gathers counted once)
 
 
-def prog_bytes(prog, sv):
-    return prog["entries"] * (4 + sv) + prog["rows"] * (8 + sv) + prog["levels"] * 4
+def prog_bytes(prog, sv, svv=None):
+    """sv: bytes of a vector element and pivot inverse; svv: of a stored value (default sv)"""
+    svv = sv if svv is None else svv
+    return prog["entries"] * (4 + svv) + prog["rows"] * (8 + sv) + prog["levels"] * 4
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over every
@@ -64,7 +66,8 @@ def class_bytes(sz, prec, iters, m, k):
     """Algorithmic bytes summed over the working launches of every kernel class of one
     solve with `iters` Arnoldi steps in cycles of m, inner GMRES of k steps."""
     n, nnz, n1, n2, ncoff = sz["n"], sz["nnz"], sz["n1"], sz["n2"], sz["nnz_coff"]
-    sv = 4 if prec == "fp32" else 8
+    sv = 8 if prec == "fp64" else 4
+    svv = 2 if prec == "bf16" else sv  # stored factor values
     full, rem = divmod(iters, m)
     steps = [m] * full + ([rem] if rem else [])
     js = [j for s in steps for j in range(s)]
@@ -79,15 +82,15 @@ def class_bytes(sz, prec, iters, m, k):
     b["fg_resid"] = (cycles + 1) * (spmv + 24 * n)
     b["fg_scale0"] = (cycles + 1) * 16 * n
     if sz["prog_bj"]["rows"]:
-        b["apply_bj"] = iters * (prog_bytes(sz["prog_bj"], sv) + 20 * n)
+        b["apply_bj"] = iters * (prog_bytes(sz["prog_bj"], sv, svv) + 20 * n)
     else:
-        fwd = prog_bytes(sz["prog_fwd"], sv) + prog_bytes(sz["prog_s"], sv) + 12 * n + sv * n
+        fwd = prog_bytes(sz["prog_fwd"], sv, svv) + prog_bytes(sz["prog_s"], sv, svv) + 12 * n + sv * n
         inner = 0
         for j in range(k):
-            inner += (ncoff * (4 + sv) + 4 * (n2 + 1) + prog_bytes(sz["prog_s"], sv)
+            inner += (ncoff * (4 + sv) + 4 * (n2 + 1) + prog_bytes(sz["prog_s"], sv, svv)
                       + 3 * sv * n2 + (j + 1) * sv * n2)                      # part A
             inner += 2 * ((j + 1) * sv * n2 + 2 * sv * n2)                     # parts B, C
-        bwd = prog_bytes(sz["prog_bwd"], sv) + sv * n1 + k * sv * n2 + 12 * n
+        bwd = prog_bytes(sz["prog_bwd"], sv, svv) + sv * n1 + k * sv * n2 + 12 * n
         b["apply_fwd"] = iters * fwd
         b["apply_inner"] = iters * inner
         b["apply_bwd"] = iters * bwd
@@ -344,7 +347,8 @@ def main():
                     help="preconditioner variant override (rap: ILU(0) smoother, MILU(0) transfer)")
     ap.add_argument("--mode", default="solve", choices=["solve", "apply", "serve"],
                     help="apply: only time the preconditioner apply (used for kernel profiling)")
-    ap.add_argument("--prec", default=None, choices=[None, "fp32", "fp64"])
+    ap.add_argument("--prec", default=None, choices=[None, "fp32", "fp64", "bf16"],
+                    help="preconditioner precision (bf16: bfloat16 factor values, FP32 arithmetic)")
     ap.add_argument("--threads", type=int, default=0, help="consumer-group threads override (0 = auto)")
     ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
     args = ap.parse_args()

@@ -60,7 +60,11 @@ typedef struct {
 typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1, ILU_VARIANT_RAP = 2 } ilu_variant;
 typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2 } ilu_fact;
 typedef enum { ILU_FORM_AUTO = 0, ILU_FORM_WZ = 1, ILU_FORM_EF = 2 } ilu_form;
-typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1 } ilu_prec;
+/* FP64, FP32: factors and arithmetic of M^{-1} in that type. BF16_STORE: FP32 arithmetic
+   with every off-diagonal factor entry of the level programs stored as bfloat16 (nearest,
+   ties to even, from the FP64 factor); pivot inverses and C_off stay FP32. W/Z form on the
+   streamed path only (ILU_ERR_UNSUPPORTED with ILUT, the E/F form or kernel_path = 1). */
+typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1, ILU_PREC_BF16_STORE = 2 } ilu_prec;
 /* Order inside each group of a subdomain before the factorisation. The groups: block
    Jacobi, the whole subdomain (it has no interface, Sec. 2.1); SCHUR and RAP, the interior
    nodes and the interface nodes of each subdomain (Sec. 2.2.1), so A_i keeps its
@@ -251,7 +255,8 @@ ilu_status ilu_get_stream_stats(void* h, int32_t program, int64_t* out);
    filled on the device, so the copy holds zeros there): blob = the chunks (layout in the
    comment of csrc/stream_layout.h), ch0 = p+1 chunk offsets per subdomain, meta[0] =
    blob bytes, meta[1] = chunk bytes, meta[2] = entries per record, meta[3] = value bytes,
-   meta[4] = consumer threads. Call with blob = ch0 = NULL to read meta first; blob must
+   meta[4] = consumer threads, meta[5] = working-vector element (and pivot-inverse) bytes;
+   meta is int64[6]. Call with blob = ch0 = NULL to read meta first; blob must
    hold meta[0] bytes and ch0 p+1 values. Host-side only. Errors: ILU_ERR_ARG (null
    handle or meta, program outside 0..3), ILU_ERR_UNSUPPORTED (program not built). */
 ilu_status ilu_get_stream(void* h, int32_t program, uint8_t* blob, int32_t* ch0, int64_t* meta);

@@ -24,7 +24,7 @@ ILU_ERR_TOO_LARGE, ILU_ERR_UNSUPPORTED = 9, 10
 VARIANTS = {"bj": 0, "schur": 1, "rap": 2}
 FACTORS = {"ilu0": 0, "milu0": 1, "ilut": 2}
 FORMS = {"auto": 0, "wz": 1, "ef": 2}
-PRECS = {"fp64": 0, "fp32": 1}
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}  # bf16: FP32 arithmetic, bfloat16 factor values
 LEVELS = {"LA": 0, "UA": 1, "LB": 2, "UB": 3, "LS": 4, "US": 5}
 
 
@@ -284,14 +284,14 @@ class Handle:
         """The streamed program ("bj", "fwd", "s", "bwd") as built on the host: raw chunk
         bytes, per-subdomain chunk offsets and the record geometry."""
         idx = ["bj", "fwd", "s", "bwd"].index(program)
-        meta = np.zeros(5, np.int64)
+        meta = np.zeros(6, np.int64)
         _check(lib().ilu_get_stream(self.ptr, idx, None, None, meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
         blob = np.zeros(int(meta[0]), np.uint8)
         ch0 = np.zeros(self.sizes()["p"] + 1, np.int32)
         _check(lib().ilu_get_stream(self.ptr, idx, blob.ctypes.data_as(C.c_void_p), ch0.ctypes.data_as(C.c_void_p),
                                     meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
         return dict(blob=blob, ch0=ch0, chunk=int(meta[1]), rw=int(meta[2]), val_bytes=int(meta[3]),
-                    threads=int(meta[4]))
+                    threads=int(meta[4]), x_bytes=int(meta[5]))
 
     def inner_solve_noalloc(self, gp, y):
         """ilu_inner_solve with the library's fixed workspace instead of the handle's

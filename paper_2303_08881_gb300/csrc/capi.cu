@@ -239,7 +239,7 @@ ilu_status device_setup(Handle& h) {
     h.d_ictl = h.alloc<InnerCtl>(1, &e);
     if (!h.d_ipart || !h.d_ictl) return map_err(e);
     CK(cudaMemsetAsync(h.d_ictl, 0, sizeof(InnerCtl), h.st));
-    ilu_status s = (h.prec == ILU_PREC_FP32) ? device_setup_t<float>(h) : device_setup_t<double>(h);
+    ilu_status s = (h.prec != ILU_PREC_FP64) ? device_setup_t<float>(h) : device_setup_t<double>(h);
     if (s != ILU_OK) return s;
     CK(cudaStreamSynchronize(h.st));
     (void)n;
@@ -369,7 +369,7 @@ cudaError_t apply_t(Handle& h, const double* r, double* z, const int32_t* done, 
 
 cudaError_t apply_any(Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st,
                       bool cap = false) {
-    return (h.prec == ILU_PREC_FP32) ? apply_t<float>(h, r, z, done, st, cap)
+    return (h.prec != ILU_PREC_FP64) ? apply_t<float>(h, r, z, done, st, cap)
                                      : apply_t<double>(h, r, z, done, st, cap);
 }
 
@@ -482,7 +482,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
     const ilu_opts& o = h->o;
     if ((o.variant != ILU_VARIANT_BJ && o.variant != ILU_VARIANT_SCHUR && o.variant != ILU_VARIANT_RAP) ||
         (o.variant == ILU_VARIANT_RAP && o.factor_B == ILU_FACT_ILUT) || o.factor_B < 0 || o.factor_B > 2 ||
-        o.factor_S < 0 || o.factor_S > 1 || (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32) ||
+        o.factor_S < 0 || o.factor_S > 1 ||
+        (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32 && o.pc_precision != ILU_PREC_BF16_STORE) ||
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
@@ -493,7 +494,9 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         delete h;
         return ILU_ERR_ARG;
     }
-    if (o.variant == ILU_VARIANT_RAP && o.kernel_path != 0) {
+    if ((o.variant == ILU_VARIANT_RAP && o.kernel_path != 0) ||
+        (o.pc_precision == ILU_PREC_BF16_STORE &&
+         (o.kernel_path != 0 || o.factor_B == ILU_FACT_ILUT || (o.variant == ILU_VARIANT_SCHUR && o.form == ILU_FORM_EF)))) {
         delete h;
         return ILU_ERR_UNSUPPORTED;
     }
@@ -515,7 +518,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
             h->smem_optin = optin;
     }
     ilu_status s = host_setup(*h, A, part, p);
-    if (s == ILU_OK && h->variant == ILU_VARIANT_RAP && !h->stream_path) s = ILU_ERR_UNSUPPORTED;
+    if (s == ILU_OK && (h->variant == ILU_VARIANT_RAP || h->prec == ILU_PREC_BF16_STORE) && !h->stream_path)
+        s = ILU_ERR_UNSUPPORTED;
     h->host_ms = now_ms() - t0;
     if (s == ILU_OK && o.analysis_only) {
         h->setup_ms = now_ms() - t0;
@@ -578,7 +582,7 @@ ilu_status ilu_inner_solve(void* hp, const double* gp, double* y) {
     Handle* h = (Handle*)hp;
     if (h->o.analysis_only) return ILU_ERR_ARG;
     if (h->variant != ILU_VARIANT_SCHUR) return ILU_ERR_ARG;
-    cudaError_t e = (h->prec == ILU_PREC_FP32) ? launch_inner_io<float>(*h, gp, y, h->st)
+    cudaError_t e = (h->prec != ILU_PREC_FP64) ? launch_inner_io<float>(*h, gp, y, h->st)
                                                 : launch_inner_io<double>(*h, gp, y, h->st);
     return map_err(e);
 }
@@ -860,6 +864,7 @@ ilu_status ilu_get_stream(void* hp, int32_t program, uint8_t* blob, int32_t* ch0
     meta[2] = S.rw;
     meta[3] = S.val_bytes;
     meta[4] = S.nt;
+    meta[5] = S.x_bytes;
     if (blob) memcpy(blob, S.blob.data(), S.blob.size());
     if (ch0) memcpy(ch0, S.ch0.data(), S.ch0.size() * sizeof(int32_t));
     return ILU_OK;

@@ -33,7 +33,7 @@ struct StreamHost {
     rawvec<int64_t> voff, doff;  // byte offsets of value / pivot-inverse slots
     rawvec<int32_t> vsrc, dsrc;  // their sources in the value array
     uint32_t chunk = 8192;
-    int idx_bytes = 2, val_bytes = 4;
+    int idx_bytes = 2, val_bytes = 4, x_bytes = 4;
     int rw = 4;                       // entries per row record (compile-time width on the device)
     uint32_t rec_bytes = 32;
     int nt = 32;                      // threads of the consumer group
@@ -55,7 +55,8 @@ struct StreamBufs {
 void host_levels(Handle& h);
 
 // Builds the chunked stream of program P; false if a single row does not fit a chunk.
-bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, uint32_t chunk,
+// x_bytes: element size of the working vector (and of dinv); val_bytes: of the values.
+bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int val_bytes, uint32_t chunk,
                   StreamHost& S);
 
 struct ProgBufs {

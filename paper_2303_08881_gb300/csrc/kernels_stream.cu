@@ -18,6 +18,7 @@
 // Kernels: k_bj_s (block Jacobi), k_fwd_s (f' = L_B^{-1} f, g' = g - W f', c = S~^{-1} g'),
 // k_coff (t = C_off v_j, grid-wide), k_inner_a_s (w = v_j + S~^{-1} t, first Gram-Schmidt
 // dots), k_bwd_s (y = V t, f'' = f' - Z y, u = U_B^{-1} f'', scatter).
+#include <cuda_bf16.h>
 #include "devutil.cuh"
 #include "handle.h"
 #include "inner_lsq.cuh"
@@ -158,25 +159,35 @@ __device__ __forceinline__ void ring_rearm(const StreamDev<T>& S, int s, const S
     __syncthreads();
 }
 
-// Row record (stream_layout.h), read with 128-bit shared-memory loads.
-template <class T, int RW>
+// Row record (stream_layout.h), read with 128-bit shared-memory loads. V is the storage
+// type of the values: T, or bfloat16 for T = float (values widened on use).
+template <class T, int RW, class V = T>
 struct __align__(16) RowRec {
     uint32_t head;  // byte offset of x[row] | n << 24 | skip bit
     T dinv;
     uint32_t col[RW];  // byte offsets (unused entries: the row's own)
-    T val[RW];         // (unused entries: zero)
+    V val[RW];         // (unused entries: zero)
 };
 
-template <class T, int RW>
+template <class T, int RW, class V = T>
 union RecU {
-    RowRec<T, RW> r;
-    uint4 v[sizeof(RowRec<T, RW>) / 16];
+    RowRec<T, RW, V> r;
+    uint4 v[sizeof(RowRec<T, RW, V>) / 16];
 };
 
-template <class T, int RW>
-__device__ __forceinline__ void rec_load(RecU<T, RW>& u, const uint8_t* p) {
-    constexpr int NV = sizeof(RowRec<T, RW>) / 16;
-    static_assert(sizeof(RowRec<T, RW>) == rec_layout(RW, sizeof(T)).bytes, "record layout");
+template <class T, class V>
+__device__ __forceinline__ T widen(V v) {
+    return (T)v;
+}
+template <>
+__device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+template <class T, int RW, class V>
+__device__ __forceinline__ void rec_load(RecU<T, RW, V>& u, const uint8_t* p) {
+    constexpr int NV = sizeof(RowRec<T, RW, V>) / 16;
+    static_assert(sizeof(RowRec<T, RW, V>) == rec_layout(RW, sizeof(V), sizeof(T)).bytes, "record layout");
     const uint4* s = reinterpret_cast<const uint4*>(p);
 #pragma unroll
     for (int i = 0; i < NV; i++) u.v[i] = s[i];
@@ -188,19 +199,19 @@ __device__ __forceinline__ T ldx(const uint8_t* xb, uint32_t off) {
 }
 
 // operands of a record: x[col[q]] and x[row]
-template <class T, int RW>
-__device__ __forceinline__ void rec_operands(const RecU<T, RW>& u, const uint8_t* xb, T (&xc)[RW], T& xr) {
+template <class T, int RW, class V>
+__device__ __forceinline__ void rec_operands(const RecU<T, RW, V>& u, const uint8_t* xb, T (&xc)[RW], T& xr) {
 #pragma unroll
     for (int q = 0; q < RW; q++) xc[q] = ldx<T>(xb, u.r.col[q]);
     xr = ldx<T>(xb, u.r.head & 0xFFFFFFu);
 }
 
 // x[row] = (x[row] - sum_q val[q] x[col[q]]) * dinv, the sum formed pairwise
-template <class T, int RW>
-__device__ __forceinline__ T rec_value(const RecU<T, RW>& u, const T (&xc)[RW], T xr) {
+template <class T, int RW, class V>
+__device__ __forceinline__ T rec_value(const RecU<T, RW, V>& u, const T (&xc)[RW], T xr) {
     T p[RW];
 #pragma unroll
-    for (int q = 0; q < RW; q++) p[q] = u.r.val[q] * xc[q];
+    for (int q = 0; q < RW; q++) p[q] = widen<T, V>(u.r.val[q]) * xc[q];
 #pragma unroll
     for (int w = 1; w < RW; w *= 2)
 #pragma unroll
@@ -215,10 +226,10 @@ __device__ __forceinline__ T rec_value(const RecU<T, RW>& u, const T (&xc)[RW], 
 // the current row writes, the value is forwarded in registers (the early load predates
 // the store). Every address stays inside the chunk and the working vector: past the
 // end the pipeline reloads the segment's first record.
-template <class T, int RW>
-__device__ __forceinline__ void run_segment(const RecU<T, RW>& first, const uint8_t* p, uint32_t stride, uint32_t nw,
+template <class T, int RW, class V>
+__device__ __forceinline__ void run_segment(const RecU<T, RW, V>& first, const uint8_t* p, uint32_t stride, uint32_t nw,
                                             uint8_t* xb) {
-    RecU<T, RW> a = first, b;
+    RecU<T, RW, V> a = first, b;
     T xa[RW], xra;
     rec_operands(a, xb, xa, xra);
     if (nw == 1) {  // a single wave: no pipeline
@@ -229,7 +240,7 @@ __device__ __forceinline__ void run_segment(const RecU<T, RW>& first, const uint
     for (uint32_t w = 0; w < nw; w++) {
         T xn[RW], xrn;
         rec_operands(b, xb, xn, xrn);
-        RecU<T, RW> c;
+        RecU<T, RW, V> c;
         rec_load(c, p + (w + 2 < nw ? (w + 2) * stride : 0u));
         const uint32_t ha = a.r.head;
         const T v = rec_value(a, xa, xra);
@@ -282,9 +293,9 @@ __device__ void ring_produce(const StreamDev<T>& S, int s, const Smem& sm, const
 // ring. The caller passes whole warps: threads 0..nt+31 (the first barrier below counts
 // the consumer warps and the refill warp). Returns false on a time-out (uniform over
 // the consumer group; bit 2 of the device error word is set).
-template <class T, int RW>
+template <class T, int RW, class V = T>
 __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const RingCfg& cfg, T* x) {
-    constexpr uint32_t RB = sizeof(RowRec<T, RW>);
+    constexpr uint32_t RB = sizeof(RowRec<T, RW, V>);
     __shared__ int abort_flag;
     const int nt = S.nt, tid = threadIdx.x, nst = cfg.nst;
     const int c0 = S.ch0[s], nch = S.ch0[s + 1] - c0;
@@ -315,13 +326,13 @@ __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const Rin
         auto mine = [&](uint2 e) { return (uint32_t)tid < ((e.x >> 16) & 0x1FFu); };
         uint2 e = tab[0];
         uint2 en = tab[nseg > 1 ? 1 : 0];
-        RecU<T, RW> r;
+        RecU<T, RW, V> r;
         if (mine(e)) rec_load(r, first_of(e));
         for (uint32_t g = 0; g < nseg; g++) {
             const uint2 enn = tab[g + 2 < nseg ? g + 2 : 0];
-            RecU<T, RW> rn;
+            RecU<T, RW, V> rn;
             if (g + 1 < nseg && mine(en)) rec_load(rn, first_of(en));
-            if (mine(e)) run_segment<T, RW>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+            if (mine(e)) run_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
             if (e.y & kSegBarrier) group_sync(nt);
             e = en;
             en = enn;
@@ -375,7 +386,7 @@ __device__ __forceinline__ T* xvec(const Smem& sm, T* xg, int q0) {
     }
 }
 
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_bj_s(SubDev sd, StreamDev<T> S, RingCfg cfg, const double* __restrict__ r,
                                               double* __restrict__ z, T* xg, const int32_t* done) {
     if (done && *done) return;
@@ -386,12 +397,12 @@ __global__ void __launch_bounds__(256) k_bj_s(SubDev sd, StreamDev<T> S, RingCfg
     T* x = xvec<T, XS>(sm, xg, q0);
     gather(x, r, sd.q_orig + q0, ns);
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     scatter(z, x, sd.q_orig + q0, ns);
 }
 
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
                                                const double* __restrict__ r, T* __restrict__ fq, T* xg,
                                                const int32_t* done) {
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCf
     T* x = xvec<T, XS>(sm, xg, q0);
     gather(x, r, sd.q_orig + q0, ns);
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     for (int l = threadIdx.x; l < ni; l += blockDim.x) fq[q0 + l] = x[l];
     const int g0 = sd.if_ptr[s];
@@ -445,7 +456,7 @@ __global__ void k_coff(SubDev sd, InnerDev<T> in, int j, T* __restrict__ t, cons
     }
 }
 
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
                                                    const T* __restrict__ t, T* xg, const int32_t* done) {
     __shared__ double red[32 * 8];
@@ -478,7 +489,7 @@ __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, Ri
     T* x = xvec<T, XS>(sm, xg + ni, q0);
     for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = t[g0 + i];
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     T* Vj = in.V + (size_t)j * n2;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -555,7 +566,7 @@ __device__ bool grid_sync(InnerCtl* ctl, uint32_t nblocks, uint64_t spin, int32_
 // The Hessenberg entries go to ctl (CTA 0); k_bwd_s solves the least squares. Every CTA
 // forms each norm from the same partials in the same order, so the stopping decisions
 // (c = 0, breakdown) are uniform and no CTA leaves the barriers early.
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, T* xg,
                                                     const int32_t* done) {
     __shared__ double red[32 * 8];
@@ -613,7 +624,7 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
             x[i] = acc * inv;
         }
         __syncthreads();
-        if (tid < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+        if (tid < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
         __syncthreads();
         T* Vj = in.V + (size_t)j * n2;
         for (int i = tid; i < nf; i += blockDim.x) {
@@ -690,7 +701,7 @@ __device__ __forceinline__ void scatter_add(double* __restrict__ z, const T* x, 
 
 // step j, first part: v_j = W_in / ||W_in|| (stopping tests as in the additive inner
 // solve), P v_j by the backward program, scattered to a full vector in the original order
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_rap_p_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
                                                  double* __restrict__ pv, T* xg, const int32_t* done) {
     if (done && *done) return;
@@ -725,14 +736,14 @@ __global__ void __launch_bounds__(256) k_rap_p_s(SubDev sd, StreamDev<T> S, Ring
         x[ni + i] = v;
     }
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     scatter(pv, x, sd.q_orig + q0, ns);
 }
 
 // step j, second part: w = S~^{-1} R (A P v_j) by the forward program on the gathered
 // product, stored for the Gram-Schmidt passes, and the first dots V_i . w
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_rap_r_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, int j,
                                                  const double* __restrict__ apv, T* xg, const int32_t* done) {
     __shared__ double red[32 * 8];
@@ -746,7 +757,7 @@ __global__ void __launch_bounds__(256) k_rap_r_s(SubDev sd, StreamDev<T> S, Ring
     T* x = xvec<T, XS>(sm, xg, q0);
     gather(x, apv, sd.q_orig + q0, ns);
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     T* __restrict__ Wout = (j & 1) ? in.W0 : in.W1;
     const int g0 = sd.if_ptr[s];
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(256) k_rap_r_s(SubDev sd, StreamDev<T> S, Ring
 }
 
 // last part: y = V t (least squares of the coarse GMRES), z = x^ + P y
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_rap_fin_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
                                                    double* __restrict__ z, T* xg, const int32_t* done) {
     __shared__ double tt[kMaxInner];
@@ -787,12 +798,12 @@ __global__ void __launch_bounds__(256) k_rap_fin_s(SubDev sd, StreamDev<T> S, Ri
         x[ni + i] = y;
     }
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     scatter_add(z, x, sd.q_orig + q0, ns);
 }
 
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
                                                const double* __restrict__ r, const T* __restrict__ fq, int ef,
                                                double* __restrict__ z, T* xg, const int32_t* done) {
@@ -816,13 +827,13 @@ __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCf
         x[ni + i] = y;
     }
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     scatter(z, x, sd.q_orig + q0, ns);
 }
 
 // standalone start of the inner solve: c = S~^{-1} gp
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in,
                                                        const double* __restrict__ gp, T* xg) {
     __shared__ double red[32];
@@ -834,7 +845,7 @@ __global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S
     const int g0 = sd.if_ptr[s];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) x[i] = (T)gp[g0 + i];
     __syncthreads();
-    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW>(S, s, sm, cfg, x);
+    if ((int)threadIdx.x < S.nt + 32) ring_run<T, RW, V>(S, s, sm, cfg, x);
     __syncthreads();
     T acc = (T)0;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -856,13 +867,24 @@ __global__ void __launch_bounds__(256) k_inner_start_s(SubDev sd, StreamDev<T> S
 
 // ---------------------------------------------------------------------------------------
 // value packing of a stream: blob[voff[e]] = (T) vals[vsrc[e]]; blob[doff[d]] = 1 / vals[dsrc[d]]
-template <class T>
+// a factor value in the record's storage type (bfloat16: nearest, ties to even, straight
+// from the double)
+template <class V>
+__device__ __forceinline__ V to_store(double v) {
+    return (V)v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) {
+    return __double2bfloat16(v);
+}
+
+template <class T, class V = T>
 __global__ void k_pack_stream(int64_t nv, int64_t nd, const int64_t* __restrict__ voff, const int32_t* __restrict__ vsrc,
                               const int64_t* __restrict__ doff, const int32_t* __restrict__ dsrc,
                               const double* __restrict__ vals, uint8_t* blob) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = tid; e < nv; e += stride) *reinterpret_cast<T*>(blob + voff[e]) = (T)vals[vsrc[e]];
+    for (int64_t e = tid; e < nv; e += stride) *reinterpret_cast<V*>(blob + voff[e]) = to_store<V>(vals[vsrc[e]]);
     for (int64_t d = tid; d < nd; d += stride) {
         const int32_t src = dsrc[d];
         *reinterpret_cast<T*>(blob + doff[d]) = (src >= 0) ? (T)(1.0 / vals[src]) : (T)1;
@@ -917,17 +939,17 @@ static cudaError_t raise_smem_limit(K kernel) {
     return e;
 }
 
-template <class T, int RW, bool XS>
+template <class T, int RW, bool XS, class V = T>
 static cudaError_t configure_stream_t() {
-    cudaError_t e = raise_smem_limit(k_bj_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_fwd_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_inner_a_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_bwd_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_inner_start_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_inner_coop<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_rap_p_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_rap_r_s<T, RW, XS>);
-    if (e == cudaSuccess) e = raise_smem_limit(k_rap_fin_s<T, RW, XS>);
+    cudaError_t e = raise_smem_limit(k_bj_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_fwd_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_a_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_bwd_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_start_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_inner_coop<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_p_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_r_s<T, RW, XS, V>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_rap_fin_s<T, RW, XS, V>);
     return e;
 }
 
@@ -939,6 +961,12 @@ cudaError_t configure_stream(const Handle& h, size_t bytes) {
     if (e == cudaSuccess) e = configure_stream_t<T, 16, true>();
     if (e == cudaSuccess) e = configure_stream_t<T, 4, false>();
     if (e == cudaSuccess) e = configure_stream_t<T, 16, false>();
+    if constexpr (sizeof(T) == 4) {  // bfloat16 value storage
+        if (e == cudaSuccess) e = configure_stream_t<T, 4, true, __nv_bfloat16>();
+        if (e == cudaSuccess) e = configure_stream_t<T, 16, true, __nv_bfloat16>();
+        if (e == cudaSuccess) e = configure_stream_t<T, 4, false, __nv_bfloat16>();
+        if (e == cudaSuccess) e = configure_stream_t<T, 16, false, __nv_bfloat16>();
+    }
     return e;
 }
 
@@ -947,7 +975,10 @@ cudaError_t launch_pack_stream(const StreamHost& sh, const int64_t* voff, const 
                                const int32_t* dsrc, const double* vals, uint8_t* blob, cudaStream_t st) {
     const int64_t nv = (int64_t)sh.voff.size(), nd = (int64_t)sh.doff.size();
     if (nv == 0 && nd == 0) return cudaSuccess;
-    k_pack_stream<T><<<1024, 256, 0, st>>>(nv, nd, voff, vsrc, doff, dsrc, vals, blob);
+    if (sizeof(T) == 4 && sh.val_bytes == 2)  // bfloat16 values, float pivot inverses
+        k_pack_stream<T, __nv_bfloat16><<<1024, 256, 0, st>>>(nv, nd, voff, vsrc, doff, dsrc, vals, blob);
+    else
+        k_pack_stream<T><<<1024, 256, 0, st>>>(nv, nd, voff, vsrc, doff, dsrc, vals, blob);
     return cudaGetLastError();
 }
 
@@ -967,18 +998,33 @@ cudaError_t launch_pack_stream(const StreamHost& sh, const int64_t* voff, const 
         constexpr bool XS = false;           \
         ILU2L_RW_DISPATCH(h, id, CALL)       \
     }
-#define ILU2L_IDX_DISPATCH(h, id, CALL) ILU2L_XS_DISPATCH(h, id, CALL)
+// value storage of the records (V): bfloat16 when a float handle stores its factors so
+#define ILU2L_V_DISPATCH(h, STMT)                  \
+    if constexpr (sizeof(T) == 4) {                \
+        if ((h).prec == ILU_PREC_BF16_STORE) {     \
+            using V = __nv_bfloat16;               \
+            STMT                                   \
+        } else {                                   \
+            using V = T;                           \
+            STMT                                   \
+        }                                          \
+    } else {                                       \
+        using V = T;                               \
+        STMT                                       \
+    }
+#define ILU2L_IDX_DISPATCH(h, id, CALL) ILU2L_V_DISPATCH(h, ILU2L_XS_DISPATCH(h, id, CALL))
+#define ILU2L_VRW_DISPATCH(h, id, CALL) ILU2L_V_DISPATCH(h, ILU2L_RW_DISPATCH(h, id, CALL))
 
 template <class T>
 cudaError_t launch_bj_s(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
-    ILU2L_IDX_DISPATCH(h, PR_BJ, (k_bj_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_IDX_DISPATCH(h, PR_BJ, (k_bj_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                               h.sub(), sdev<T>(h, PR_BJ), rcfg(h), r, z, (T*)h.d_xg, done)));
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_fwd_s(const Handle& h, const double* r, const int32_t* done, cudaStream_t st) {
-    ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_fwd_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_fwd_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                               h.sub(), sdev<T>(h, PR_FWDS), rcfg(h), h.innerdev<T>(), r, (T*)h.d_fq, (T*)h.d_xg,
                               done)));
     return cudaGetLastError();
@@ -993,7 +1039,7 @@ cudaError_t inner_coop_fits(const Handle& h, bool* fits) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (e != cudaSuccess || !coop) return e;
     ILU2L_IDX_DISPATCH(h, PR_S, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                     &nb, k_inner_coop<T, RW, XS>, 256, stream_smem(h, sizeof(T)))));
+                                     &nb, k_inner_coop<T, RW, XS, V>, 256, stream_smem(h, sizeof(T)))));
     if (e == cudaSuccess) *fits = (int64_t)nb * h.sm_count >= h.p;
     return e;
 }
@@ -1011,7 +1057,7 @@ static cudaError_t launch_inner_coop(const Handle& h, const int32_t* done, cudaS
     lc.attrs = at;
     lc.numAttrs = 1;
     cudaError_t e = cudaSuccess;
-    ILU2L_IDX_DISPATCH(h, PR_S, (e = cudaLaunchKernelEx(&lc, k_inner_coop<T, RW, XS>, h.sub(), sdev<T>(h, PR_S),
+    ILU2L_IDX_DISPATCH(h, PR_S, (e = cudaLaunchKernelEx(&lc, k_inner_coop<T, RW, XS, V>, h.sub(), sdev<T>(h, PR_S),
                                                          rcfg(h), h.innerdev<T>(), (T*)h.d_xg, done)));
     return e;
 }
@@ -1023,7 +1069,7 @@ cudaError_t launch_inner_s(const Handle& h, const int32_t* done, cudaStream_t st
     const int gb = std::max(1, std::min(h.sm_count * 4, (h.n2 + 255) / 256));
     for (int j = 0; j < h.inner_k; j++) {
         k_coff<T><<<gb, 256, 0, st>>>(h.sub(), h.innerdev<T>(), j, (T*)h.d_tbuf, done);
-        ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+        ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                   h.sub(), sdev<T>(h, PR_S), rcfg(h), h.innerdev<T>(), j, (const T*)h.d_tbuf,
                                   (T*)h.d_xg, done)));
         cudaError_t e = cudaGetLastError();
@@ -1036,7 +1082,7 @@ cudaError_t launch_inner_s(const Handle& h, const int32_t* done, cudaStream_t st
 
 template <class T>
 cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int32_t* done, cudaStream_t st) {
-    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_bwd_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_bwd_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                               h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), r, (const T*)h.d_fq,
                               h.form == ILU_FORM_EF ? 1 : 0, z, (T*)h.d_xg, done)));
     return cudaGetLastError();
@@ -1044,7 +1090,7 @@ cudaError_t launch_bwd_s(const Handle& h, const double* r, double* z, const int3
 
 template <class T>
 cudaError_t launch_inner_start_s(const Handle& h, const double* gp, cudaStream_t st) {
-    ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_IDX_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                               h.sub(), sdev<T>(h, PR_S), rcfg(h), h.innerdev<T>(), gp, (T*)h.d_xg)));
     return cudaGetLastError();
 }
@@ -1057,13 +1103,13 @@ cudaError_t launch_inner_io_ws(const Handle& h, const InnerDev<T>& in, T* tbuf, 
     if (h.n2 == 0) return cudaSuccess;
     constexpr bool XS = true;
     T* xdummy = tbuf;  // unused by the shared-memory kernels
-    ILU2L_RW_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_VRW_DISPATCH(h, PR_S, (k_inner_start_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                    h.sub(), sdev<T>(h, PR_S), rcfg(h), in, gp, xdummy)));
     cudaError_t e = cudaGetLastError();
     const int gb = std::max(1, std::min(h.sm_count * 4, (h.n2 + 255) / 256));
     for (int j = 0; j < h.inner_k && e == cudaSuccess; j++) {
         k_coff<T><<<gb, 256, 0, st>>>(h.sub(), in, j, tbuf, nullptr);
-        ILU2L_RW_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+        ILU2L_VRW_DISPATCH(h, PR_S, (k_inner_a_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                        h.sub(), sdev<T>(h, PR_S), rcfg(h), in, j, tbuf, xdummy, nullptr)));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = launch_inner_bc_ws<T>(h, in, j, 0, st);
@@ -1078,13 +1124,13 @@ cudaError_t launch_rap_inner_s(const Handle& h, const int32_t* done, cudaStream_
     if (h.n2 == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < h.inner_k && e == cudaSuccess; j++) {
-        ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_p_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+        ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_p_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                           h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), j, h.rap_pv,
                                           (T*)h.d_xg, done)));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = launch_rap_resid(h, nullptr, h.rap_pv, h.rap_apv, done, st);
         if (e == cudaSuccess) {
-            ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_rap_r_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+            ILU2L_IDX_DISPATCH(h, PR_FWDS, (k_rap_r_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                                h.sub(), sdev<T>(h, PR_FWDS), rcfg(h), h.innerdev<T>(), j,
                                                h.rap_apv, (T*)h.d_xg, done)));
             e = cudaGetLastError();
@@ -1098,7 +1144,7 @@ cudaError_t launch_rap_inner_s(const Handle& h, const int32_t* done, cudaStream_
 template <class T>
 cudaError_t launch_rap_fin_s(const Handle& h, double* z, const int32_t* done, cudaStream_t st) {
     if (h.n2 == 0) return cudaSuccess;
-    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_fin_s<T, RW, XS><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
+    ILU2L_IDX_DISPATCH(h, PR_BWD, (k_rap_fin_s<T, RW, XS, V><<<h.p, 256, stream_smem(h, sizeof(T)), st>>>(
                                       h.sub(), sdev<T>(h, PR_BWD), rcfg(h), h.innerdev<T>(), z, (T*)h.d_xg,
                                       done)));
     return cudaGetLastError();

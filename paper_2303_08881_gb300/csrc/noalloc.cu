@@ -80,5 +80,5 @@ extern "C" ilu_status ilu_inner_solve_noalloc(void* hp, const double* gp, double
     Handle* h = static_cast<Handle*>(hp);
     if (h->o.analysis_only || h->variant != ILU_VARIANT_SCHUR) return ILU_ERR_ARG;
     if (!h->stream_path || h->max_ns + 1 > h->smem_len_stream) return ILU_ERR_UNSUPPORTED;
-    return (h->prec == ILU_PREC_FP32) ? inner_noalloc<float>(*h, gp, y) : inner_noalloc<double>(*h, gp, y);
+    return (h->prec != ILU_PREC_FP64) ? inner_noalloc<float>(*h, gp, y) : inner_noalloc<double>(*h, gp, y);
 }

@@ -360,7 +360,7 @@ int ilut_local(const int32_t* rp, const int32_t* ci, const double* a, int32_t m,
 // ====================================================================================
 // chunked streams (stream_layout.h)
 
-bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, uint32_t chunk,
+bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int val_bytes, uint32_t chunk,
                   StreamHost& S) {
     S.blob.clear();
     S.ch0.assign(1, 0);
@@ -371,6 +371,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     S.chunk = chunk;
     S.idx_bytes = idx_bytes;
     S.val_bytes = val_bytes;
+    S.x_bytes = x_bytes;
     S.levels = (int64_t)P.lvl_ptr.size() - 1;
     S.rows = (int64_t)P.prow.size();
     S.entries = (int64_t)P.pcol.size();
@@ -380,7 +381,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
     for (size_t k = 0; k + 1 < P.pptr.size(); k++) longer += (P.pptr[k + 1] - P.pptr[k]) > 4;
     S.rw = (longer * 20 <= (int64_t)P.prow.size()) ? 4 : 16;
     const int32_t RW = S.rw;
-    const RecLayout RL = rec_layout((uint32_t)S.rw, (uint32_t)val_bytes);
+    const RecLayout RL = rec_layout((uint32_t)S.rw, (uint32_t)val_bytes, (uint32_t)x_bytes);
     S.rec_bytes = RL.bytes;
     // a whole wave (one record per consumer thread) must fit one chunk
     const int nt_fit = (int)(((chunk - kChunkHdr - 16) / RL.bytes) / 32 * 32);
@@ -597,7 +598,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
                                 put(rb, kRecSkip, 4);
                                 continue;
                             }
-                            const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)val_bytes;
+                            const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)x_bytes;
                             put(rb, row_off | ((uint32_t)pc->n << 24), 4);
                             F.doff.push_back((int64_t)(rb + RL.dinv));
                             F.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
@@ -607,7 +608,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int val_bytes, ui
                                     continue;
                                 }
                                 const int32_t src = P.pptr[pc->k] + pc->q0 + q;
-                                put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)val_bytes, 4);
+                                put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)x_bytes, 4);
                                 F.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
                                 F.vsrc.push_back(P.psrc[src]);
                             }
@@ -1198,8 +1199,10 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     // ---- chunked streams of the programs the apply runs (TMA fast path)
     if (h.stream_path) {
         h.idx_bytes = 4;
-        if ((int64_t)(h.max_ns + 1) * (h.prec == ILU_PREC_FP32 ? 4 : 8) >= (1 << 24)) h.stream_path = false;
-        const int vb = (h.prec == ILU_PREC_FP32) ? 4 : 8;
+        // working vector (and dinv) in the arithmetic type; values in it or in bfloat16
+        const int vb = (h.prec == ILU_PREC_FP64) ? 8 : 4;
+        const int valb = (h.prec == ILU_PREC_BF16_STORE) ? 2 : vb;
+        if ((int64_t)(h.max_ns + 1) * vb >= (1 << 24)) h.stream_path = false;
         std::vector<int> ids = rap     ? std::vector<int>{PR_BJ, PR_FWDS, PR_BWD}
                                : schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD}
                                        : std::vector<int>{PR_BJ};
@@ -1235,7 +1238,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 break;
             }
         bool ok = true;
-        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, h.chunk, h.sh[id]);
+        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, valb, h.chunk, h.sh[id]);
         if (!ok) h.stream_path = false;
     }
     return ILU_OK;

@@ -19,7 +19,7 @@
 //   uint32 head      byte offset of x[row] | (n << 24); bit 31 marks a skip record
 //   T      dinv      1 / u_ii for an upper-triangular row, 1 for a unit-lower row
 //   uint32 col[RW]   byte offsets of x[col]; entries n.. hold the row's own offset
-//   T      val[RW]   entries n.. hold zero
+//   V      val[RW]   entries n.. hold zero (V = T, or bfloat16 with T = float)
 // and computes x[row] = (x[row] - sum_{q<RW} val[q] * x[col[q]]) * dinv, the sum formed
 // pairwise. The padded entries add exact zeros, so every record takes the same
 // branch-free path. A skip record (a hole in a wave) reads slot 0 and stores nothing.
@@ -52,9 +52,11 @@ struct RecLayout {
     uint32_t dinv, col, val, bytes;
 };
 
-ILU2L_HD constexpr RecLayout rec_layout(uint32_t rw, uint32_t val_bytes) {
-    return RecLayout{val_bytes, 2 * val_bytes, al(2 * val_bytes + rw * 4, val_bytes),
-                     al(al(2 * val_bytes + rw * 4, val_bytes) + rw * val_bytes, 16)};
+// byte offsets of dinv, col and val and the record size, for values of val_bytes and
+// vector elements (and dinv) of x_bytes
+ILU2L_HD constexpr RecLayout rec_layout(uint32_t rw, uint32_t val_bytes, uint32_t x_bytes) {
+    return RecLayout{x_bytes, 2 * x_bytes, al(2 * x_bytes + rw * 4, val_bytes),
+                     al(al(2 * x_bytes + rw * 4, val_bytes) + rw * val_bytes, 16)};
 }
 
 }  // namespace ilu2l

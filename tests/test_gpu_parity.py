@@ -339,6 +339,50 @@ def test_rap_fgmres_matches_oracle(ilu, prec):
     h.close()
 
 
+@pytest.mark.parametrize("name", ["poisson64", "aniso2d_ragged", "conv3d", "cuts3d", "rand", "p1", "dense_rows"])
+@pytest.mark.parametrize("variant", ["bj", "schur", "rap"])
+def test_bf16_storage_apply_matches_oracle(ilu, name, variant):
+    """bfloat16 factor values in the records, FP32 arithmetic: against the oracle whose
+    off-diagonal factor entries are rounded to bfloat16 the same way, the only difference
+    left is the FP32 arithmetic, so the FP32 bar applies."""
+    pr = _prob(name)
+    cfg = dict(variant=variant, factor_B="ilu0", factor_S="milu0")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="bf16", **cfg))
+    orc = O.Oracle.from_problem(pr, store_bf16=True, **cfg)
+    assert h.stats()["stream_path"]
+    r = np.random.default_rng(29).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    torch.cuda.synchronize()
+    got, ref = z.cpu().numpy(), orc.apply(r)
+    assert np.isfinite(got).all() and h.stats()["device_error"] == 0
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL32
+    # and it is not the unrounded preconditioner
+    ref32 = O.Oracle.from_problem(pr, **cfg).apply(r)
+    assert np.linalg.norm(got - ref32) > np.linalg.norm(got - ref)
+    h.close()
+
+
+def test_bf16_storage_fgmres_matches_oracle(ilu):
+    pr = _prob("aniso2d_ragged")
+    cfg = dict(variant="schur", factor_B="ilu0", factor_S="milu0")
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="bf16", **cfg))
+    ro = O.Oracle.from_problem(pr, store_bf16=True, **cfg).fgmres(pr.b, rtol=1e-8, restart=50, maxit=5000)
+    b = _dev(pr.b)
+    x = torch.zeros_like(b)
+    info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=50, maxit=5000)
+    assert ro["status"] == 0 and info["status"] == 0 and info["rel_res_true"] <= 1e-8
+    assert abs(info["iters"] - ro["iters"]) <= max(2, ro["iters"] // 10), (info["iters"], ro["iters"])
+    h.close()
+
+
+def test_bf16_storage_refuses_what_it_does_not_cover(ilu):
+    pr = _prob("poisson64")
+    for kw in (dict(factor_B="ilut"), dict(form="ef"), dict(kernel_path="generic")):
+        with pytest.raises(ilu.IluError):
+            ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="bf16", **kw))
+
+
 def test_rap_needs_the_streamed_path(ilu):
     pr = _prob("aniso2d_ragged")
     with pytest.raises(ilu.IluError) as e:

@@ -34,6 +34,8 @@ CFGS = [
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="rcm"),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="rcm"),
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", pc_precision="bf16"),
+    dict(variant="rap", factor_B="ilu0", factor_S="milu0", pc_precision="bf16"),
 ]
 SKIP = 1 << 31
 BARRIER = 1 << 31
@@ -56,8 +58,9 @@ def parse(st):
     list of waves; a wave is a list of (thread, write_slot, [read slots]) with skip
     records left out. Checks the geometry and the padding of every record."""
     blob, ch0, chunk, rw, vb = st["blob"].tobytes(), st["ch0"], st["chunk"], st["rw"], st["val_bytes"]
-    col_off = 2 * vb
-    rec_bytes = _al(_al(2 * vb + 4 * rw, vb) + rw * vb, 16)
+    xb = st["x_bytes"]  # element size of the working vector and of dinv
+    col_off = 2 * xb
+    rec_bytes = _al(_al(2 * xb + 4 * rw, vb) + rw * vb, 16)
     subs = []
     for s in range(len(ch0) - 1):
         stretches, cur = [], []
@@ -80,9 +83,9 @@ def parse(st):
                             assert head == SKIP and not any(cols)
                             continue
                         n, roff = (head >> 24) & 0x7F, head & 0xFFFFFF
-                        assert n <= rw and roff % vb == 0 and all(x % vb == 0 for x in cols)
+                        assert n <= rw and roff % xb == 0 and all(x % xb == 0 for x in cols)
                         assert all(x == roff for x in cols[n:]), "unused entries read the row's own slot"
-                        wave.append((t, roff // vb, [x // vb for x in cols[:n]]))
+                        wave.append((t, roff // xb, [x // xb for x in cols[:n]]))
                     cur.append(wave)
                 if w1 & BARRIER:
                     stretches.append(cur)
