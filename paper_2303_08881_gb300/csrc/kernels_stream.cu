@@ -163,7 +163,7 @@ __device__ __forceinline__ void ring_rearm(const StreamDev<T>& S, int s, const S
 // type of the values: T, or bfloat16 for T = float (values widened on use).
 template <class T, int RW, class V = T>
 struct __align__(16) RowRec {
-    uint32_t head;  // byte offset of x[row] | n << 24 | skip bit
+    uint32_t head;  // element index of x[row] | n << 24 | skip bit
     T dinv;
     uint32_t col[RW];  // byte offsets (unused entries: the row's own)
     V val[RW];         // (unused entries: zero)
@@ -193,6 +193,12 @@ __device__ __forceinline__ void rec_load(RecU<T, RW, V>& u, const uint8_t* p) {
     for (int i = 0; i < NV; i++) u.v[i] = s[i];
 }
 
+// byte offset of a record's own slot x[row] (the head holds the row's element index)
+template <class T>
+__device__ __forceinline__ uint32_t row_byte(uint32_t head) {
+    return (head & 0xFFFFFFu) * (uint32_t)sizeof(T);
+}
+
 template <class T>
 __device__ __forceinline__ T ldx(const uint8_t* xb, uint32_t off) {
     return *reinterpret_cast<const T*>(xb + off);
@@ -203,7 +209,7 @@ template <class T, int RW, class V>
 __device__ __forceinline__ void rec_operands(const RecU<T, RW, V>& u, const uint8_t* xb, T (&xc)[RW], T& xr) {
 #pragma unroll
     for (int q = 0; q < RW; q++) xc[q] = ldx<T>(xb, u.r.col[q]);
-    xr = ldx<T>(xb, u.r.head & 0xFFFFFFu);
+    xr = ldx<T>(xb, row_byte<T>(u.r.head));
 }
 
 // x[row] = (x[row] - sum_q val[q] x[col[q]]) * dinv, the sum formed pairwise
@@ -233,7 +239,7 @@ __device__ __forceinline__ void run_segment(const RecU<T, RW, V>& first, const u
     T xa[RW], xra;
     rec_operands(a, xb, xa, xra);
     if (nw == 1) {  // a single wave: no pipeline
-        if ((a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + (a.r.head & 0xFFFFFFu)) = rec_value(a, xa, xra);
+        if ((a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(a.r.head)) = rec_value(a, xa, xra);
         return;
     }
     rec_load(b, p + (nw > 1 ? stride : 0u));
@@ -245,11 +251,11 @@ __device__ __forceinline__ void run_segment(const RecU<T, RW, V>& first, const u
         const uint32_t ha = a.r.head;
         const T v = rec_value(a, xa, xra);
         const bool real = (ha & kRecSkip) == 0;
-        const uint32_t fwd = real ? (ha & 0xFFFFFFu) : 0xFFFFFFFFu;
-        if (real) *reinterpret_cast<T*>(xb + (ha & 0xFFFFFFu)) = v;
+        const uint32_t fwd = real ? row_byte<T>(ha) : 0xFFFFFFFFu;
+        if (real) *reinterpret_cast<T*>(xb + fwd) = v;
 #pragma unroll
         for (int q = 0; q < RW; q++) xa[q] = (b.r.col[q] == fwd) ? v : xn[q];
-        xra = ((b.r.head & 0xFFFFFFu) == fwd) ? v : xrn;
+        xra = (row_byte<T>(b.r.head) == fwd) ? v : xrn;
         a = b;
         b = c;
     }

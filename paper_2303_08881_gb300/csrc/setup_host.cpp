@@ -599,7 +599,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                                 continue;
                             }
                             const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)x_bytes;
-                            put(rb, row_off | ((uint32_t)pc->n << 24), 4);
+                            put(rb, (uint32_t)P.prow[pc->k] | ((uint32_t)pc->n << 24), 4);  // row index | n
                             F.doff.push_back((int64_t)(rb + RL.dinv));
                             F.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
                             for (int32_t q = 0; q < RW; q++) {
@@ -1202,7 +1202,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         // working vector (and dinv) in the arithmetic type; values in it or in bfloat16
         const int vb = (h.prec == ILU_PREC_FP64) ? 8 : 4;
         const int valb = (h.prec == ILU_PREC_BF16_STORE) ? 2 : vb;
-        if ((int64_t)(h.max_ns + 1) * vb >= (1 << 24)) h.stream_path = false;
+        if ((int64_t)h.max_ns + 1 >= (1 << 24)) h.stream_path = false;  // the head's row index: 24 bits
         std::vector<int> ids = rap     ? std::vector<int>{PR_BJ, PR_FWDS, PR_BWD}
                                : schur ? std::vector<int>{PR_FWDS, PR_S, PR_BWD}
                                        : std::vector<int>{PR_BJ};

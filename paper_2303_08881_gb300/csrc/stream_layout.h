@@ -16,15 +16,16 @@
 // (the builder arranges this; a thread's own program order covers everything else).
 //
 // A row record (16-byte aligned, read with 128-bit shared-memory loads) holds
-//   uint32 head      byte offset of x[row] | (n << 24); bit 31 marks a skip record
+//   uint32 head      element index of x[row] | (n << 24); bit 31 marks a skip record
 //   T      dinv      1 / u_ii for an upper-triangular row, 1 for a unit-lower row
 //   uint32 col[RW]   byte offsets of x[col]; entries n.. hold the row's own offset
 //   V      val[RW]   entries n.. hold zero (V = T, or bfloat16 with T = float)
 // and computes x[row] = (x[row] - sum_{q<RW} val[q] * x[col[q]]) * dinv, the sum formed
 // pairwise. The padded entries add exact zeros, so every record takes the same
 // branch-free path. A skip record (a hole in a wave) reads slot 0 and stores nothing.
-// Offsets are pre-scaled by the element size so the consumer adds them to the vector's
-// base.
+// Column offsets are pre-scaled by the element size so the consumer adds them to the
+// vector's base; the row index is scaled on use (24 bits: up to 2^24 rows per subdomain in
+// either precision).
 #pragma once
 
 #include <stdint.h>

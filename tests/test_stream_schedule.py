@@ -82,10 +82,10 @@ def parse(st):
                         if head & SKIP:
                             assert head == SKIP and not any(cols)
                             continue
-                        n, roff = (head >> 24) & 0x7F, head & 0xFFFFFF
-                        assert n <= rw and roff % xb == 0 and all(x % xb == 0 for x in cols)
-                        assert all(x == roff for x in cols[n:]), "unused entries read the row's own slot"
-                        wave.append((t, roff // xb, [x // xb for x in cols[:n]]))
+                        n, row = (head >> 24) & 0x7F, head & 0xFFFFFF  # the head holds the row's index
+                        assert n <= rw and all(x % xb == 0 for x in cols)
+                        assert all(x == row * xb for x in cols[n:]), "unused entries read the row's own slot"
+                        wave.append((t, row, [x // xb for x in cols[:n]]))
                     cur.append(wave)
                 if w1 & BARRIER:
                     stretches.append(cur)
