@@ -17,13 +17,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
-ILU0, MILU0, ILUT, EXACT = 0, 1, 2, 3
+ILU0, MILU0, ILUT, EXACT, PMILU0 = 0, 1, 2, 3, 4
 BJ, SCHUR, RAP = 0, 1, 2
 FORM_AUTO, FORM_WZ, FORM_EF = 0, 1, 2
 ORDER_NATURAL, ORDER_RCM = 0, 1
 OK, ERR_ARG, ERR_CSR, ERR_OOM, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 
-_FACT = {"ilu0": ILU0, "milu0": MILU0, "ilut": ILUT, "exact": EXACT}
+_FACT = {"ilu0": ILU0, "milu0": MILU0, "ilut": ILUT, "exact": EXACT, "pmilu0": PMILU0}
 _VAR = {"bj": BJ, "schur": SCHUR, "rap": RAP}
 
 

@@ -115,7 +115,7 @@ static int pivot_rule(double* uii, double rowmax, double eps, int* npert) {
    dropped entries of row i, H_ij = -l_ik u_kj, are summed into Delta_i and added to
    the pivot, u_ii + Delta_i, so that the row sums of LU equal those of A. */
 static int ilu0_factor(int n, const int* rp, const int* ci, const double* a, int milu,
-                       double eps, double* f, int* npert) {
+                       int milu_from, double eps, double* f, int* npert) {
     int* pos = (int*)malloc(((size_t)n + 1) * sizeof(int));
     int* dpos = (int*)malloc(((size_t)n + 1) * sizeof(int));
     if (!pos || !dpos) {
@@ -142,7 +142,7 @@ static int ilu0_factor(int n, const int* rp, const int* ci, const double* a, int
                 int j = ci[t];
                 if (pos[j] >= 0)
                     f[pos[j]] -= lik * f[t];
-                else
+                else if (k >= milu_from) /* only these pivots' drops are compensated */
                     delta -= lik * f[t];
             }
         }
@@ -158,7 +158,7 @@ static int ilu0_factor(int n, const int* rp, const int* ci, const double* a, int
 int orc_ilu0_csr(int n, const int* rp, const int* ci, const double* val, int milu,
                  double pivot_eps, double* out_val, int* npert) {
     int np = 0;
-    int st = ilu0_factor(n, rp, ci, val, milu, pivot_eps, out_val, &np);
+    int st = ilu0_factor(n, rp, ci, val, milu, 0, pivot_eps, out_val, &np);
     if (npert) *npert = np;
     return st;
 }
@@ -902,14 +902,19 @@ void orc_free(void* hp) {
 }
 
 /* factor one local matrix with the requested kind */
-static int factor_kind(const csr_t* M, int kind, const orc_opts* o, csr_t* out, int* npert) {
-    if (kind == ORC_ILU0 || kind == ORC_MILU0) {
+/* ni: interior rows of the local block (where the interface rows begin) */
+static int factor_kind(const csr_t* M, int kind, const orc_opts* o, int ni, csr_t* out, int* npert) {
+    if (kind == ORC_ILU0 || kind == ORC_MILU0 || kind == ORC_PMILU0) {
         int st = csr_init(out, M->nr, M->nc, M->nnz);
         if (st) return st;
         memcpy(out->rp, M->rp, ((size_t)M->nr + 1) * sizeof(int));
         memcpy(out->ci, M->ci, (size_t)M->nnz * sizeof(int));
-        return ilu0_factor(M->nr, M->rp, M->ci, M->v, kind == ORC_MILU0, o->pivot_eps, out->v,
-                           npert);
+        /* PMILU0 (Sec. 3.2, partial ILU): in IKJ order the interior pivots come first, so
+           eliminating them with plain dropping and the interface pivots with MILU's
+           compensation is the partial ILU(0) of A_i followed by MILU(0) of the Schur
+           complement it leaves */
+        return ilu0_factor(M->nr, M->rp, M->ci, M->v, kind != ORC_ILU0, kind == ORC_PMILU0 ? ni : 0,
+                           o->pivot_eps, out->v, npert);
     }
     if (kind == ORC_ILUT)
         return ilut_factor(M->nr, M->rp, M->ci, M->v, o->ilut_tau, o->ilut_p, o->pivot_eps, out,
@@ -1100,7 +1105,8 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
     /* ILU(k) / MILU(k): each local block stored in its level-k pattern, so that ILU(0) /
        MILU(0) of the stored block is ILU(k) / MILU(k) of A_s */
     if (h->o.fill_level < 0 ||
-        (h->o.fill_level > 0 && (h->o.factor_B > ORC_MILU0 || h->o.factor_S > ORC_MILU0))) {
+        (h->o.fill_level > 0 && (h->o.factor_B > ORC_MILU0 ||
+                                 (h->o.factor_S > ORC_MILU0 && h->o.factor_S != ORC_PMILU0)))) {
         st = ORC_ERR_ARG;
         goto fail;
     }
@@ -1128,8 +1134,9 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
             st = ORC_ERR_ARG;
             goto fail;
         }
-        if (kB < 0 || kB > 3 || kS < 0 || kS > 3 || kS == ORC_ILUT ||
-            (h->o.variant == ORC_RAP && kB == ORC_ILUT)) {
+        if (kB < 0 || kB > 3 || kS < 0 || kS > 4 || kS == ORC_ILUT ||
+            (h->o.variant == ORC_RAP && kB == ORC_ILUT) ||
+            (kS == ORC_PMILU0 && h->o.variant != ORC_SCHUR)) {
             st = ORC_ERR_ARG;
             goto fail;
         }
@@ -1140,10 +1147,10 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
             if (bonly) {
                 csr_t B;
                 st = extract_B(&h->Aloc[s], nint_of(h, s), &B);
-                if (!st) st = factor_kind(&B, kB, &h->o, &h->F1[s], &h->npert);
+                if (!st) st = factor_kind(&B, kB, &h->o, nint_of(h, s), &h->F1[s], &h->npert);
                 csr_release(&B);
             } else {
-                st = factor_kind(&h->Aloc[s], kB, &h->o, &h->F1[s], &h->npert);
+                st = factor_kind(&h->Aloc[s], kB, &h->o, nint_of(h, s), &h->F1[s], &h->npert);
             }
         }
         if (st) goto fail;
@@ -1154,7 +1161,7 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
                 goto fail;
             }
             for (int s = 0; s < p && !st; s++)
-                st = factor_kind(&h->Aloc[s], kS, &h->o, &h->F2[s], &h->npert);
+                st = factor_kind(&h->Aloc[s], kS, &h->o, nint_of(h, s), &h->F2[s], &h->npert);
             if (st) goto fail;
         } else {
             h->F2 = h->F1;

@@ -35,6 +35,8 @@ extern "C" {
 #define ORC_MILU0 1
 #define ORC_ILUT 2
 #define ORC_EXACT 3   /* full LU without dropping (ILUT with tau = 0, p = inf); pins only */
+#define ORC_PMILU0 4  /* factor_S of SCHUR: partial ILU(0) of A_i (interior pivots, plain
+                         dropping), then MILU(0) of the Schur complement it leaves (Sec. 3.2) */
 
 /* variants and forms */
 #define ORC_BJ 0

@@ -372,6 +372,48 @@ def test_exact_two_level_apply_is_A_inverse(kind, form):
     np.testing.assert_allclose(z, np.linalg.solve(pr.scipy().toarray(), r), rtol=1e-9, atol=1e-10)
 
 
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "cuts3d"])
+def test_pmilu0_is_milu0_of_the_partial_ilu_schur_complement(kind):
+    """Sec. 3.2 (partial ILU): the partial ILU(0) of A_i leaves S~ = (C - W Z) on the pattern
+    of C, with W = E U_B^{-1} and Z = L_B^{-1} F from the ILU(0) factors (Eq. pILU); factor_S =
+    pmilu0 is MILU(0) of that S~. Built here from the ILU(0) factors by a sparse product and
+    the separately pinned MILU(0) routine; the interior rows are plain ILU(0)."""
+    pr = P.aniso3d_cuts(10, ncuts=(1, 1, 1), seed=3) if kind == "cuts3d" else _small_dd(kind)
+    kw = dict(variant="schur", factor_B="ilu0", pivot_eps=0.0)
+    o = O.Oracle.from_problem(pr, factor_S="pmilu0", **kw)
+    o0 = O.Oracle.from_problem(pr, factor_S="ilu0", **kw)
+    pm = o.perm()
+    checked = 0
+    for sd in range(pr.p):
+        ni = int(pm["int_ptr"][sd + 1] - pm["int_ptr"][sd])
+        rp, ci, av = o.local_csr(sd)
+        m = rp.size - 1
+        if ni == m or ni == 0:
+            continue
+        f1 = o0.local_factor(sd, 1)                 # ILU(0) of A_i
+        f2 = o.local_factor(sd, 2)                  # the pmilu0 factorisation
+        F1 = sp.csr_matrix((f1, ci, rp), shape=(m, m)).toarray()
+        Am = sp.csr_matrix((av, ci, rp), shape=(m, m)).toarray()
+        pat = sp.csr_matrix((np.ones(ci.size), ci, rp), shape=(m, m)).toarray() != 0
+        W, Z = F1[ni:, :ni], F1[:ni, ni:]
+        St = np.where(pat[ni:, ni:], Am[ni:, ni:] - W @ Z, 0.0)
+        Sc = sp.csr_matrix(St * pat[ni:, ni:])
+        # keep the pattern of C (explicit zeros included)
+        Sc = sp.csr_matrix((St[pat[ni:, ni:]], np.nonzero(pat[ni:, ni:])[1],
+                            np.r_[0, np.cumsum(pat[ni:, ni:].sum(axis=1))]), shape=(m - ni, m - ni))
+        fS, st, _ = O.ilu0(m - ni, Sc.indptr, Sc.indices, Sc.data, milu=True)
+        assert st == 0
+        F2 = sp.csr_matrix((f2, ci, rp), shape=(m, m)).toarray()
+        got = F2[ni:, ni:][pat[ni:, ni:]]
+        np.testing.assert_allclose(got, fS, rtol=1e-11, atol=1e-12 * np.abs(fS).max())
+        # interior rows: plain ILU(0), identical
+        assert np.array_equal(f2[:rp[ni]], f1[:rp[ni]])
+        checked += 1
+    assert checked > 0
+    with pytest.raises(RuntimeError):
+        O.Oracle.from_problem(pr, variant="bj", factor_S="pmilu0")
+
+
 def test_inner_gmres_full_steps_solves_preconditioned_schur_system():
     """Eq. preSS: (I + S~^{-1} C_off) y = S~^{-1} g'  <=>  (blockdiag(L_S U_S) + C_off) y = g'.
     With k = n2 steps inner GMRES returns that solution; residuals shrink with k."""
