@@ -58,7 +58,11 @@ typedef struct {
    factor_B is the smoother on each whole local block (ILU(0) or MILU(0)), factor_S gives R,
    P and the coarse preconditioner L_S U_S (MILU(0) in the paper); streamed path only. */
 typedef enum { ILU_VARIANT_BJ = 0, ILU_VARIANT_SCHUR = 1, ILU_VARIANT_RAP = 2 } ilu_variant;
-typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2 } ilu_fact;
+/* PMILU0 (factor_S of SCHUR only): the partial ILU(0) of A_i (interior pivots, plain
+   dropping) followed by MILU(0) of the Schur complement it leaves (Sec. 3.2, partial ILU),
+   computed as one factorisation of A_i whose modification counts only the updates dropped by
+   interface pivots. */
+typedef enum { ILU_FACT_ILU0 = 0, ILU_FACT_MILU0 = 1, ILU_FACT_ILUT = 2, ILU_FACT_PMILU0 = 3 } ilu_fact;
 typedef enum { ILU_FORM_AUTO = 0, ILU_FORM_WZ = 1, ILU_FORM_EF = 2 } ilu_form;
 /* FP64, FP32: factors and arithmetic of M^{-1} in that type. BF16_STORE: FP32 arithmetic
    with every off-diagonal factor entry of the level programs stored as bfloat16 (nearest,

@@ -22,7 +22,7 @@ ILU_OK, ILU_ERR_ARG, ILU_ERR_CSR, ILU_ERR_OOM, ILU_ERR_ZERO_PIVOT = 0, 1, 2, 3, 
 ILU_ERR_NOT_CONVERGED, ILU_ERR_BREAKDOWN, ILU_ERR_TIMEOUT, ILU_ERR_CUDA = 5, 6, 7, 8
 ILU_ERR_TOO_LARGE, ILU_ERR_UNSUPPORTED = 9, 10
 VARIANTS = {"bj": 0, "schur": 1, "rap": 2}
-FACTORS = {"ilu0": 0, "milu0": 1, "ilut": 2}
+FACTORS = {"ilu0": 0, "milu0": 1, "ilut": 2, "pmilu0": 3}  # pmilu0: factor_S of SCHUR only
 FORMS = {"auto": 0, "wz": 1, "ef": 2}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}  # bf16: FP32 arithmetic, bfloat16 factor values
 LEVELS = {"LA": 0, "UA": 1, "LB": 2, "UB": 3, "LS": 4, "US": 5}

@@ -227,7 +227,9 @@ ilu_status device_setup(Handle& h) {
     CK(upload(h, &h.d_num_lvl, h.numprog.lvl_ptr));
     CK(upload(h, &h.d_num_row, h.numprog.prow));
     if (h.f1_device) CK(launch_ilu_numeric(h, h.d_vals + h.f1.base, h.kB == ILU_FACT_MILU0 ? 1 : 0, h.st));
-    if (!h.f2_alias) CK(launch_ilu_numeric(h, h.d_vals + h.f2.base, h.kS == ILU_FACT_MILU0 ? 1 : 0, h.st));
+    if (!h.f2_alias)
+        CK(launch_ilu_numeric(h, h.d_vals + h.f2.base,
+                              h.kS == ILU_FACT_MILU0 ? 1 : (h.kS == ILU_FACT_PMILU0 ? 2 : 0), h.st));
     int32_t herr = 0, hpert = 0;
     CK(cudaMemcpyAsync(&herr, h.d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, h.st));
     CK(cudaMemcpyAsync(&hpert, h.d_npert, sizeof(int32_t), cudaMemcpyDeviceToHost, h.st));
@@ -482,7 +484,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
     const ilu_opts& o = h->o;
     if ((o.variant != ILU_VARIANT_BJ && o.variant != ILU_VARIANT_SCHUR && o.variant != ILU_VARIANT_RAP) ||
         (o.variant == ILU_VARIANT_RAP && o.factor_B == ILU_FACT_ILUT) || o.factor_B < 0 || o.factor_B > 2 ||
-        o.factor_S < 0 || o.factor_S > 1 ||
+        o.factor_S < 0 || o.factor_S > 3 || o.factor_S == ILU_FACT_ILUT ||
+        (o.factor_S == ILU_FACT_PMILU0 && o.variant != ILU_VARIANT_SCHUR) || o.factor_B == ILU_FACT_PMILU0 ||
         (o.pc_precision != ILU_PREC_FP64 && o.pc_precision != ILU_PREC_FP32 && o.pc_precision != ILU_PREC_BF16_STORE) ||
         o.inner_iters < 1 || o.inner_iters > kMaxInner || o.form < 0 || o.form > 2 || o.pivot_eps < 0.0 ||
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||

@@ -24,7 +24,8 @@ struct NumArgs {
     const double* a;      // original values (pattern of A_i)
     double* f;            // factor values, initialised to a
     double eps;
-    int milu;
+    int milu;             // 0: ILU(0); 1: MILU(0); 2: MILU only for interface pivots (pmilu0)
+    const int32_t* nint;  // interior rows per subdomain (milu = 2)
     int32_t* npert;
     int32_t* err;
 };
@@ -47,6 +48,9 @@ __global__ void k_ilu_numeric(NumArgs A) {
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int q0 = A.qoff[s];
+    // pmilu0 (Sec. 3.2, partial ILU): the interior pivots drop plainly, the interface pivots
+    // (the Schur complement's own elimination) compensate the diagonal
+    const int mfrom = (A.milu == 2) ? A.nint[s] : 0;
     for (int e = A.sub_lvl[s]; e < A.sub_lvl[s + 1]; e++) {
         for (int t = A.lvl_ptr[e] + warp; t < A.lvl_ptr[e + 1]; t += nwarp) {
             const int i = A.rows[t];
@@ -71,7 +75,7 @@ __global__ void k_ilu_numeric(NumArgs A) {
                         pos = find_col(A.ci, rb, re, j);
                         if (pos >= 0) A.f[pos] = __dsub_rn(A.f[pos], prod);
                     }
-                    unsigned drop = __ballot_sync(kFull, act && pos < 0);
+                    unsigned drop = __ballot_sync(kFull, act && pos < 0 && k >= mfrom);
                     while (drop) {  // ascending order of u, like the sequential loop
                         const int b = __ffs(drop) - 1;
                         const double v = __shfl_sync(kFull, prod, b);
@@ -115,6 +119,7 @@ cudaError_t launch_ilu_numeric(const Handle& h, double* F, int milu, cudaStream_
     a.f = F;
     a.eps = h.o.pivot_eps;
     a.milu = milu;
+    a.nint = h.d_nint;
     a.npert = h.d_npert;
     a.err = h.d_err;
     cudaError_t e = cudaMemcpyAsync(F, a.a, (size_t)h.q_rp[h.n] * sizeof(double),

@@ -58,6 +58,8 @@ CONFIGS = [
     dict(variant="bj", factor_B="milu0", factor_S="milu0", fill_level=1),
     # l1 block Jacobi (Sec. 4.3)
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", l1_block=True),
+    # MILU(0) of the partial-ILU(0) Schur complement (Sec. 3.2)
+    dict(variant="schur", factor_B="ilu0", factor_S="pmilu0"),
 ]
 
 
@@ -128,7 +130,7 @@ def test_setup_structure_bit_exact(ilu, name, cfg):
 
 @pytest.mark.parametrize("name", list(PROBS))
 @pytest.mark.parametrize("cfg", [CONFIGS[0], CONFIGS[2], CONFIGS[4], CONFIGS[7], CONFIGS[8], CONFIGS[9],
-                                 CONFIGS[10], CONFIGS[11]], ids=_cid)
+                                 CONFIGS[10], CONFIGS[11], CONFIGS[12]], ids=_cid)
 def test_device_factors_bit_exact(ilu, name, cfg):
     pr, h, orc = _pair(ilu, name, cfg, "fp64")
     facts = [1] if cfg["variant"] == "bj" or cfg["factor_B"] == cfg["factor_S"] else [1, 2]
@@ -523,6 +525,7 @@ def test_bad_vectors_are_rejected(ilu):
     ("aniso2d_ragged", CONFIGS[0], "fp64", 100),
     ("poisson64", CONFIGS[0], "fp64", 256),
     ("cuts3d", CONFIGS[11], "fp32", 50),
+    ("aniso2d_ragged", CONFIGS[12], "fp64", 50),
 ])
 @pytest.mark.parametrize("graphs", [True, False])
 def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):

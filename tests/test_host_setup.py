@@ -31,6 +31,7 @@ CFGS = [
     dict(variant="schur", factor_B="ilu0", factor_S="milu0", fill_level=2),
     dict(variant="rap", factor_B="ilu0", factor_S="milu0", fill_level=1, local_order="rcm"),
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", l1_block=True, local_order="rcm"),
+    dict(variant="schur", factor_B="ilu0", factor_S="pmilu0"),
 ]
 
 
