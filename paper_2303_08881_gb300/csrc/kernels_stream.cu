@@ -349,32 +349,49 @@ __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const Rin
     return true;
 }
 
-// Gather / scatter with four independent loads in flight per thread.
+// Gather / scatter / copy with several independent loads in flight per thread (the loads
+// of a subdomain's vector sit on the critical path before its level program starts).
 template <class T>
 __device__ __forceinline__ void gather(T* x, const double* __restrict__ r, const int32_t* __restrict__ idx, int n) {
     const int stride = blockDim.x;
     int l = threadIdx.x;
-    for (; l + 3 * stride < n; l += 4 * stride) {
-        const int i0 = idx[l], i1 = idx[l + stride], i2 = idx[l + 2 * stride], i3 = idx[l + 3 * stride];
-        const double v0 = r[i0], v1 = r[i1], v2 = r[i2], v3 = r[i3];
-        x[l] = (T)v0;
-        x[l + stride] = (T)v1;
-        x[l + 2 * stride] = (T)v2;
-        x[l + 3 * stride] = (T)v3;
+    for (; l + 3 * stride < n; l += 4 * stride) {  // four: the first chunk copies run meanwhile
+        int i[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) i[u] = idx[l + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = r[i[u]];
+#pragma unroll
+        for (int u = 0; u < 4; u++) x[l + u * stride] = (T)v[u];
     }
     for (; l < n; l += stride) x[l] = (T)r[idx[l]];
+}
+
+template <class T>
+__device__ __forceinline__ void copy_in(T* x, const T* __restrict__ src, int n) {
+    const int stride = blockDim.x;
+    int l = threadIdx.x;
+    for (; l + 7 * stride < n; l += 8 * stride) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = src[l + u * stride];
+#pragma unroll
+        for (int u = 0; u < 8; u++) x[l + u * stride] = v[u];
+    }
+    for (; l < n; l += stride) x[l] = src[l];
 }
 
 template <class T>
 __device__ __forceinline__ void scatter(double* __restrict__ z, const T* x, const int32_t* __restrict__ idx, int n) {
     const int stride = blockDim.x;
     int l = threadIdx.x;
-    for (; l + 3 * stride < n; l += 4 * stride) {
-        const int i0 = idx[l], i1 = idx[l + stride], i2 = idx[l + 2 * stride], i3 = idx[l + 3 * stride];
-        z[i0] = (double)x[l];
-        z[i1] = (double)x[l + stride];
-        z[i2] = (double)x[l + 2 * stride];
-        z[i3] = (double)x[l + 3 * stride];
+    for (; l + 7 * stride < n; l += 8 * stride) {
+        int i[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) i[u] = idx[l + u * stride];
+#pragma unroll
+        for (int u = 0; u < 8; u++) z[i[u]] = (double)x[l + u * stride];
     }
     for (; l < n; l += stride) z[idx[l]] = (double)x[l];
 }
@@ -821,11 +838,10 @@ __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCf
     ring_start(S, s, sm, cfg.nst);
     const int steps = (sd.n2 > 0) ? inner_lsq(in.ctl, in.part, sd.p, in.k, tt) : 0;
     T* x = xvec<T, XS>(sm, xg, q0);
-    if (ef) {
-        for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)r[sd.q_orig[q0 + l]];
-    } else {
-        for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = fq[q0 + l];
-    }
+    if (ef)
+        gather(x, r, sd.q_orig + q0, ni);
+    else
+        copy_in(x, fq + q0, ni);
     const int g0 = sd.if_ptr[s];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         T y = (T)0;
