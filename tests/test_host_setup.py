@@ -106,3 +106,51 @@ def test_streamed_programs_are_built(ilu, name, cfg, prec):
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, pc_precision=prec, **cfg))
     assert h.stats()["stream_path"]
     h.close()
+
+
+def _analysis_digest(h):
+    import hashlib
+    m = hashlib.sha256()
+    for k, v in sorted(h.perm().items()):
+        m.update(np.ascontiguousarray(v).tobytes())
+    for prog in ("bj", "fwd", "s", "bwd"):
+        try:
+            st = h.stream(prog)
+        except Exception:
+            continue
+        m.update(st["blob"].tobytes())
+        m.update(st["ch0"].tobytes())
+    for sd in range(h.sizes()["p"]):
+        rp, ci = h.local_pattern(sd)
+        m.update(rp.tobytes())
+        m.update(ci.tobytes())
+    return m.hexdigest()
+
+
+@pytest.mark.parametrize("cfg", [dict(variant="schur"), dict(variant="rap", local_order="rcm", fill_level=1)],
+                         ids=["schur", "rap-rcm-iluk"])
+def test_concurrent_setups_build_the_same_analysis(ilu, cfg):
+    """The host analysis runs its per-subdomain phases on worker threads and divides the
+    threads among setups running at the same time; the result must not depend on the split:
+    four concurrent setups give byte-identical orders, patterns and streams to a lone one."""
+    import threading
+    pr = CASES["aniso2d_ragged"]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **cfg))
+    ref = _analysis_digest(h)
+    h.close()
+    got, errs = [], []
+
+    def one():
+        try:
+            hh = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **cfg))
+            got.append(_analysis_digest(hh))
+            hh.close()
+        except Exception as e:  # reported below
+            errs.append(repr(e))
+
+    ts = [threading.Thread(target=one) for _ in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(120)
+    assert not errs and got == [ref] * 4
