@@ -557,7 +557,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         return s;
     }
     // host copies of the value arrays are no longer needed
-    std::vector<double>().swap(h->q_v);
+    decltype(h->q_v)().swap(h->q_v);
     std::vector<double>().swap(h->f1_host_vals);
     h->setup_ms = now_ms() - t0;
     h->device_ms = h->setup_ms - h->host_ms;

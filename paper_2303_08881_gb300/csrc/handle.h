@@ -90,8 +90,9 @@ struct Handle {
 
     // host products (kept for introspection)
     std::vector<int32_t> part, iface, perm, iperm, int_ptr, if_ptr, qoff, nint, q_orig;
-    std::vector<int32_t> q_rp, q_ci, q_dpos;  // local CSR of every A_s, Q order
-    std::vector<double> q_v;
+    std::vector<int32_t> q_rp, q_dpos;  // local CSR of every A_s, Q order
+    rawvec<int32_t> q_ci;               // (filled by host threads: no zero fill first)
+    rawvec<double> q_v;
     std::vector<int32_t> lev[6];
     int32_t nlev[6] = {0, 0, 0, 0, 0, 0};
     FPat f1, f2;           // patterns of the two factorisations (f2 may equal f1)

@@ -771,7 +771,7 @@ static void rcm_group(const ilu_csr* A, const int32_t* part, int32_t s, std::vec
 // in a sorted singly linked list (head = ns), so fill is inserted in place. Output: local
 // CSR (orp, oci) and, for the values, the position of each kept entry in the input (-1 =
 // fill).
-static void iluk_block(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, int32_t q0, int32_t ns,
+static void iluk_block(const std::vector<int32_t>& rp, const rawvec<int32_t>& ci, int32_t q0, int32_t ns,
                        int k, std::vector<int32_t>& orp, std::vector<int32_t>& oci, std::vector<int64_t>& osrc) {
     const int32_t head = ns;
     std::vector<int32_t> nxt(ns + 1, -1), lev(ns, -1), diag(ns, -1);
@@ -992,8 +992,9 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         int64_t tot = 0;
         for (int32_t s = 0; s < p; s++) tot += (int64_t)bci[s].size();
         if (tot >= (int64_t)INT32_MAX) return ILU_ERR_TOO_LARGE;
-        std::vector<int32_t> rp2(n + 1, 0), ci2;
-        std::vector<double> v2;
+        std::vector<int32_t> rp2(n + 1, 0);
+        rawvec<int32_t> ci2;
+        rawvec<double> v2;
         ci2.reserve(tot);
         v2.reserve(tot);
         for (int32_t s = 0; s < p; s++) {
