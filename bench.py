@@ -3,7 +3,7 @@ GB300 (or N replicas), plus the preconditioner-apply bandwidth, mixed vs FP64, t
 roofline of the dominant kernel, an end-to-end number through the C ABI with host
 buffers, and the FP64 CPU oracle as the baseline.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl ilu2l|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload aniso2d_1024_p64] [--impl ilu2l|reference]
 
 A step is one complete solve: FGMRES from x0 = 0 to ||b - Ax|| <= 1e-8 ||b|| on the
 workload's synthetic right-hand side with the factors resident (the setup is timed
@@ -30,6 +30,9 @@ from paper_2303_08881_gb300 import problems as P  # noqa: E402
 
 METRIC = "GMRES time-to-rtol 1e-8, PC-apply HBM GB/s, mixed vs FP64, p50/p99 latency"
 UNIT = "solves/s"
+# the workload a default run times: the 2D rotated anisotropic 9-point problem on a 1024^2
+# grid in 8 x 8 subdomains, two-level ILU(0)/MILU(0), FP32 preconditioner, FGMRES(50)
+DEFAULT_WORKLOAD = "aniso2d_1024_p64"
 RTOL = 1e-8
 
 
@@ -184,7 +187,7 @@ class ClockSampler:
 
 
 def solver_opts(cfg, prec):
-    sol = dict(P.CONFIG_SOLVER[cfg])
+    sol = dict(P.WORKLOAD_SOLVER[cfg])
     restart = sol.pop("restart")
     sol.pop("prec")
     sol["pc_precision"] = prec
@@ -197,7 +200,7 @@ def cpu_baseline(cfg, sample_cycles=1):
     import oracle as O
     sol, restart = solver_opts(cfg, "fp64")
     sol.pop("pc_precision")
-    pr = P.make_config(cfg)
+    pr = P.make_workload(cfg)
     t0 = time.perf_counter()
     o = O.Oracle.from_problem(pr, **sol)
     t1 = time.perf_counter()
@@ -237,13 +240,13 @@ def run_reference(args):
     import oracle
     oracle.build()
     for _ in range(args.warmup):   # warm-up: the oracle's setup phase on the same workload
-        sol, _ = solver_opts(args.config, "fp64")
+        sol, _ = solver_opts(args.workload, "fp64")
         sol.pop("pc_precision")
-        oracle.Oracle.from_problem(P.make_config(args.config), **sol)
+        oracle.Oracle.from_problem(P.make_workload(args.workload), **sol)
     vals, times = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cb = cpu_baseline(args.config)
+        cb = cpu_baseline(args.workload)
         vals.append(cb["value"])
         times.append(cb["time_to_rtol_s"])
     wall = time.perf_counter() - t0
@@ -252,7 +255,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.config)},
+            "config": {"workload": workload_name(args.workload)},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -260,8 +263,8 @@ def run_reference(args):
 
 
 def workload_name(cfg):
-    pr_spec = dict(P.FULL_CONFIGS[cfg])
-    sol = P.CONFIG_SOLVER[cfg]
+    pr_spec = dict(P.WORKLOADS[cfg])
+    sol = P.WORKLOAD_SOLVER[cfg]
     fn = pr_spec.pop("fn")
     shape = "_".join(f"{k}{v}" for k, v in pr_spec.items())
     return (f"{fn}_{shape}_{sol['variant']}_{sol['factor_B']}+{sol['factor_S']}_"
@@ -290,7 +293,7 @@ def apply_only(args, ilu, h, pr, dev, stream, setup_s, prec, restart, sol):
     byte = by.get("_apply_one") or by.get("apply_bj")
     hbm, kind = _peaks()
     st = h.stats()
-    print(json.dumps({"mode": "apply", "workload": workload_name(args.config), "pc_precision": prec,
+    print(json.dumps({"mode": "apply", "workload": workload_name(args.workload), "pc_precision": prec,
                       "apply_ms": ms, "bytes": byte, "gbs": byte / ms / 1e6, "frac": byte / ms / 1e6 / hbm,
                       "setup_s": setup_s, "stream_path": st["stream_path"], "device_error": st["device_error"],
                       "levels": {k: sz[f"prog_{k}"]["levels"] for k in ("bj", "fwd", "s", "bwd")}}))
@@ -335,7 +338,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="2")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(P.WORKLOADS))
     ap.add_argument("--impl", default="ilu2l", choices=["ilu2l", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -383,14 +386,14 @@ def main():
                               "latency": st}))
         return
 
-    cfg = args.config
-    sol, restart = solver_opts(cfg, args.prec or P.CONFIG_SOLVER[cfg]["prec"])
+    cfg = args.workload
+    sol, restart = solver_opts(cfg, args.prec or P.WORKLOAD_SOLVER[cfg]["prec"])
     if args.variant:
         sol["variant"] = args.variant
         if args.variant == "rap":
             sol.update(factor_B="ilu0", factor_S="milu0")
     prec = sol["pc_precision"]
-    pr = P.make_config(cfg, seed=0)
+    pr = P.make_workload(cfg, seed=0)
     stream = torch.cuda.current_stream()
 
     sol["block_threads"] = args.threads
@@ -546,7 +549,7 @@ def main():
 
     h.close()
     latency = None
-    if rank == 0 and world == 1 and args.serve_requests > 0 and cfg == "2":
+    if rank == 0 and world == 1 and args.serve_requests > 0 and cfg == DEFAULT_WORKLOAD:
         latency = serve_leg(args.serve_requests, args.serve_workers)
     if rank == 0:
         line = {

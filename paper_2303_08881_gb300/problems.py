@@ -296,29 +296,29 @@ def convdiff3d_boxes(side: int, boxes: int, pe: float = 50.0, seed: int = 0) -> 
                     grid=(side,) * 3, pe=pe)
 
 
-#: The five workload families at their full sizes (the suffix "a"/"b" splits the fourth).
-FULL_CONFIGS = {
-    "1": dict(fn="poisson2d_boxes", side=64, boxes=2),
-    "2": dict(fn="aniso2d_boxes", side=1024, boxes=8),
-    "3": dict(fn="aniso3d_cuts", side=128),
-    "4a": dict(fn="randsparse", n=500_000, p=64),
-    "4b": dict(fn="convdiff3d_boxes", side=96, boxes=4),
+#: The named workloads at their full sizes (problem, grid or size, subdomains in the name).
+WORKLOADS = {
+    "poisson2d_64_p4": dict(fn="poisson2d_boxes", side=64, boxes=2),
+    "aniso2d_1024_p64": dict(fn="aniso2d_boxes", side=1024, boxes=8),
+    "aniso3d_cuts_128_p256": dict(fn="aniso3d_cuts", side=128),
+    "randsparse_500k_p64": dict(fn="randsparse", n=500_000, p=64),
+    "convdiff3d_96_p64": dict(fn="convdiff3d_boxes", side=96, boxes=4),
 }
 
 #: Solver options per workload family (variant, factors, precision, restart).
-CONFIG_SOLVER = {
-    "1": dict(variant="bj", factor_B="ilu0", factor_S="ilu0", prec="fp64", restart=30),
-    "2": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
-    "3": dict(variant="schur", factor_B="ilut", factor_S="milu0", prec="fp32", restart=50,
-              ilut_tau=1e-3, ilut_p=10),
-    "4a": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
-    "4b": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
+WORKLOAD_SOLVER = {
+    "poisson2d_64_p4": dict(variant="bj", factor_B="ilu0", factor_S="ilu0", prec="fp64", restart=30),
+    "aniso2d_1024_p64": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
+    "aniso3d_cuts_128_p256": dict(variant="schur", factor_B="ilut", factor_S="milu0", prec="fp32", restart=50,
+                                  ilut_tau=1e-3, ilut_p=10),
+    "randsparse_500k_p64": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
+    "convdiff3d_96_p64": dict(variant="schur", factor_B="ilu0", factor_S="milu0", prec="fp32", restart=50),
 }
 
 
-def make_config(key: str, seed: int = 0, **override) -> Problem:
+def make_workload(key: str, seed: int = 0, **override) -> Problem:
     """Build one of the named workloads; keyword overrides shrink it for tests."""
-    spec = dict(FULL_CONFIGS[key])
+    spec = dict(WORKLOADS[key])
     spec.update(override)
     fn = globals()[spec.pop("fn")]
     return fn(seed=seed, **spec)

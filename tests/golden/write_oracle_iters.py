@@ -2,7 +2,7 @@
 and time-to-solution on the named workloads (calls only oracle/ and the seeded
 generators). The CPU baseline scales a one-cycle oracle sample by this count.
 
-    python tests/golden/write_oracle_iters.py 2 [1 ...]
+    python tests/golden/write_oracle_iters.py aniso2d_1024_p64 [poisson2d_64_p4 ...]
 """
 import json
 import os
@@ -21,10 +21,10 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fgmres_it
 def main(keys):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for k in keys:
-        sol = dict(P.CONFIG_SOLVER[k])
+        sol = dict(P.WORKLOAD_SOLVER[k])
         restart = sol.pop("restart")
         sol.pop("prec")
-        pr = P.make_config(k)
+        pr = P.make_workload(k)
         t0 = time.perf_counter()
         o = O.Oracle.from_problem(pr, **sol)
         t1 = time.perf_counter()
@@ -37,4 +37,4 @@ def main(keys):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["2"])
+    main(sys.argv[1:] or ["aniso2d_1024_p64"])

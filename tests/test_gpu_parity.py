@@ -30,7 +30,7 @@ TOL32 = 2e-4
 
 def _problems():
     return {
-        "poisson64": lambda: P.make_config("1"),
+        "poisson64": lambda: P.make_workload("poisson2d_64_p4"),
         "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
         "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
         "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),

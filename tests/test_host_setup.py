@@ -8,7 +8,7 @@ import oracle as O
 from paper_2303_08881_gb300 import problems as P
 
 CASES = {
-    "poisson64": lambda: P.make_config("1"),
+    "poisson64": lambda: P.make_workload("poisson2d_64_p4"),
     "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
     "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
     "cuts3d": lambda: P.aniso3d_cuts(20, ncuts=(2, 2, 1), seed=3),
@@ -80,7 +80,7 @@ def test_full_size_2d_workload_structure(ilu):
     """1024^2 9-point anisotropic problem on 8x8 boxes: the counts of the interior /
     interface split and the level depth of L_B (natural order: level x + 2y; the corner
     boxes have a 127 x 127 interior, so 126 + 2*126 + 1 levels)."""
-    pr = P.make_config("2")
+    pr = P.make_workload("aniso2d_1024_p64")
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
     s = h.sizes()
     assert (s["n"], s["nnz"], s["n1"], s["n2"], s["nnz_coff"]) == (
@@ -90,7 +90,7 @@ def test_full_size_2d_workload_structure(ilu):
 
 
 def test_analysis_handle_refuses_device_calls(ilu):
-    pr = P.make_config("1")
+    pr = P.make_workload("poisson2d_64_p4")
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
     import ctypes as C
     assert ilu.lib().ilu_apply(h.ptr, C.c_void_p(16), C.c_void_p(32)) == ilu.ILU_ERR_ARG

@@ -311,7 +311,7 @@ def test_structural_counts_of_the_2d_workload():
     """64x64 5-point Poisson on 2x2 boxes: interface = the two grid lines next to each cut
     (each box side has 32 nodes): n2 = 4*2*32 - 4 = 252, n1 = 4096 - 252. Block Jacobi
     factors whole blocks (Sec. 2.1): no interface, no C_off."""
-    pr = P.make_config("1")
+    pr = P.make_workload("poisson2d_64_p4")
     o = O.Oracle.from_problem(pr, variant="schur", factor_B="ilu0", factor_S="milu0")
     s = o.sizes()
     assert (s.n, s.nnz, s.n1, s.n2, s.nnz_coff) == (4096, 20224, 3844, 252, 256)

@@ -17,7 +17,7 @@ import pytest
 from paper_2303_08881_gb300 import problems as P
 
 CASES = {
-    "poisson64": lambda: P.make_config("1"),
+    "poisson64": lambda: P.make_workload("poisson2d_64_p4"),
     "aniso2d_ragged": lambda: P.aniso2d_boxes(70, 3, seed=1),
     "aniso2d_128box": lambda: P.aniso2d_boxes(256, 2, seed=7),
     "conv3d": lambda: P.convdiff3d_boxes(14, 2, seed=2),
