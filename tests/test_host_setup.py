@@ -154,3 +154,31 @@ def test_concurrent_setups_build_the_same_analysis(ilu, cfg):
     for t in ts:
         t.join(120)
     assert not errs and got == [ref] * 4
+
+
+@pytest.mark.parametrize("opts,ok", [
+    (dict(variant="bj", factor_S="pmilu0"), False),            # PMILU0 is an S factor of SCHUR
+    (dict(variant="rap", factor_S="pmilu0"), False),
+    (dict(variant="schur", factor_B="pmilu0"), False),
+    (dict(variant="schur", factor_S="ilut"), False),           # ILUT only for the B factor
+    (dict(variant="rap", factor_B="ilut"), False),
+    (dict(variant="schur", l1_block=True), False),             # l1 augmentation: block Jacobi only
+    (dict(variant="schur", factor_B="ilut", fill_level=1), False),
+    (dict(variant="schur", factor_S="pmilu0", fill_level=1), True),
+    (dict(variant="schur", factor_S="pmilu0", local_order="rcm"), True),
+    (dict(variant="bj", l1_block=True, fill_level=2, local_order="rcm"), True),
+    (dict(variant="rap", fill_level=1, pc_precision="bf16"), True),
+    (dict(variant="schur", factor_B="ilut", pc_precision="bf16"), False),
+    (dict(variant="schur", form="ef", pc_precision="bf16"), False),
+    (dict(variant="schur", kernel_path="generic", pc_precision="bf16"), False),
+    (dict(variant="rap", kernel_path="generic"), False),
+], ids=lambda v: str(v) if isinstance(v, bool) else "-".join(f"{k}={x}" for k, x in v.items()))
+def test_option_combinations(ilu, opts, ok):
+    pr = CASES["aniso2d_ragged"]()
+    if ok:
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **opts))
+        assert h.sizes()["n"] == pr.n
+        h.close()
+    else:
+        with pytest.raises(ilu.IluError):
+            ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **opts))
