@@ -20,8 +20,14 @@
  *   Algorithm "Additive block ILU solve" (Sec. 2.2.2) for the E/F form;
  *   Algorithm "Block Jacobi ILU on GPU" (Sec. 3.1) for block Jacobi;
  *   Sec. 4.1.1  flexible GMRES(m) outside, because the inner GMRES makes M^{-1}
- *               nonlinear.
- * Readings where the paper is silent are stated at each function.
+ *               nonlinear;
+ *   Sec. 3.3    the multiplicative two-level variant (RAP) with R and P from MILU(0);
+ *   Sec. 3.1    RCM order of the local blocks; Sec. 4.2-4.4 ILU(k) by level of fill;
+ *   Sec. 4.3    l1 block Jacobi; Sec. 3.2 MILU(0) of the partial-ILU Schur complement;
+ *               bfloat16 storage of the factors (a precision option, not in the paper).
+ * Readings where the paper is silent are stated at each function. The test
+ * infrastructure pins every function here to facts outside the oracle (the paper's
+ * printed counts, closed forms, library routines, brute force).
  */
 #include "oracle.h"
 
