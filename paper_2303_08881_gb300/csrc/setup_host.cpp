@@ -24,28 +24,6 @@ namespace {
 // ------------------------------------------------------------------------------------
 // validation
 
-ilu_status validate(const ilu_csr* A, const int32_t* part, int32_t p) {
-    if (!A || !part || p < 1 || A->n < 0 || A->nnz < 0) return ILU_ERR_ARG;
-    if (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->val))) return ILU_ERR_ARG;
-    const int32_t n = A->n;
-    if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return ILU_ERR_CSR;
-    for (int32_t i = 0; i < n; i++) {
-        const int32_t b = A->rowptr[i], e = A->rowptr[i + 1];
-        if (e < b) return ILU_ERR_CSR;
-        bool diag = false;
-        for (int32_t q = b; q < e; q++) {
-            const int32_t c = A->colind[q];
-            if (c < 0 || c >= n) return ILU_ERR_CSR;
-            if (q > b && c <= A->colind[q - 1]) return ILU_ERR_CSR;
-            diag |= (c == i);
-        }
-        if (!diag) return ILU_ERR_CSR;
-    }
-    for (int32_t i = 0; i < n; i++)
-        if (part[i] < 0 || part[i] >= p) return ILU_ERR_ARG;
-    return ILU_OK;
-}
-
 // ------------------------------------------------------------------------------------
 // level computation on a window of a factor pattern (rows r0..r1-1 of one subdomain,
 // local numbering, q0 = the subdomain's first Q row).
@@ -158,6 +136,36 @@ void prog_concat(ProgHost& D, const std::vector<const ProgHost*>& fr) {
         D.max_level_rows = std::max(D.max_level_rows, fr[t]->max_level_rows);
         D.max_levels = std::max(D.max_levels, fr[t]->max_levels);
     }
+}
+
+// Input checks (CSR shape, sorted unique columns, stored diagonal, partition range). Rows
+// are checked on host threads; any bad row gives ILU_ERR_CSR, as a sequential scan would,
+// and the partition is checked only when every row is valid.
+ilu_status validate(const ilu_csr* A, const int32_t* part, int32_t p) {
+    if (!A || !part || p < 1 || A->n < 0 || A->nnz < 0) return ILU_ERR_ARG;
+    if (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->val))) return ILU_ERR_ARG;
+    const int32_t n = A->n;
+    if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return ILU_ERR_CSR;
+    std::atomic<int> bad_row{0}, bad_part{0};
+    for_ranges(n, [&](int, int32_t i0, int32_t i1) {
+        for (int32_t i = i0; i < i1; i++) {
+            const int32_t b = A->rowptr[i], e = A->rowptr[i + 1];
+            bool ok = e >= b && e <= A->nnz && b >= 0, diag = false;
+            for (int32_t q = b; ok && q < e; q++) {
+                const int32_t c = A->colind[q];
+                if (c < 0 || c >= n || (q > b && c <= A->colind[q - 1])) ok = false;
+                diag |= (c == i);
+            }
+            if (!ok || !diag) {
+                bad_row.store(1, std::memory_order_relaxed);
+                return;
+            }
+            if (part[i] < 0 || part[i] >= p) bad_part.store(1, std::memory_order_relaxed);
+        }
+    });
+    if (bad_row.load()) return ILU_ERR_CSR;
+    if (bad_part.load()) return ILU_ERR_ARG;
+    return ILU_OK;
 }
 
 void prog_push_row(ProgHost& P, const FPat& F, int32_t q0, int32_t r, int32_t clo, int32_t chi,
@@ -832,14 +840,19 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
     //      or A^T (symmetrised pattern keeps B, E, F block diagonal for any pattern).
     //      Block Jacobi factors each whole A_i (Sec. 2.1): it has no interface.
     h.iface.assign(n, 0);
-    for (int32_t i = 0; i < n && h.variant != ILU_VARIANT_BJ; i++)
-        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
-            const int32_t j = A->colind[q];
-            if (part[j] != part[i]) {
-                h.iface[i] = 1;
-                h.iface[j] = 1;
-            }
-        }
+    if (h.variant != ILU_VARIANT_BJ) {
+        int32_t* iface = h.iface.data();
+        for_ranges(n, [&](int, int32_t i0, int32_t i1) {  // marks may cross ranges: atomic stores
+            for (int32_t i = i0; i < i1; i++)
+                for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+                    const int32_t j = A->colind[q];
+                    if (part[j] != part[i]) {
+                        __atomic_store_n(&iface[i], 1, __ATOMIC_RELAXED);
+                        __atomic_store_n(&iface[j], 1, __ATOMIC_RELAXED);
+                    }
+                }
+        });
+    }
 
     // ---- interior-first relabelling (Eq. equ22)
     h.int_ptr.assign(p + 1, 0);
