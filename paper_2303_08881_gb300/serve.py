@@ -170,6 +170,7 @@ class Record:
     host_ms: float = 0.0     # the handle's host analysis, device setup and graph build (library clocks)
     device_ms: float = 0.0
     graph_ms: float = 0.0
+    x: object = None         # the solution (host numpy) when serve(keep_solutions=True)
 
 
 @dataclass
@@ -185,7 +186,8 @@ class Report:
 
 
 def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int = 50, rtol: float = 1e-8,
-          maxit: int = 5000, opts: dict | None = None, check_residual: bool = True) -> Report:
+          maxit: int = 5000, opts: dict | None = None, check_residual: bool = True,
+          keep_solutions: bool = False) -> Report:
     """Run the requests (sorted by arrival) in real time and return per-request records."""
     import torch
     import paper_2303_08881_gb300 as ilu
@@ -242,6 +244,8 @@ def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int =
                 rec.done = now()
                 rec.solve_s = time.perf_counter() - ts
                 rec.iters, rec.status = info["iters"], info["status"]
+                if keep_solutions:
+                    rec.x = xs
                 rec.device_bytes = h.stats()["device_bytes"]
                 tm = h.times()
                 if not rec.reused:
