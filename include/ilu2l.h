@@ -94,7 +94,8 @@ typedef struct {
     int32_t use_graphs;   /* capture one FGMRES cycle as a CUDA graph (1) or launch (0) */
     int32_t block_threads;/* threads per CTA of the per-subdomain kernels (0 = autotune) */
     int32_t analysis_only;/* 1: host analysis only (no device memory, no factorisation);
-                             only ilu_get_sizes / _perm / _levels and ilu_free are valid */
+                             only ilu_get_sizes / _perm / _levels / _local_pattern /
+                             _stream / _stream_stats / _times and ilu_free are valid */
     int32_t kernel_path;  /* 0: level programs streamed into shared memory by TMA (falls
                              back to 1 when a row does not fit a chunk);
                              1: generic level kernels reading the programs from global memory */
@@ -114,7 +115,7 @@ typedef struct {
 } ilu_opts;
 
 typedef struct {
-    int32_t iters;        /* Arnoldi steps over all cycles (hypre's counting) */
+    int32_t iters;        /* Arnoldi steps over all cycles (the count the paper reports) */
     int32_t restarts;     /* completed cycles */
     double rel_res_true;  /* ||b - A x||_2 / ||b||_2 computed in FP64 at the end */
     double rel_res_est;   /* last Givens residual estimate / ||b|| */
@@ -132,13 +133,16 @@ void ilu_opts_default(ilu_opts* opts);
    GPU", Setup). A: host CSR; part: host int32[n] with values in [0, p); p >= 1.
    Host side: validation, interior/interface classification (a node is interface if a
    stored a_ij or a_ji couples it to another subdomain), interior-first permutation
-   (interior grouped by subdomain, then interface grouped by subdomain, ascending
-   original index inside each group), local blocks A_i = [B_i F_i; E_i C_i], level sets.
-   Device side: ILU(0)/MILU(0) numeric factorisation of every A_i (ILUT is computed on
-   the host), factor extraction and packing. The library copies A and part; on success
+   (interior grouped by subdomain, then interface grouped by subdomain; block Jacobi has
+   no interface, each subdomain is one group; inside a group the order opts.ordering
+   gives), local blocks A_i = [B_i F_i; E_i C_i] (in their level-k pattern with
+   fill_level k), level sets, the level programs. Device side: ILU(0)/MILU(0) numeric
+   factorisation of every A_i (ILUT is computed on the host), factor extraction and
+   packing. ILU_ERR_UNSUPPORTED for option combinations only the streamed path covers
+   when it cannot be used (RAP, bfloat16 storage). The library copies A and part; on success
    *h owns all device memory until ilu_free. Errors: ILU_ERR_CSR, ILU_ERR_ARG,
    ILU_ERR_TOO_LARGE, ILU_ERR_OOM, ILU_ERR_ZERO_PIVOT (only with pivot_eps = 0),
-   ILU_ERR_CUDA. On error *h is NULL. Synchronises the stream before returning. */
+   ILU_ERR_UNSUPPORTED, ILU_ERR_CUDA. On error *h is NULL. Synchronises the stream before returning. */
 ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu_opts* opts,
                      void** h);
 
