@@ -196,10 +196,11 @@ ilu_status ilu_get_perm(void* h, int32_t* perm, int32_t* iperm, int32_t* int_ptr
    Level: 0 without dependencies, else 1 + max level of the rows it depends on. */
 ilu_status ilu_get_levels(void* h, int32_t which, int32_t* lev, int32_t* nlev);
 
-/* Combined L\U values (host double[nnz(A_s)]) of the device factorisation of local
-   block s in the local CSR pattern (local order: interior then interface, ascending
-   original index): fact = 1 the factor giving L_B, U_B, W, Z; fact = 2 the one giving
-   L_S, U_S. ILU_ERR_ARG if that factor does not have the pattern of A_s (ILUT). */
+/* Combined L\U values (host double[nnz of the stored block]) of the device factorisation
+   of local block s in the pattern ilu_get_local_pattern returns (local order: the
+   subdomain's groups as ilu_setup describes; the level-k pattern with fill_level k):
+   fact = 1 the factor giving L_B, U_B, W, Z (block Jacobi: L_A, U_A); fact = 2 the one
+   giving L_S, U_S. ILU_ERR_ARG if that factor does not have the stored pattern (ILUT). */
 ilu_status ilu_get_local_factor(void* h, int32_t s, int32_t fact, double* val);
 
 /* Pattern of local block s as stored for the factorisation (A_s in the local order; with
