@@ -182,3 +182,45 @@ def test_option_combinations(ilu, opts, ok):
     else:
         with pytest.raises(ilu.IluError):
             ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, **opts))
+
+
+def _corrupt(kind, r, n, rp, ci, part, p):
+    rp, ci, part = rp.copy(), ci.copy(), part.copy()
+    b, e = int(rp[r]), int(rp[r + 1])
+    if kind == "unsorted":
+        ci[b], ci[b + 1] = ci[b + 1], ci[b]
+    elif kind == "duplicate":
+        ci[b + 1] = ci[b]
+    elif kind == "out_of_range":
+        ci[e - 1] = n
+    elif kind == "negative":
+        ci[b] = -1
+    elif kind == "no_diagonal":
+        d = b + int(np.nonzero(ci[b:e] == r)[0][0])
+        ci = np.delete(ci, d)
+        rp[r + 1:] -= 1
+    elif kind == "part":
+        part[r] = p
+    elif kind == "row_and_part":
+        ci[b], ci[b + 1] = ci[b + 1], ci[b]
+        part[(r + n // 3) % n] = -1
+    return rp, ci, part
+
+
+@pytest.mark.parametrize("where", ["first", "middle", "last"])
+@pytest.mark.parametrize("kind,status", [("unsorted", "ILU_ERR_CSR"), ("duplicate", "ILU_ERR_CSR"),
+                                         ("out_of_range", "ILU_ERR_CSR"), ("negative", "ILU_ERR_CSR"),
+                                         ("no_diagonal", "ILU_ERR_CSR"), ("part", "ILU_ERR_ARG"),
+                                         ("row_and_part", "ILU_ERR_CSR")])
+def test_input_checks_find_every_bad_row(ilu, kind, status, where):
+    """The input checks run on host threads over row ranges: a bad row or partition entry
+    anywhere gives the same status a sequential scan would (a bad row wins over a bad
+    partition entry)."""
+    pr = P.poisson2d_boxes(40, 2)
+    n = pr.n
+    r = {"first": 0, "middle": n // 2, "last": n - 1}[where]
+    rp, ci, part = _corrupt(kind, r, n, pr.rowptr, pr.colind, pr.part, pr.p)
+    val = np.ones(ci.size)
+    with pytest.raises(ilu.IluError) as ei:
+        ilu.ilu_setup(n, rp, ci, val, part, pr.p, ilu.Opts(analysis_only=True))
+    assert ei.value.status == getattr(ilu, status)
