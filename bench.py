@@ -55,14 +55,32 @@ def prog_bytes(prog, sv, svv=None):
     return prog["entries"] * (4 + svv) + prog["rows"] * (8 + sv) + prog["levels"] * 4
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over every
-# launch of the timed solve) from the ncu capture summarised in
-# profiles/k_fg_cgs_dram_aniso2d_1024_p64.md; valid for that workload and for the kernel as
-# captured there (set to None when the kernel changes)
+# DRAM bytes per launch of a kernel (dram__bytes_read.sum + dram__bytes_write.sum averaged
+# over every launch of one timed solve, from an ncu capture) on one workload. Each record
+# names the SHA-256 prefix of the kernel's source file at capture time: when the file has
+# changed since, the record no longer describes the kernel and the line reports no traffic.
 MEASURED_TRAFFIC = {
-    ("aniso2d_boxes_side1024_boxes8_schur_ilu0+milu0_fp32pc_fgmres50_rtol1e-8", "schur", "ilu0+milu0", "fp32",
-     "fg_cgs"): 409.0e6,
+    ("aniso2d_boxes_side1024_boxes8_schur_ilu0+milu0_fp32pc_fgmres50_rtol1e-8", "fg_cgs"):
+        dict(bytes=409.0e6, source="kernels_krylov.cu", sha256="bbf9f1b05a654afc"),
 }
+
+
+def source_sha(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2303_08881_gb300", "csrc", name)
+    try:
+        return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def measured_traffic(workload, kernel):
+    rec = MEASURED_TRAFFIC.get((workload, kernel))
+    if rec is None:
+        return None, "no ncu capture of this kernel on this workload"
+    if source_sha(rec["source"]) != rec["sha256"]:
+        return None, f"{rec['source']} changed since the ncu capture"
+    return rec["bytes"], "ncu capture of this source (sha256 prefix " + rec["sha256"] + ")"
 
 
 def class_bytes(sz, prec, iters, m, k):
@@ -101,9 +119,11 @@ def class_bytes(sz, prec, iters, m, k):
     return b
 
 
-# FP64 arithmetic of the outer FGMRES kernels (flops = 2 per multiply-add). GB300 runs
-# FP64 at 2 fused multiply-adds per SM per clock: 152 SMs x 2 x 2 flops x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 arithmetic of the outer FGMRES kernels (flops = 2 per multiply-add). The FP64 peak
+# they are compared with is measured on the run's GPU (ilu_measure_fp64_peak); the nominal
+# figure, 2 fused multiply-adds per SM per clock (152 SMs x 2 x 2 flops x 2.07 GHz), is
+# only the fallback when the probe fails.
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def class_flops64(sz, iters, m):
@@ -194,25 +214,63 @@ def solver_opts(cfg, prec):
     return sol, restart
 
 
-def cpu_baseline(cfg, sample_cycles=1):
-    """The FP64 oracle, single-threaded: setup + `sample_cycles` FGMRES cycles, scaled to
-    the oracle's own iteration count on this workload (tests/golden)."""
+def host_info():
+    """The host's CPU count and model, recorded beside every oracle time."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_core():
+    """The CPU the oracle is pinned to: the last one this process may run on."""
+    return max(os.sched_getaffinity(0))
+
+
+def oracle_leg(cfg, cycles_warmup=0):
+    """Runs in a child process pinned to one CPU: oracle setup, then one complete FP64
+    FGMRES solve from x0 = 0 to rtol 1e-8 (factors resident). Prints one JSON line."""
     import oracle as O
+    core = oracle_core()
+    os.sched_setaffinity(0, {core})
     sol, restart = solver_opts(cfg, "fp64")
     sol.pop("pc_precision")
     pr = P.make_workload(cfg)
     t0 = time.perf_counter()
     o = O.Oracle.from_problem(pr, **sol)
     t1 = time.perf_counter()
-    out = o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=restart * sample_cycles)
+    for _ in range(cycles_warmup):
+        o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=restart)
     t2 = time.perf_counter()
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_fgmres_iters.json")))
-    iters = gold[cfg]["iters"]
-    est = (t1 - t0) + (t2 - t1) * iters / max(out["iters"], 1)
-    return dict(value=1.0 / est, unit=UNIT, cores=1, kind="oracle",
-                sample=(f"oracle setup + {out['iters']} FGMRES({restart}) steps of {pr.name} "
-                        f"({t2 - t1:.2f} s), scaled to the oracle's {iters} steps to rtol 1e-8"),
-                time_to_rtol_s=est, setup_s=t1 - t0, iters=iters)
+    out = o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=20000)
+    t3 = time.perf_counter()
+    print(json.dumps({"setup_s": t1 - t0, "solve_s": t3 - t2, "iters": out["iters"], "relres": out["relres"],
+                      "status": out["status"], "core": core, "name": pr.name}))
+
+
+def cpu_baseline(cfg):
+    """The FP64 oracle as it stands, on one pinned host CPU: setup, then one complete
+    FGMRES solve to rtol 1e-8 (no extrapolation)."""
+    import oracle
+    oracle.build()
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", cfg],
+                       capture_output=True, text=True, timeout=3600)
+    if p.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + p.stderr[-2000:])
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    hi = host_info()
+    return dict(value=1.0 / r["solve_s"], unit=UNIT, cores=1, kind="oracle",
+                sample=(f"one complete FP64 oracle FGMRES solve of {r['name']} to rtol 1e-8 "
+                        f"({r['iters']} Arnoldi steps, {r['solve_s']:.1f} s; factors resident, setup "
+                        f"{r['setup_s']:.2f} s timed apart), pinned to CPU {r['core']} with sched_setaffinity"),
+                time_to_rtol_s=r["solve_s"], setup_s=r["setup_s"], iters=r["iters"], rel_res=r["relres"],
+                pinned_cpu=r["core"], **hi)
 
 
 def max_over_ranks(v, world, device):
@@ -234,32 +292,67 @@ def replica_value(t_ms_local, steps, world, device):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, pinned to one host CPU. Every step
+    is one complete FGMRES solve to rtol 1e-8 with the oracle's factors resident (as the
+    GPU arm's steps are); a warm-up step runs one FGMRES cycle."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    for _ in range(args.warmup):   # warm-up: the oracle's setup phase on the same workload
-        sol, _ = solver_opts(args.workload, "fp64")
-        sol.pop("pc_precision")
-        oracle.Oracle.from_problem(P.make_workload(args.workload), **sol)
-    vals, times = [], []
+    core = oracle_core()
+    os.sched_setaffinity(0, {core})
+    cfg = args.workload
+    sol, restart = solver_opts(cfg, "fp64")
+    sol.pop("pc_precision")
+    pr = P.make_workload(cfg)
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_problem(pr, **sol)
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=restart)
+    times, iters = [], None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cb = cpu_baseline(args.workload)
-        vals.append(cb["value"])
-        times.append(cb["time_to_rtol_s"])
+        t1 = time.perf_counter()
+        out = o.fgmres(pr.b, rtol=RTOL, restart=restart, maxit=20000)
+        times.append(time.perf_counter() - t1)
+        iters = out["iters"]
     wall = time.perf_counter() - t0
-    v = statistics.mean(vals)
-    cb["value"] = v
+    v = args.steps / sum(times)
+    hi = host_info()
+    cb = dict(value=v, unit=UNIT, cores=1, kind="oracle",
+              sample=(f"{args.steps} complete FP64 oracle FGMRES solves of {pr.name} to rtol 1e-8 "
+                      f"({iters} Arnoldi steps each; factors resident, setup {setup_s:.2f} s before the clock), "
+                      f"pinned to CPU {core} with sched_setaffinity"),
+              time_to_rtol_s=sum(times) / len(times), setup_s=setup_s, iters=iters, pinned_cpu=core, **hi)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.workload)},
+            "config": bench_config(cfg, sol_for_config(cfg, args), pr, args.gpus),
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "wall_s": wall, "rel_res": out["relres"]}
     print(json.dumps(line))
+
+
+def sol_for_config(cfg, args):
+    """The GPU arm's solver options (what its `config` describes)."""
+    sol, restart = solver_opts(cfg, args.prec or P.WORKLOAD_SOLVER[cfg]["prec"])
+    if args.variant:
+        sol["variant"] = args.variant
+        if args.variant == "rap":
+            sol.update(factor_B="ilu0", factor_S="milu0")
+    sol["restart"] = restart
+    return sol
+
+
+def bench_config(cfg, sol, pr, world):
+    return {"workload": workload_name(cfg), "variant": sol["variant"],
+            "factors": f"{sol['factor_B']}+{sol['factor_S']}", "n": pr.n, "nnz": pr.nnz, "p": pr.p,
+            "restart": sol["restart"], "rtol": RTOL, "pc_precision": sol["pc_precision"],
+            "parallelism": f"replicas{world}",
+            "l2": "working set larger than L2 (FGMRES basis alone 0.8 GB)"}
 
 
 def workload_name(cfg):
@@ -298,6 +391,27 @@ def apply_only(args, ilu, h, pr, dev, stream, setup_s, prec, restart, sol):
                       "setup_s": setup_s, "stream_path": st["stream_path"], "device_error": st["device_error"],
                       "levels": {k: sz[f"prog_{k}"]["levels"] for k in ("bj", "fwd", "s", "bwd")}}))
     h.close()
+
+
+def latency_floor(ilu, h, stream, k_inner):
+    """The least time the apply's dependent steps can take on this GPU, in SM cycles: every
+    group barrier of the longest subdomain program of each streamed kernel (forward, k
+    inner steps of the local Schur program, backward; or block Jacobi) costs at least one
+    dependent level, whose latency for that consumer-group size is measured here
+    (ilu_measure_level_latency)."""
+    if not h.stats()["stream_path"]:
+        return None
+    parts = [("bj", 1)] if h.stream_stats("bj")["threads"] else [("fwd", 1), ("s", k_inner), ("bwd", 1)]
+    cyc_of, out, total = {}, {}, 0.0
+    for prog, mult in parts:
+        st = h.stream_stats(prog)
+        nt = st["threads"]
+        if nt not in cyc_of:
+            cyc_of[nt] = ilu.measure_level_latency(nt, stream.cuda_stream)
+        c = mult * st["max_barriers"] * cyc_of[nt]
+        out[prog] = {"barriers": st["max_barriers"], "times": mult, "threads": nt, "cycles_per_level": cyc_of[nt]}
+        total += c
+    return {"cycles": total, "programs": out}
 
 
 def serve_leg(n_requests, workers):
@@ -354,7 +468,10 @@ def main():
                     help="preconditioner precision (bf16: bfloat16 factor values, FP32 arithmetic)")
     ap.add_argument("--threads", type=int, default=0, help="consumer-group threads override (0 = auto)")
     ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_leg:
+        return oracle_leg(args.oracle_leg)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -456,6 +573,13 @@ def main():
                 "frac": apply_bytes / apply_ms / 1e6 / hbm, "peak_gbs": hbm, "peak_kind": peak_kind,
                 "levels": {k: sz[f"prog_{k}"]["levels"] for k in ("bj", "fwd", "s", "bwd")}}
 
+    # ---- measured denominators: FP64 FMA rate and the latency of one dependent level
+    try:
+        fp64_peak, fp64_kind = ilu.measure_fp64_peak(stream.cuda_stream), "measured: ilu_measure_fp64_peak on this GPU"
+    except Exception:
+        fp64_peak, fp64_kind = FP64_NOMINAL_TFLOPS, "nominal: 2 FP64 FMA/SM/clock x 152 SMs x 2.07 GHz"
+    floor = latency_floor(ilu, h, stream, k_inner)
+
     # ---- profiled solve: per kernel class device time (events on the launching stream)
     h.profile(True)
     pinfo = solve(h)
@@ -471,9 +595,9 @@ def main():
         c = {"ms": ms, "launches": nl, "avg_us": 1000.0 * ms / nl, "gbs": (by / ms / 1e6) if by else None}
         # the binding roofline: the larger of bytes / HBM peak and FP64 flops / FP64 peak
         t_hbm = by / (hbm * 1e9) if by else 0.0
-        t_alu = fl / (FP64_PEAK_TFLOPS * 1e12) if fl else 0.0
+        t_alu = fl / (fp64_peak * 1e12) if fl else 0.0
         if t_alu > t_hbm:
-            c.update(bound="alu", achieved=fl / ms / 1e9, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", arith="f64")
+            c.update(bound="alu", achieved=fl / ms / 1e9, peak=fp64_peak, unit="TFLOP/s", arith="f64")
         else:
             c.update(bound="hbm", achieved=c["gbs"], peak=hbm, unit="GB/s")
         c["frac"] = (c["achieved"] / c["peak"]) if c["achieved"] else None
@@ -481,19 +605,26 @@ def main():
     dom = max(classes, key=lambda k: classes[k]["ms"])
     total_prof = sum(c["ms"] for c in classes.values())
     d = classes[dom]
-    traffic = MEASURED_TRAFFIC.get((workload_name(cfg), sol["variant"], f'{sol["factor_B"]}+{sol["factor_S"]}',
-                                    prec, dom))
+    traffic, traffic_src = measured_traffic(workload_name(cfg), dom)
     alg_bytes = cbytes.get(dom) / d["launches"] if cbytes.get(dom) else None
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu, see profiles/)",
+                "traffic_unit": "DRAM bytes per launch", "traffic_source": traffic_src,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "traffic_per_algorithmic": (traffic / alg_bytes) if (traffic and alg_bytes) else None,
                 "arith": d.get("arith"),
                 "share": d["ms"] / total_prof,
-                "peak_kind": "derived: 2 FP64 FMA/SM/clock x 152 SMs x 2.07 GHz" if d["bound"] == "alu"
-                else peak_kind,
+                "peak_kind": fp64_kind if d["bound"] == "alu" else peak_kind,
                 "avg_launch_us": d["avg_us"], "launches": d["launches"]}
+    # the preconditioner apply (the method's hot path) against HBM and against the floor its
+    # dependent levels set
+    clk_mhz = 2070.0
+    roofline_pc = {"kernel": "pc_apply (forward + inner + backward)", "bound": "hbm", "achieved": pc_apply["gbs"],
+                   "peak": hbm, "unit": "GB/s", "frac": pc_apply["frac"], "peak_kind": peak_kind,
+                   "algorithmic_bytes": apply_bytes, "apply_us": 1000.0 * apply_ms,
+                   "latency_floor_us": floor["cycles"] / clk_mhz if floor else None,
+                   "frac_of_latency_floor": (floor["cycles"] / clk_mhz) / (1000.0 * apply_ms) if floor else None,
+                   "latency_floor": floor}
 
     # ---- mixed vs FP64 (same workload, FP64 preconditioner)
     mixed = None
@@ -556,16 +687,20 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "variant": sol["variant"],
-                       "factors": f"{sol['factor_B']}+{sol['factor_S']}", "n": pr.n, "nnz": pr.nnz, "p": pr.p,
-                       "restart": restart, "rtol": RTOL, "pc_precision": prec, "parallelism": f"replicas{world}",
-                       "l2": "working set larger than L2 (FGMRES basis alone 0.8 GB)"},
+            "config": bench_config(cfg, dict(sol, restart=restart), pr, world),
+            "roofline": roofline, "roofline_pc_apply": roofline_pc,
             "time_to_rtol_s": time_to_rtol, "iters": info["iters"], "rel_res_true": relres,
-            "err_vs_x_true": err_true, "setup_s": setup_s,
-            "pc_apply": pc_apply, "roofline": roofline, "kernels": classes, "mixed_vs_fp64": mixed,
+            "err_vs_x_true": err_true, "setup_s": setup_s, "fp64_peak_tflops": fp64_peak,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
-            "clocks": clk.summary(), "latency": latency,
+            "clocks": clk.summary(), "mixed_vs_fp64": mixed, "pc_apply": pc_apply, "latency": latency,
+            "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in c.items()}
+                        for k, c in classes.items()},
         }
+        if line["clocks"] and line["clocks"].get("sm_mhz"):
+            clk_mhz = line["clocks"]["sm_mhz"]
+            if floor:
+                roofline_pc["latency_floor_us"] = floor["cycles"] / clk_mhz
+                roofline_pc["frac_of_latency_floor"] = roofline_pc["latency_floor_us"] / (1000.0 * apply_ms)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -254,8 +254,11 @@ ilu_status ilu_get_times(void* h, double* out);
    would need), out[8] = bytes of the shared-memory ring the chunks stream through,
    out[9] = 1 when every subdomain's working vector fits in shared memory beside the ring
    (else the kernels keep it in a global scratch vector; known once the device setup ran,
-   0 for analysis-only handles). A program the handle does not use reports zeros. out
-   must hold 10 values.
+   0 for analysis-only handles), out[10] = scan waves (chains solved 32 rows per warp and
+   wave, stream_layout.h) of the subdomain program with most, out[11] = group barriers plus
+   scan waves, largest over the subdomain programs (its dependent steps), out[12] =
+   subdomains whose chain section (the interface rows) runs as chains rather than levels.
+   A program the handle does not use reports zeros. out must hold 13 values.
    Host-side only: needs no device. Errors: ILU_ERR_ARG for a null pointer or a program
    outside 0..3. */
 ilu_status ilu_get_stream_stats(void* h, int32_t program, int64_t* out);
@@ -271,19 +274,40 @@ ilu_status ilu_get_stream_stats(void* h, int32_t program, int64_t* out);
 ilu_status ilu_get_stream(void* h, int32_t program, uint8_t* blob, int32_t* ch0, int64_t* meta);
 
 /* ---------------------------------------------------------------------------------
+ * Measurement probes (no counterpart in the paper): the denominators the benchmark
+ * reports its rooflines against, measured on the current device. Each allocates a few
+ * bytes of scratch on `stream` (a cudaStream_t, NULL = legacy stream), synchronises it
+ * and frees them. Errors: ILU_ERR_ARG, ILU_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+
+/* FP64 fused multiply-add throughput: a grid of 8 CTAs of 256 threads per SM, every thread
+   running eight independent FMA chains of 2^14 steps, timed with CUDA events after a
+   warm-up launch. *tflops = 2 * FMAs / time / 1e12. */
+ilu_status ilu_measure_fp64_peak(void* stream, double* tflops);
+
+/* Latency of one dependent level: one CTA of `threads` threads (32..256, a multiple of
+   32) runs 4096 levels; in each, every thread reads four values other threads stored in
+   the previous level, stores their weighted sum, and the group meets at a barrier
+   (bar.sync on the group; __syncwarp for one warp). *cycles_per_level = SM clock cycles
+   (clock64) per level: the floor of a level of a level-scheduled triangular solve
+   (Sec. 3.1) on this GPU. */
+ilu_status ilu_measure_level_latency(void* stream, int32_t threads, double* cycles_per_level);
+
+/* ---------------------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  * --------------------------------------------------------------------------------- */
 
 /* The inner Schur solve of ilu_inner_solve, for callers that cannot allocate device
-   memory at call time: code that records the call into a CUDA graph, runs on a fixed
-   memory budget, or must not trigger the implicit synchronisation of an allocation.
+   memory at call time: code that runs on a fixed device-memory budget set aside up front,
+   or that must not trigger the implicit synchronisation an allocation can bring.
    Identical inputs, outputs and arithmetic (gp, y: DEVICE double[n2], interface
    numbering), but the Krylov workspace lives in a fixed 8 MiB device array the library
    holds on every GPU that loads it, until the process exits; the call allocates nothing.
-   The first call on a device looks up the array's device address (do it before any
-   stream capture); later calls reuse it. Every call shares the array and clears its
-   control block first; calls that overlap on the GPU (other streams or host threads)
-   race on it. Needs the default streamed kernels with every subdomain's working vector
+   The first call on a device looks up the array's device address (make that first call
+   before any stream capture); later calls reuse it, so a cudaDeviceReset after it is not
+   supported. Every call shares the array, which keeps the last call's contents; each call
+   re-initialises the control state it reads. Calls that overlap on the GPU (other streams
+   or host threads) race on it. Needs the default streamed kernels with every subdomain's working vector
    in shared memory (else ILU_ERR_UNSUPPORTED). ILU_ERR_TOO_LARGE when the workspace,
    256-byte aligned pieces of (inner_iters + 4) * n2 vector elements of the
    preconditioner type, 792 * p bytes of partial sums and a 9 KB control block, exceeds

@@ -88,6 +88,8 @@ def lib():
             "ilu_get_times": (I, [P, P]),
             "ilu_get_stream": (I, [P, I, P, P, P]),
             "ilu_inner_solve_noalloc": (I, [P, P, P]),
+            "ilu_measure_fp64_peak": (I, [P, P]),
+            "ilu_measure_level_latency": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -104,11 +106,17 @@ def status_str(s: int) -> str:
         return "unknown"
 
 
-def _ptr(t):
-    """device pointer of a contiguous torch CUDA float64 tensor"""
+def _ptr(t, n=None, device=None):
+    """device pointer of a contiguous torch CUDA float64 tensor; with n, its length must be
+    n, and with device (a CUDA ordinal), it must live on that device (the kernels read and
+    write exactly n elements on the handle's device)"""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"tensor on cuda:{t.device.index}, the handle on cuda:{device}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -178,6 +186,11 @@ class Handle:
         self.n = n
         self.p = p
         self.opts = opts
+        self.device = None  # the CUDA ordinal current at setup (None: analysis only / no GPU)
+        if not opts.analysis_only:
+            import torch
+            if torch.cuda.is_available():
+                self.device = torch.cuda.current_device()
 
     @property
     def ptr(self):
@@ -246,10 +259,12 @@ class Handle:
         return v
 
     def spmv(self, x, y):
-        _check(lib().ilu_spmv(self.ptr, _ptr(x), _ptr(y)), "ilu_spmv")
+        _check(lib().ilu_spmv(self.ptr, _ptr(x, self.n, self.device), _ptr(y, self.n, self.device)), "ilu_spmv")
 
     def inner_solve(self, gp, y):
-        _check(lib().ilu_inner_solve(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve")
+        n2 = self.sizes()["n2"]
+        _check(lib().ilu_inner_solve(self.ptr, _ptr(gp, n2, self.device), _ptr(y, n2, self.device)),
+               "ilu_inner_solve")
 
     def stats(self) -> dict:
         out = np.zeros(16, np.int64)
@@ -271,13 +286,14 @@ class Handle:
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,
         consumer threads, chunks, waves, records, skip records, group barriers of the
-        longest subdomain program, levels of the deepest one, ring bytes and whether the
-        working vectors stay in shared memory."""
-        out = np.zeros(10, np.int64)
+        longest subdomain program, levels of the deepest one, ring bytes, whether the
+        working vectors stay in shared memory, scan waves, dependent steps (barriers + scan
+        waves) and the subdomains whose interface rows run as chains."""
+        out = np.zeros(13, np.int64)
         idx = ["bj", "fwd", "s", "bwd"].index(program)
         _check(lib().ilu_get_stream_stats(self.ptr, idx, out.ctypes.data_as(C.c_void_p)), "ilu_get_stream_stats")
         keys = ["record_entries", "threads", "chunks", "waves", "records", "skips", "max_barriers", "max_levels",
-                "ring_bytes", "vector_in_shared"]
+                "ring_bytes", "vector_in_shared", "max_scan_waves", "max_steps", "chain_sections"]
         return {k: int(v) for k, v in zip(keys, out)}
 
     def stream(self, program: str) -> dict:
@@ -296,7 +312,9 @@ class Handle:
     def inner_solve_noalloc(self, gp, y):
         """ilu_inner_solve with the library's fixed workspace instead of the handle's
         (allocates nothing; see include/ilu2l.h)."""
-        _check(lib().ilu_inner_solve_noalloc(self.ptr, _ptr(gp), _ptr(y)), "ilu_inner_solve_noalloc")
+        n2 = self.sizes()["n2"]
+        _check(lib().ilu_inner_solve_noalloc(self.ptr, _ptr(gp, n2, self.device), _ptr(y, n2, self.device)),
+               "ilu_inner_solve_noalloc")
 
     def profile(self, enable: bool):
         _check(lib().ilu_profile(self.ptr, int(enable)), "ilu_profile")
@@ -343,14 +361,14 @@ def ilu_setup_problem(prob, opts: Opts | None = None) -> Handle:
 
 def ilu_apply(h: Handle, r, z) -> None:
     """z = M^{-1} r for torch CUDA float64 vectors in the original ordering."""
-    _check(lib().ilu_apply(h.ptr, _ptr(r), _ptr(z)), "ilu_apply")
+    _check(lib().ilu_apply(h.ptr, _ptr(r, h.n, h.device), _ptr(z, h.n, h.device)), "ilu_apply")
 
 
 def gmres_solve(h: Handle, b, x, rtol: float = 1e-8, restart: int = 50, maxit: int = 10000,
                 raise_on_fail: bool = False) -> dict:
     """FGMRES(restart) for A x = b; x (torch CUDA float64) holds x0 on entry."""
     info = ilu_solve_info()
-    st = lib().gmres_solve(h.ptr, _ptr(b), _ptr(x), float(rtol), int(restart), int(maxit), C.byref(info))
+    st = lib().gmres_solve(h.ptr, _ptr(b, h.n, h.device), _ptr(x, h.n, h.device), float(rtol), int(restart), int(maxit), C.byref(info))
     if st not in (ILU_OK, ILU_ERR_NOT_CONVERGED) or (raise_on_fail and st != ILU_OK):
         raise IluError(st, "gmres_solve")
     return dict(status=int(st), iters=info.iters, restarts=info.restarts,
@@ -360,6 +378,22 @@ def gmres_solve(h: Handle, b, x, rtol: float = 1e-8, restart: int = 50, maxit: i
 
 def ilu_free(h: Handle) -> None:
     h.close()
+
+
+def measure_fp64_peak(stream=None) -> float:
+    """FP64 FMA throughput of the current device in TFLOP/s (ilu_measure_fp64_peak)."""
+    v = C.c_double(0.0)
+    _check(lib().ilu_measure_fp64_peak(C.c_void_p(int(stream) if stream else 0), C.byref(v)),
+           "ilu_measure_fp64_peak")
+    return v.value
+
+
+def measure_level_latency(threads: int, stream=None) -> float:
+    """SM clock cycles of one dependent level of `threads` threads (ilu_measure_level_latency)."""
+    v = C.c_double(0.0)
+    _check(lib().ilu_measure_level_latency(C.c_void_p(int(stream) if stream else 0), int(threads), C.byref(v)),
+           "ilu_measure_level_latency")
+    return v.value
 
 
 __all__ = ["Opts", "Handle", "IluError", "ilu_setup", "ilu_setup_problem", "ilu_apply",

@@ -6,9 +6,14 @@
 // variant places the same workspace in the file-scope array below instead, so the call
 // itself never allocates: no cudaMalloc, no cudaFree, no allocating library routine.
 // Every GPU that loads the library holds the array (kWorkspaceBytes) until the process
-// exits. Calls share the array and it keeps the last call's contents; the control block
-// is cleared at the start of every call. Calls whose executions overlap on the GPU (two
-// streams, or two host threads) race on the array.
+// exits. Calls share the array and it keeps the last call's contents: the start kernel of
+// every call re-initialises the control state it relies on (step counter, zero flag,
+// barrier words) and writes every vector before reading it; the memset of the control
+// block before it is a defensive extra that also clears the Hessenberg entries. Calls
+// whose executions overlap on the GPU (two streams, or two host threads) race on the array.
+// The array's device address is looked up once per device and cached for the life of the
+// process: a cudaDeviceReset (or any reset of the device's primary context) invalidates it,
+// and calls after such a reset are not supported.
 #include <mutex>
 
 #include "handle.h"

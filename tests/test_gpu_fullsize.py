@@ -1,0 +1,122 @@
+"""Parity at the benchmark's full sizes, built exactly as bench.py builds them
+(`problems.make_workload(key, seed=0)` with the workload's solver options).
+
+  * The preconditioner apply against the FP64 oracle's apply, element by element, on the
+    1024^2 anisotropic workload (64 subdomain CTAs, ~380-level programs, 64 KB chunks, the
+    single-launch inner solve) and on the other full-size workloads: FP64 within 1e-12,
+    FP32 within the normwise and element-wise FP32 bars of test_gpu_parity.
+  * FGMRES to rtol 1e-8 against the oracle's record in tests/golden/oracle_fgmres_iters.json
+    (written by tests/golden/write_oracle_iters.py, which calls only the oracle): iteration
+    count within +-1 (FP64 preconditioner) or 10 % (FP32), true residual <= 1e-8, and the
+    solution within 1e-6 of the oracle's: its 2-norm relative to the oracle's, and every
+    sampled element (the digest's evenly spaced indices) within 1e-6 * ||x_oracle||_inf.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_08881_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "oracle_fgmres_iters.json")))
+TOL32, ELT32 = 2e-4, 1e-3   # the FP32 bars of test_gpu_parity (derivation there)
+
+FULL = ["aniso2d_1024_p64", "aniso3d_cuts_128_p256", "randsparse_500k_p64", "convdiff3d_96_p64"]
+
+
+def _sample_index(n):
+    # the digest's indices (tests/golden/write_oracle_iters.py: sample_index)
+    return np.unique(np.linspace(0, n - 1, min(1024, n)).round().astype(np.int64))
+
+
+@pytest.fixture(scope="module")
+def ilu():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+_probs = {}
+
+
+def _workload(key):
+    if key not in _probs:
+        _probs.clear()   # one full-size problem in host memory at a time
+        _probs[key] = P.make_workload(key, seed=0)
+    return _probs[key]
+
+
+def _solver(key, prec):
+    sol = dict(P.WORKLOAD_SOLVER[key])
+    restart = sol.pop("restart")
+    sol.pop("prec")
+    return sol, restart
+
+
+@pytest.mark.parametrize("key", FULL)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fullsize_apply_matches_oracle(ilu, key, prec):
+    if key != "aniso2d_1024_p64" and prec == "fp64":
+        pytest.skip("FP64 full-size apply: the benchmark workload only")
+    pr = _workload(key)
+    sol, _ = _solver(key, prec)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, **sol))
+    st = h.stats()
+    assert st["stream_path"]
+    if key == "aniso2d_1024_p64":
+        # the launch configuration the benchmark times (FP32: two 64 KB ring stages beside the
+        # working vector; FP64: two of 32 KB)
+        ring = 2 * 65536 if prec == "fp32" else 2 * 32768
+        assert st["inner_single_launch"] and h.stream_stats("fwd")["ring_bytes"] == ring
+    orc = O.Oracle.from_problem(pr, **sol)
+    r = np.random.default_rng(101).standard_normal(pr.n)
+    z = torch.full((pr.n,), np.nan, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, torch.from_numpy(r).cuda(), z)
+    torch.cuda.synchronize()
+    assert h.stats()["device_error"] == 0
+    got, ref = z.cpu().numpy(), orc.apply(r)
+    assert np.isfinite(got).all()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    elt = np.abs(got - ref).max() / np.abs(ref).max()
+    if prec == "fp64":
+        assert rel <= 1e-12 and elt <= 1e-12, (rel, elt)
+    else:
+        assert rel <= TOL32 and elt <= ELT32, (rel, elt)
+    h.close()
+
+
+@pytest.mark.parametrize("key,prec", [("aniso2d_1024_p64", "fp32"), ("aniso2d_1024_p64", "fp64"),
+                                      ("aniso3d_cuts_128_p256", "fp32"), ("randsparse_500k_p64", "fp32"),
+                                      ("convdiff3d_96_p64", "fp32")])
+def test_fullsize_fgmres_matches_oracle_record(ilu, key, prec):
+    gold = GOLD[key]
+    pr = _workload(key)
+    assert gold["n"] == pr.n and gold["status"] == 0
+    sol, restart = _solver(key, prec)
+    assert restart == gold["restart"]
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, **sol))
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros_like(b)
+    info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=restart, maxit=20000)
+    assert info["status"] == 0, info
+    xs = x.cpu().numpy()
+    res = np.linalg.norm(pr.b - pr.scipy() @ xs) / np.linalg.norm(pr.b)
+    assert res <= 1e-8 and info["rel_res_true"] <= 1e-8, (res, info)
+    it, it_o = info["iters"], gold["iters"]
+    if prec == "fp64":
+        assert abs(it - it_o) <= 1, (it, it_o)
+    else:
+        assert abs(it - it_o) <= max(2, it_o // 10), (it, it_o)
+    assert abs(np.linalg.norm(xs) - gold["x_norm2"]) <= 1e-6 * gold["x_norm2"]
+    samp = xs[_sample_index(pr.n)]
+    ref = np.array(gold["x_sample"])
+    assert np.abs(samp - ref).max() <= 1e-6 * gold["x_absmax"], np.abs(samp - ref).max()
+    h.close()
