@@ -841,8 +841,11 @@ ilu_status ilu_get_stream_stats(void* hp, int32_t program, int64_t* out) {
     const Handle* h = (const Handle*)hp;
     const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
     const StreamHost& S = h->sh[ids[program]];
-    for (int i = 0; i < 10; i++) out[i] = 0;
+    for (int i = 0; i < 13; i++) out[i] = 0;
     if (S.ch0.empty()) return ILU_OK;
+    out[10] = S.max_scan_waves;
+    out[11] = S.max_steps;
+    out[12] = S.chain_sections;
     out[8] = (int64_t)h->nst * h->chunk;
     out[9] = (!h->o.analysis_only && h->max_ns + 1 <= h->smem_len_stream) ? 1 : 0;
     out[0] = S.rw;

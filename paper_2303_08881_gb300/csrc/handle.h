@@ -41,6 +41,9 @@ struct StreamHost {
     int64_t waves = 0, segments = 0, records = 0, skips = 0;  // totals over the subdomains
     int64_t max_barriers = 0;                   // group barriers of the longest subdomain program
     int64_t max_levels_sub = 0;                 // levels of the deepest subdomain program
+    int64_t max_scan_waves = 0;                 // scan waves of the subdomain program with most
+    int64_t max_steps = 0;                      // barriers + scan waves, largest over the subdomains
+    int64_t chain_sections = 0;                 // subdomains whose chain section runs as chains
 };
 
 struct StreamBufs {

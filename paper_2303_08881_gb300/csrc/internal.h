@@ -55,8 +55,12 @@ struct NoInitAlloc : std::allocator<T> {
 template <class T>
 using rawvec = std::vector<T, NoInitAlloc<T>>;
 
+// scan_lvl (optional, one entry per subdomain): the first level of the subdomain's chain
+// section -- the levels from there to sub_lvl[s+1] may be scheduled as chains solved by
+// warp scans (stream_layout.h); empty when the program has no such section.
 struct ProgHost {
     rawvec<int32_t> sub_lvl, lvl_ptr, prow, pptr, pcol, psrc, pdsrc;
+    std::vector<int32_t> scan_lvl;
     int32_t max_level_rows = 0, max_levels = 0;
     int64_t nnz() const { return (int64_t)pcol.size(); }
 };

@@ -261,6 +261,53 @@ __device__ __forceinline__ void run_segment(const RecU<T, RW, V>& first, const u
     }
 }
 
+// One warp's part of a scan segment (stream_layout.h): lane l runs record l of each of its
+// nw waves. A linked record's predecessor is the record one lane below (or, for lane 0,
+// the previous wave's last record, already stored): lane l forms x_l = a_l + b_l x_{l-1}
+// with a_l from the values final before the wave -- x[row] and its columns, the linked
+// one left out -- and b_l = -val[0] / u_ll (column link) or 1 / u_ll (own-slot link), 0
+// without a link. Five shuffle rounds compose the maps (Kogge-Stone inclusive scan); a lane
+// whose map no longer depends on lower lanes (b = 0) keeps its value, so an unlinked row
+// gives exactly the level formula's operations. Loads of the wave precede its stores
+// (the shuffles join them), so a row may overwrite a slot an earlier row of the wave read.
+template <class T, int RW, class V>
+__device__ __forceinline__ void run_scan_segment(const RecU<T, RW, V>& first, const uint8_t* p, uint32_t stride,
+                                                 uint32_t nw, uint8_t* xb) {
+    const uint32_t lane = threadIdx.x & 31u;
+    RecU<T, RW, V> a = first, b;
+    for (uint32_t w = 0; w < nw; w++) {
+        rec_load(b, p + (w + 1 < nw ? (w + 1) * stride : 0u));
+        T xc[RW], xr;
+        rec_operands(a, xb, xc, xr);
+        const uint32_t hd = a.r.head;
+        const bool lc = lane != 0 && (hd & kRecLinkCol) != 0;
+        const bool ls = lane != 0 && (hd & kRecLinkSelf) != 0;
+        T pv[RW];
+#pragma unroll
+        for (int q = 0; q < RW; q++) pv[q] = widen<T, V>(a.r.val[q]) * xc[q];
+        if (lc) pv[0] = (T)0;
+#pragma unroll
+        for (int d = 1; d < RW; d *= 2)
+#pragma unroll
+            for (int q = 0; q + d < RW; q += 2 * d) pv[q] += pv[q + d];
+        const T dinv = a.r.dinv;
+        T al = ((ls ? (T)0 : xr) - pv[0]) * dinv;
+        T be = lc ? -widen<T, V>(a.r.val[0]) * dinv : (ls ? dinv : (T)0);
+#pragma unroll
+        for (int d = 1; d < 32; d *= 2) {
+            const T au = __shfl_up_sync(kFull, al, d);
+            const T bu = __shfl_up_sync(kFull, be, d);
+            if (lane >= (uint32_t)d && be != (T)0) {
+                al = fma(be, au, al);
+                be = be * bu;
+            }
+        }
+        if ((hd & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(hd)) = al;
+        __syncwarp();
+        a = b;
+    }
+}
+
 // The refill side of the ring (one thread outside the consumer group): chunk c >= nst
 // goes into stage c % nst once every consumer thread released chunk c - nst. Stops when
 // the consumers abort or a wait runs out, then waits (bounded) until every copy it or
@@ -338,7 +385,12 @@ __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const Rin
             const uint2 enn = tab[g + 2 < nseg ? g + 2 : 0];
             RecU<T, RW, V> rn;
             if (g + 1 < nseg && mine(en)) rec_load(rn, first_of(en));
-            if (mine(e)) run_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+            if (mine(e)) {
+                if (e.y & kSegScan)
+                    run_scan_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+                else
+                    run_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+            }
             if (e.y & kSegBarrier) group_sync(nt);
             e = en;
             en = enn;

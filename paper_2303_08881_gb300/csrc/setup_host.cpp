@@ -66,6 +66,7 @@ void prog_init(ProgHost& P) {
     P.pcol.clear();
     P.psrc.clear();
     P.pdsrc.clear();
+    P.scan_lvl.clear();
     P.max_level_rows = 0;
     P.max_levels = 0;
 }
@@ -135,6 +136,7 @@ void prog_concat(ProgHost& D, const std::vector<const ProgHost*>& fr) {
     for (size_t t = 0; t < nf; t++) {
         D.max_level_rows = std::max(D.max_level_rows, fr[t]->max_level_rows);
         D.max_levels = std::max(D.max_levels, fr[t]->max_levels);
+        for (int32_t e : fr[t]->scan_lvl) D.scan_lvl.push_back(e + (int32_t)lv[t]);
     }
 }
 
@@ -363,6 +365,264 @@ int ilut_local(const int32_t* rp, const int32_t* ci, const double* a, int32_t m,
     return ILU_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// pieces and waves of a streamed program (stream_layout.h)
+
+struct Piece {
+    int32_t k;      // packed row (-1: skip record, a hole in a wave)
+    int32_t q0, n;  // entries [q0, q0+n) of the row
+    bool last;      // applies the pivot inverse
+    uint8_t link;   // scan waves: 0 none, kLinkCol (entry `lead` holds the previous row's
+                    // value), kLinkSelf (the own slot does)
+    int32_t lead;   // with kLinkCol: the entry written first, in position 0 (else -1)
+};
+struct Wave {
+    size_t p0, p1;  // pieces
+    bool sync;      // group barrier after the wave
+    bool scan;      // a scan wave: width a multiple of 32, warp u holds pieces [32u, 32u + 32)
+};
+constexpr uint8_t kLinkCol = 1, kLinkSelf = 2;
+
+// Estimated consumer-group cycles of a wave schedule, used to pick between the level and the
+// chain schedule of a section: a plain wave costs about one row's latency (operand loads,
+// the product, the store), a scan wave the same plus five shuffle rounds, a barrier about
+// the rest of a level. (Measured on GB300: a 48-row level with its barrier takes ~400
+// cycles, a chained row ~70.)
+constexpr double kCostWave = 70.0, kCostScanWave = 260.0, kCostBarrier = 330.0;
+// the shortest chain worth a scan phase
+constexpr int32_t kMinChain = 3;
+
+double schedule_cost(const std::vector<Wave>& waves, size_t w0) {
+    double c = 0.0;
+    for (size_t w = w0; w < waves.size(); w++)
+        c += (waves[w].scan ? kCostScanWave : kCostWave) + (waves[w].sync ? kCostBarrier : 0.0);
+    return c;
+}
+
+// Chain schedule of packed rows [k0, k1) of one subdomain program (a section that starts
+// after a group barrier), appended to pieces / waves; every phase ends with a barrier.
+//
+// Dependencies between the rows follow the program order: a row reads its columns and its
+// own slot (after the last earlier writer of each) and overwrites its own slot (after every
+// earlier reader of it since that write). A phase takes the rows whose dependencies are all
+// done. From them it grows chains: a row joins the end of a chain when everything it needs
+// is done except the chain's last row, whose value it reads through one column or its own
+// slot (the link), or earlier rows of the same chain whose slots it only overwrites.
+// Such a chain is a first-order linear recurrence, x_i = a_i + b_i x_{i-1}, which a warp
+// solves 32 rows at a time by a prefix composition of the affine maps (the scan waves of
+// the device). When the longest chain is at least kMinChain rows the phase runs the chains
+// (single-piece rows only; longest first, each on the warp with the fewest rows, as far
+// as the longest chain's wave count allows); otherwise the ready rows run as one level
+// (plain waves, sub-levels for rows split into pieces). Chains of one phase touch
+// disjoint state, so the warps need no synchronisation until the phase's barrier.
+void phase_schedule(const ProgHost& P, int32_t k0, int32_t k1, int32_t RW, uint32_t nt,
+                    std::vector<int32_t>& lw, std::vector<std::vector<int32_t>>& rd,
+                    std::vector<Piece>& pieces, std::vector<Wave>& waves) {
+    const int32_t m = k1 - k0;
+    if (m <= 0) return;
+    struct Dep {
+        int32_t d;
+        int8_t kind;  // 0: d read the slot this row overwrites; kLinkCol: reads d's slot
+                      // through entry q; kLinkSelf: reads d's value in its own slot
+        int32_t q;
+    };
+    std::vector<int32_t> dptr((size_t)m + 1, 0);
+    std::vector<Dep> deps;
+    std::vector<int32_t> touched;
+    for (int32_t i = 0; i < m; i++) {
+        const int32_t k = k0 + i;
+        dptr[i] = (int32_t)deps.size();
+        const int32_t a = P.pptr[k], n = P.pptr[k + 1] - a, w = P.prow[k];
+        for (int32_t q = 0; q < n; q++) {
+            const int32_t c = P.pcol[a + q];
+            if (lw[c] >= 0) deps.push_back({lw[c], (int8_t)kLinkCol, q});
+        }
+        if (lw[w] >= 0) deps.push_back({lw[w], (int8_t)kLinkSelf, -1});
+        for (int32_t r : rd[w])
+            if (r != i) deps.push_back({r, 0, -1});
+        for (int32_t q = 0; q < n; q++) {
+            const int32_t c = P.pcol[a + q];
+            rd[c].push_back(i);
+            touched.push_back(c);
+        }
+        rd[w].clear();
+        lw[w] = i;
+        touched.push_back(w);
+    }
+    dptr[m] = (int32_t)deps.size();
+    for (int32_t c : touched) {  // leave the slot maps clean for the next section
+        lw[c] = -1;
+        rd[c].clear();
+    }
+    // successors (distinct), open dependency counts, heights (longest path to the end)
+    std::vector<int32_t> sptr((size_t)m + 1, 0), succ, left(m, 0), h(m, 1), np(m, 1);
+    {
+        std::vector<int32_t> seen(m, -1);
+        std::vector<std::pair<int32_t, int32_t>> edges;
+        for (int32_t i = 0; i < m; i++)
+            for (int32_t e = dptr[i]; e < dptr[i + 1]; e++) {
+                const int32_t d = deps[e].d;
+                if (seen[d] == i) continue;
+                seen[d] = i;
+                edges.push_back({d, i});
+                left[i]++;
+            }
+        for (auto& ed : edges) sptr[ed.first + 1]++;
+        for (int32_t i = 0; i < m; i++) sptr[i + 1] += sptr[i];
+        succ.resize(edges.size());
+        std::vector<int32_t> fill(sptr.begin(), sptr.end() - 1);
+        for (auto& ed : edges) succ[fill[ed.first]++] = ed.second;
+    }
+    for (int32_t i = m - 1; i >= 0; i--)
+        for (int32_t e = sptr[i]; e < sptr[i + 1]; e++) h[i] = std::max(h[i], 1 + h[succ[e]]);
+    for (int32_t i = 0; i < m; i++) {
+        const int32_t n = P.pptr[k0 + i + 1] - P.pptr[k0 + i];
+        np[i] = std::max(1, (n + RW - 1) / RW);
+    }
+    std::vector<char> done(m, 0), taken(m, 0);
+    std::vector<int32_t> chain_of(m, -1), link(m, 0), lead(m, -1), ready, next_ready;
+    for (int32_t i = 0; i < m; i++)
+        if (left[i] == 0) ready.push_back(i);
+    const uint32_t W = std::max(1u, nt / 32);
+    int32_t remaining = m;
+    std::vector<std::vector<int32_t>> chains;
+    auto finish = [&](int32_t i) {
+        done[i] = 1;
+        remaining--;
+        for (int32_t e = sptr[i]; e < sptr[i + 1]; e++)
+            if (--left[succ[e]] == 0) next_ready.push_back(succ[e]);
+    };
+    while (remaining > 0) {
+        std::vector<int32_t> R;
+        for (int32_t i : ready)
+            if (!done[i]) R.push_back(i);
+        for (int32_t i : next_ready)
+            if (!done[i]) R.push_back(i);
+        next_ready.clear();
+        std::sort(R.begin(), R.end());
+        R.erase(std::unique(R.begin(), R.end()), R.end());
+        if (R.empty()) break;  // unreachable: the program order is a topological order
+        std::stable_sort(R.begin(), R.end(), [&](int32_t a, int32_t b) { return h[a] > h[b]; });
+        // grow chains
+        chains.clear();
+        size_t lmax = 0;
+        for (int32_t i0 : R) {
+            if (np[i0] != 1 || taken[i0]) continue;
+            const int32_t cid = (int32_t)chains.size();
+            chains.push_back({i0});
+            taken[i0] = 1;
+            chain_of[i0] = cid;
+            link[i0] = 0;
+            lead[i0] = -1;
+            int32_t tail = i0;
+            for (;;) {
+                int32_t best = -1, bl = 0, bq = -1;
+                for (int32_t e = sptr[tail]; e < sptr[tail + 1]; e++) {
+                    const int32_t c = succ[e];
+                    if (taken[c] || done[c] || np[c] != 1) continue;
+                    bool ok = true;
+                    int32_t lk = 0, lq = -1;
+                    for (int32_t f = dptr[c]; f < dptr[c + 1] && ok; f++) {
+                        const Dep& D = deps[f];
+                        if (done[D.d]) continue;
+                        if (D.d == tail && D.kind == (int8_t)kLinkCol) {
+                            lk = kLinkCol;
+                            lq = D.q;
+                        } else if (D.d == tail && D.kind == (int8_t)kLinkSelf) {
+                            lk = kLinkSelf;
+                        } else if (!(D.kind == 0 && taken[D.d] && chain_of[D.d] == cid)) {
+                            ok = false;
+                        }
+                    }
+                    if (ok && (best < 0 || h[c] > h[best])) {
+                        best = c;
+                        bl = lk;
+                        bq = lq;
+                    }
+                }
+                if (best < 0) break;
+                chains[cid].push_back(best);
+                taken[best] = 1;
+                chain_of[best] = cid;
+                link[best] = bl;
+                lead[best] = bq;
+                tail = best;
+            }
+            lmax = std::max(lmax, chains[cid].size());
+        }
+        if ((int32_t)lmax < kMinChain) {
+            // a plain level: every ready row, sub-level j holding piece j of each row
+            for (auto& ch : chains)
+                for (int32_t i : ch) taken[i] = 0, chain_of[i] = -1;
+            int32_t npm = 1;
+            for (int32_t i : R) npm = std::max(npm, np[i]);
+            std::sort(R.begin(), R.end());
+            for (int32_t j = 0; j < npm; j++) {
+                std::vector<Piece> sub;
+                for (int32_t i : R) {
+                    const int32_t n = P.pptr[k0 + i + 1] - P.pptr[k0 + i];
+                    if (j < np[i]) sub.push_back({k0 + i, j * RW, std::min(RW, n - j * RW), j == np[i] - 1, 0, -1});
+                }
+                if (!waves.empty()) waves.back().sync = true;
+                for (size_t t = 0; t < sub.size(); t += nt) {
+                    const size_t t1 = std::min(sub.size(), t + nt);
+                    waves.push_back({pieces.size() + t, pieces.size() + t1, false, false});
+                }
+                pieces.insert(pieces.end(), sub.begin(), sub.end());
+            }
+            waves.back().sync = true;
+            for (int32_t i : R) finish(i);
+            ready.clear();
+            continue;
+        }
+        // a scan phase: chains onto warps, longest first, each on the least loaded warp,
+        // within the longest chain's wave count; chains that do not fit wait
+        std::vector<size_t> order(chains.size());
+        for (size_t c = 0; c < order.size(); c++) order[c] = c;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t a, size_t b) { return chains[a].size() > chains[b].size(); });
+        const size_t cap = 32 * ((lmax + 31) / 32);
+        std::vector<std::vector<int32_t>> seq(W);
+        for (size_t c : order) {
+            size_t u = 0;
+            for (size_t v = 1; v < W; v++)
+                if (seq[v].size() < seq[u].size()) u = v;
+            if (seq[u].size() + chains[c].size() <= cap) {
+                seq[u].insert(seq[u].end(), chains[c].begin(), chains[c].end());
+            } else {
+                for (int32_t i : chains[c]) taken[i] = 0, chain_of[i] = -1;
+            }
+        }
+        size_t used = 0, len = 0;
+        for (size_t u = 0; u < W; u++)
+            if (!seq[u].empty()) used = u + 1, len = std::max(len, seq[u].size());
+        const size_t nwv = (len + 31) / 32;
+        for (size_t wv = 0; wv < nwv; wv++) {
+            const size_t p0 = pieces.size();
+            for (size_t u = 0; u < used; u++)
+                for (size_t l = 0; l < 32; l++) {
+                    const size_t pos = 32 * wv + l;
+                    if (pos < seq[u].size()) {
+                        const int32_t i = seq[u][pos];
+                        const int32_t n = P.pptr[k0 + i + 1] - P.pptr[k0 + i];
+                        pieces.push_back({k0 + i, 0, n, true, (uint8_t)link[i], lead[i]});
+                    } else {
+                        pieces.push_back({-1, 0, 0, false, 0, -1});
+                    }
+                }
+            waves.push_back({p0, pieces.size(), false, true});
+        }
+        waves.back().sync = true;
+        for (size_t u = 0; u < used; u++)
+            for (int32_t i : seq[u]) {
+                taken[i] = 0;
+                chain_of[i] = -1;
+                finish(i);
+            }
+        ready = R;
+    }
+}
+
 }  // namespace
 
 // ====================================================================================
@@ -396,15 +656,6 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
     if (nt_fit < 32 || chunk > (1u << 20)) return false;
     S.nt = std::min(S.nt, std::min(nt_fit, kMaxConsumers));
     const uint32_t nt = (uint32_t)S.nt;
-    struct Piece {
-        int32_t k;      // packed row (-1: skip record, a hole in a merged wave)
-        int32_t q0, n;  // entries [q0, q0+n) of the row
-        bool last;      // applies the pivot inverse
-    };
-    struct Wave {
-        size_t p0, p1;  // pieces
-        bool sync;
-    };
     // Barrier elimination. A sub-level joins the current barrier-free stretch (no group
     // barrier before it) when each of its pieces can run on one consumer thread that
     // already holds, within the stretch, everything the piece touches -- the writer of
@@ -427,6 +678,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
         rawvec<int64_t> voff, doff;
         rawvec<int32_t> vsrc, dsrc;
         int64_t waves = 0, segments = 0, records = 0, skips = 0, max_barriers = 0, max_levels_sub = 0;
+        int64_t max_scan_waves = 0, max_steps = 0, chain_sections = 0;
         bool ok = true;
     };
     std::vector<Frag> frag(16);
@@ -461,14 +713,19 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
             wep[w] = epoch;
             wth[w] = t;
         };
-        for (int32_t s = s0; s < s1; s++) {
-            // pieces and waves of this subdomain, in program order
-            pieces.clear();
-            waves.clear();
-            epoch++;
-            int64_t nchunks = 0;
-            F.max_levels_sub = std::max<int64_t>(F.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
-            for (int32_t e = P.sub_lvl[s]; e < P.sub_lvl[s + 1]; e++) {
+        // slot maps of the chain schedule (all -1 / empty between sections)
+        std::vector<int32_t> ch_lw;
+        std::vector<std::vector<int32_t>> ch_rd;
+        if (!P.scan_lvl.empty()) {
+            ch_lw.assign((size_t)maxpos + 1, -1);
+            ch_rd.resize((size_t)maxpos + 1);
+        }
+        std::vector<Piece> alt_pieces;
+        std::vector<Wave> alt_waves;
+        // the level schedule of levels [ea, eb) of the current subdomain (barrier elimination
+        // above), appended to pieces / waves
+        auto level_schedule = [&](int32_t ea, int32_t eb) {
+            for (int32_t e = ea; e < eb; e++) {
                 const int32_t k0 = P.lvl_ptr[e], k1 = P.lvl_ptr[e + 1];
                 int32_t np = 1;
                 for (int32_t k = k0; k < k1; k++) np = std::max(np, (P.pptr[k + 1] - P.pptr[k] + RW - 1) / RW);
@@ -477,7 +734,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                     for (int32_t k = k0; k < k1; k++) {
                         const int32_t n = P.pptr[k + 1] - P.pptr[k];
                         const int32_t npk = std::max(1, (n + RW - 1) / RW);
-                        if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1});
+                        if (j < npk) sub.push_back({k, j * RW, std::min(RW, n - j * RW), j == npk - 1, 0, -1});
                     }
                     bool merge = !waves.empty() && sub.size() <= nt;
                     if (merge) {
@@ -527,26 +784,62 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                                 pieces.push_back(pc);
                                 mark(pc, (int32_t)t);
                             } else {
-                                pieces.push_back({-1, 0, 0, false});
+                                pieces.push_back({-1, 0, 0, false, 0, -1});
                             }
                         }
-                        waves.push_back({p0, pieces.size(), false});
+                        waves.push_back({p0, pieces.size(), false, false});
                     } else {
                         if (!waves.empty()) waves.back().sync = true;
                         epoch++;
                         for (size_t t = 0; t < sub.size(); t += nt) {
                             const size_t t1 = std::min(sub.size(), t + nt);
-                            waves.push_back({pieces.size() + t, pieces.size() + t1, false});
+                            waves.push_back({pieces.size() + t, pieces.size() + t1, false, false});
                         }
                         for (size_t i = 0; i < sub.size(); i++) mark(sub[i], (int32_t)(i % nt));
                         pieces.insert(pieces.end(), sub.begin(), sub.end());
                     }
                 }
             }
+        };
+        for (int32_t s = s0; s < s1; s++) {
+            // pieces and waves of this subdomain, in program order
+            pieces.clear();
+            waves.clear();
+            epoch++;
+            int64_t nchunks = 0;
+            F.max_levels_sub = std::max<int64_t>(F.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
+            const int32_t e_end = P.sub_lvl[s + 1];
+            const int32_t e_sec = P.scan_lvl.empty() ? e_end : std::max(P.sub_lvl[s], std::min(P.scan_lvl[s], e_end));
+            level_schedule(P.sub_lvl[s], e_sec);
+            if (e_sec < e_end) {
+                // the chain section: both schedules after a barrier, the cheaper one kept
+                if (!waves.empty()) waves.back().sync = true;
+                epoch++;
+                const size_t p_mark = pieces.size(), w_mark = waves.size();
+                level_schedule(e_sec, e_end);
+                if (waves.size() > w_mark) waves.back().sync = true;
+                const double c_level = schedule_cost(waves, w_mark);
+                alt_pieces.assign(pieces.begin() + (std::ptrdiff_t)p_mark, pieces.end());
+                alt_waves.assign(waves.begin() + (std::ptrdiff_t)w_mark, waves.end());
+                pieces.resize(p_mark);
+                waves.resize(w_mark);
+                phase_schedule(P, P.lvl_ptr[e_sec], P.lvl_ptr[e_end], RW, nt, ch_lw, ch_rd, pieces, waves);
+                const double c_chain = schedule_cost(waves, w_mark);
+                if (c_level <= c_chain) {
+                    pieces.resize(p_mark);
+                    waves.resize(w_mark);
+                    pieces.insert(pieces.end(), alt_pieces.begin(), alt_pieces.end());
+                    waves.insert(waves.end(), alt_waves.begin(), alt_waves.end());
+                } else {
+                    F.chain_sections++;
+                }
+            }
             if (!waves.empty()) waves.back().sync = true;
-            int64_t barriers = 0;
-            for (const Wave& W : waves) barriers += W.sync;
+            int64_t barriers = 0, scans = 0;
+            for (const Wave& W : waves) barriers += W.sync, scans += W.scan;
             F.max_barriers = std::max(F.max_barriers, barriers);
+            F.max_scan_waves = std::max(F.max_scan_waves, scans);
+            F.max_steps = std::max(F.max_steps, barriers + scans);
             F.waves += (int64_t)waves.size();
             // Pack the waves into chunks as segments: runs of consecutive waves of one width
             // (a narrower wave joins when the padding at most doubles it), never crossing a
@@ -555,6 +848,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 size_t w0, w1;
                 uint32_t width;
                 bool barrier;
+                bool scan;
             };
             std::vector<Seg> segs;
             size_t wi = 0;
@@ -567,6 +861,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 while (wi < waves.size()) {
                     const uint32_t ww = (uint32_t)(waves[wi].p1 - waves[wi].p0);
                     const bool join = !segs.empty() && !segs.back().barrier && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
+                                      segs.back().scan == waves[wi].scan &&
                                       (ww == segs.back().width || (ww < segs.back().width && segs.back().width <= 2 * ww));
                     if (join) {
                         if (!fits(segs.size(), recs + segs.back().width)) break;
@@ -574,7 +869,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                         recs += segs.back().width;
                     } else {
                         if (!fits(segs.size() + 1, recs + ww)) break;
-                        segs.push_back({wi, wi + 1, ww, false});
+                        segs.push_back({wi, wi + 1, ww, false, waves[wi].scan});
                         recs += ww;
                     }
                     if (waves[wi].sync) segs.back().barrier = true;
@@ -593,7 +888,8 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 for (size_t g = 0; g < segs.size(); g++) {
                     const Seg& G = segs[g];
                     put(cb + kChunkHdr + kSegEntry * g, (uint32_t)(roff / 16) | (G.width << 16), 4);
-                    put(cb + kChunkHdr + kSegEntry * g + 4, (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u), 4);
+                    put(cb + kChunkHdr + kSegEntry * g + 4,
+                        (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u) | (G.scan ? kSegScan : 0u), 4);
                     for (size_t w = G.w0; w < G.w1; w++) {
                         const Wave& W = waves[w];
                         for (uint32_t t = 0; t < G.width; t++) {
@@ -607,7 +903,8 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                                 continue;
                             }
                             const uint32_t row_off = (uint32_t)P.prow[pc->k] * (uint32_t)x_bytes;
-                            put(rb, (uint32_t)P.prow[pc->k] | ((uint32_t)pc->n << 24), 4);  // row index | n
+                            const uint32_t lbits = pc->link == kLinkCol ? kRecLinkCol : pc->link == kLinkSelf ? kRecLinkSelf : 0u;
+                            put(rb, (uint32_t)P.prow[pc->k] | ((uint32_t)pc->n << 24) | lbits, 4);  // row | n | link
                             F.doff.push_back((int64_t)(rb + RL.dinv));
                             F.dsrc.push_back(pc->last ? P.pdsrc[pc->k] : -1);  // -1: the pack writes 1
                             for (int32_t q = 0; q < RW; q++) {
@@ -615,7 +912,11 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                                     put(rb + RL.col + (size_t)q * 4, row_off, 4);
                                     continue;
                                 }
-                                const int32_t src = P.pptr[pc->k] + pc->q0 + q;
+                                // with a column link the linked entry comes first, the others
+                                // keep their order
+                                int32_t qq = q;
+                                if (pc->link == kLinkCol && pc->lead >= 0) qq = (q == 0) ? pc->lead : (q <= pc->lead ? q - 1 : q);
+                                const int32_t src = P.pptr[pc->k] + pc->q0 + qq;
                                 put(rb + RL.col + (size_t)q * 4, (uint32_t)P.pcol[src] * (uint32_t)x_bytes, 4);
                                 F.voff.push_back((int64_t)(rb + RL.val + (size_t)q * val_bytes));
                                 F.vsrc.push_back(P.psrc[src]);
@@ -629,6 +930,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
     });
     // the fragments one after the other: arrays sized once, one host thread per fragment
     S.waves = S.segments = S.records = S.skips = S.max_barriers = S.max_levels_sub = 0;
+    S.max_scan_waves = S.max_steps = S.chain_sections = 0;
     std::vector<size_t> nb(nfrag + 1, 0), nv(nfrag + 1, 0), nd(nfrag + 1, 0);
     for (int t = 0; t < nfrag; t++) {
         const Frag& F = frag[t];
@@ -643,6 +945,9 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
         S.skips += F.skips;
         S.max_barriers = std::max(S.max_barriers, F.max_barriers);
         S.max_levels_sub = std::max(S.max_levels_sub, F.max_levels_sub);
+        S.max_scan_waves = std::max(S.max_scan_waves, F.max_scan_waves);
+        S.max_steps = std::max(S.max_steps, F.max_steps);
+        S.chain_sections += F.chain_sections;
     }
     S.blob.resize(nb[nfrag]);
     S.voff.resize(nv[nfrag]);
@@ -1167,22 +1472,25 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                     P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                     P.max_levels = std::max(P.max_levels, a);
                 }
-                {   // forward and the first local Schur solve in one program (base 0)
+                {   // forward and the first local Schur solve in one program (base 0); the
+                    // chain section starts at the interface rows (the W or E product)
                     ProgHost& P = G[PR_FWDS];
                     int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
-                    if (wz) {
+                    if (!wz) a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
+                    P.scan_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
+                    if (wz)
                         a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
-                    } else {
-                        a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
+                    else
                         a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
-                    }
                     a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
                     a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, 0, lev);
                     P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                     P.max_levels = std::max(P.max_levels, a);
                 }
-                {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni)
+                {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni), one
+                    // chain section
                     ProgHost& P = G[PR_S];
+                    P.scan_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                     int a = prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, ni, lev);
                     a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, ni, lev);
                     P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
@@ -1232,6 +1540,9 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 w90 = wid[(wid.size() * 9) / 10];
             }
             int nt = std::min(128, std::max(32, (w90 + 31) / 32 * 32));
+            // programs with a chain section: at least two warps, so that independent chains
+            // (the sides of a subdomain's interface) run side by side
+            if (!P.scan_lvl.empty()) nt = std::max(nt, 64);
             if (h.o.block_threads) nt = std::max(32, (int)h.o.block_threads);
             h.sh[id].nt = std::min(nt, kMaxConsumers);
         }

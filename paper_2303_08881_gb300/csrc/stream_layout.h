@@ -8,6 +8,7 @@
 //       word 0: bits 0..15  offset of the segment's first record, in 16-byte units
 //               bits 16..24 width: records per wave (<= the consumer group's threads)
 //       word 1: bits 0..15  waves in the segment
+//               bit  30     a scan segment (below)
 //               bit  31     synchronise the consumer group after the segment
 //   the records of every segment, wave after wave, each wave `width` records.
 // Consumer thread t runs record t of every wave of a segment, in wave order; threads
@@ -15,8 +16,19 @@
 // barriers no thread reads or overwrites a slot another thread writes or reads there
 // (the builder arranges this; a thread's own program order covers everything else).
 //
+// Scan segments (width a multiple of 32) hold chains: warp u takes records 32u..32u+31 of
+// each wave, and the records a warp takes, wave after wave, form its sequence. A record
+// may be linked to the one before it in the sequence: it reads that row's result through
+// its first column (head bit 30) or in its own slot (head bit 29). A wave's 32 rows are
+// then x_l = a_l + b_l x_{l-1}, a_l and b_l formed from values final before the wave, and
+// the warp composes the affine maps by a prefix scan over its lanes; lane 0 reads its
+// predecessor (stored by the previous wave) from the vector. Every other value a record
+// reads was final before its segment or written by its own warp in an earlier wave; scan
+// stretches hold scan segments only and end at a barrier.
+//
 // A row record (16-byte aligned, read with 128-bit shared-memory loads) holds
-//   uint32 head      element index of x[row] | (n << 24); bit 31 marks a skip record
+//   uint32 head      element index of x[row] | (n << 24) | link bits 29, 30; bit 31 marks a
+//                    skip record
 //   T      dinv      1 / u_ii for an upper-triangular row, 1 for a unit-lower row
 //   uint32 col[RW]   byte offsets of x[col]; entries n.. hold the row's own offset
 //   V      val[RW]   entries n.. hold zero (V = T, or bfloat16 with T = float)
@@ -35,6 +47,10 @@ namespace ilu2l {
 constexpr int kChunkHdr = 16;
 constexpr int kSegEntry = 8;
 constexpr uint32_t kSegBarrier = 1u << 31;
+constexpr uint32_t kSegScan = 1u << 30;
+constexpr uint32_t kRecLinkCol = 1u << 30;   // linked through col[0]
+constexpr uint32_t kRecLinkSelf = 1u << 29;  // linked through the own slot
+constexpr uint32_t kRecNMask = 0x1Fu;        // (head >> 24) & kRecNMask = n (<= 16)
 constexpr uint32_t kSegMaxWaves = 0xFFFF;
 constexpr uint32_t kRecSkip = 1u << 31;
 // consumer threads of a stream kernel (its block has 256: one more warp hosts the

@@ -39,6 +39,9 @@ CFGS = [
 ]
 SKIP = 1 << 31
 BARRIER = 1 << 31
+SCAN = 1 << 30        # segment word 1: a scan segment
+LINK_COL = 1 << 30    # record head: linked to the previous row of the warp through col[0]
+LINK_SELF = 1 << 29   # record head: linked through the own slot
 
 
 @pytest.fixture(scope="module")
@@ -55,8 +58,9 @@ def _al(x, a):
 
 def parse(st):
     """Per subdomain: a list of stretches (the rows between two barriers); a stretch is a
-    list of waves; a wave is a list of (thread, write_slot, [read slots]) with skip
-    records left out. Checks the geometry and the padding of every record."""
+    list of waves; a wave is a list of (thread, write_slot, [read slots], link) with skip
+    records left out, link = None in plain waves and 0 / "col" / "self" in scan waves.
+    Checks the geometry and the padding of every record."""
     blob, ch0, chunk, rw, vb = st["blob"].tobytes(), st["ch0"], st["chunk"], st["rw"], st["val_bytes"]
     xb = st["x_bytes"]  # element size of the working vector and of dinv
     col_off = 2 * xb
@@ -72,6 +76,8 @@ def parse(st):
                 w0, w1 = struct.unpack_from("<II", blob, cb + 16 + 8 * g)
                 off, width, nw = (w0 & 0xFFFF) * 16, (w0 >> 16) & 0x1FF, w1 & 0xFFFF
                 assert off >= end and off + nw * width * rec_bytes <= chunk and 1 <= width <= st["threads"]
+                scan = bool(w1 & SCAN)
+                assert not scan or width % 32 == 0
                 end = off + nw * width * rec_bytes
                 for w in range(nw):
                     wave = []
@@ -82,10 +88,13 @@ def parse(st):
                         if head & SKIP:
                             assert head == SKIP and not any(cols)
                             continue
-                        n, row = (head >> 24) & 0x7F, head & 0xFFFFFF  # the head holds the row's index
+                        n, row = (head >> 24) & 0x1F, head & 0xFFFFFF  # the head holds the row's index
+                        link = ("col" if head & LINK_COL else "self" if head & LINK_SELF else 0) if scan else None
+                        assert scan or not head & (LINK_COL | LINK_SELF), "links only in scan segments"
+                        assert not (head & LINK_COL and head & LINK_SELF) and (link != "col" or n >= 1)
                         assert n <= rw and all(x % xb == 0 for x in cols)
                         assert all(x == row * xb for x in cols[n:]), "unused entries read the row's own slot"
-                        wave.append((t, row, [x // xb for x in cols[:n]]))
+                        wave.append((t, row, [x // xb for x in cols[:n]], link))
                     cur.append(wave)
                 if w1 & BARRIER:
                     stretches.append(cur)
@@ -96,37 +105,67 @@ def parse(st):
     return subs
 
 
+def _is_scan(stretch):
+    kinds = {r[3] is not None for wave in stretch for r in wave}
+    assert len(kinds) <= 1, "a stretch mixes scan and plain waves"
+    return kinds == {True}
+
+
 def hazards(stretches):
+    """Plain stretches: a thread may read a slot only if no other thread wrote it in the
+    stretch, and overwrite one only if no other thread read or wrote it there. Scan
+    stretches: the executor is the warp, in (wave, lane) order; a value written in the same
+    wave may be read only through the link (one lane below, via col[0] or the own slot), a
+    link must name exactly that writer, and no slot is shared between warps."""
     bad = 0
     for stretch in stretches:
+        scan = _is_scan(stretch)
         writer, readers = {}, {}
-        for wave in stretch:
-            for t, w, cols in wave:
-                for c in list(cols) + [w]:
-                    if writer.get(c, t) != t:
-                        bad += 1
-                    readers.setdefault(c, set()).add(t)
-                if writer.get(w, t) != t or readers[w] - {t}:
+        for wi, wave in enumerate(stretch):
+            for t, w, cols, link in wave:
+                ex = t // 32 if scan else t
+                lane = t % 32
+                for qi, c in enumerate(list(cols) + [w]):
+                    wr = writer.get(c)
+                    if wr is not None:
+                        if wr[0] != ex:
+                            bad += 1
+                        elif scan and wr[1] == wi:
+                            via = "self" if c == w and qi == len(cols) else ("col" if qi == 0 else None)
+                            if not (link == via and wr[2] == lane - 1 and lane > 0):
+                                bad += 1
+                    readers.setdefault(c, set()).add(ex)
+                if scan and link and lane > 0:
+                    c = cols[0] if link == "col" else w
+                    if writer.get(c) != (ex, wi, lane - 1):
+                        bad += 1   # the link must name the previous row of the warp
+                wr = writer.get(w)
+                if (wr is not None and wr[0] != ex) or readers[w] - {ex}:
                     bad += 1
-                writer[w] = t
+                writer[w] = (ex, wi, lane)
     return bad
 
 
 def replay(stretches, order):
+    """The rows with hashed values, stretch after stretch. "wave": wave by wave, threads in
+    order; "up" / "down": each executor's rows in its own order (plain: thread, scan:
+    warp), executors ascending / descending."""
     x = {}
     rid = 0
     for stretch in stretches:
+        scan = _is_scan(stretch)
         recs = []
         for wi, wave in enumerate(stretch):
-            for t, w, cols in wave:
-                recs.append((t, wi, w, cols, rid))
+            for t, w, cols, link in wave:
+                ex = t // 32 if scan else t
+                recs.append((ex, wi, t, w, cols, rid))
                 rid += 1
         if order == "wave":
             seq = recs
         else:
-            key = (lambda r: (r[0], r[1])) if order == "up" else (lambda r: (-r[0], r[1]))
-            seq = sorted(recs, key=key)
-        for t, wi, w, cols, r in seq:
+            sign = 1 if order == "up" else -1
+            seq = sorted(recs, key=lambda r: (sign * r[0], r[1], r[2]))
+        for ex, wi, t, w, cols, r in seq:
             x[w] = hash((x.get(w, ("in", w)), tuple(x.get(c, ("in", c)) for c in cols), r))
     return x
 
@@ -145,12 +184,15 @@ def test_stretches_are_race_free(ilu, name, cfg):
         assert stats["threads"] == st["threads"]
         n_rec = sum(len(w) for stretches in subs for s in stretches for w in s)
         n_ent = sum(len(r[2]) for stretches in subs for s in stretches for w in s for r in w)
+        n_scan = max(sum(len(s) for s in stretches if _is_scan(s)) for stretches in subs)
+        assert n_scan == stats["max_scan_waves"] or prog == "bj"
         assert n_rec == stats["records"] - stats["skips"]
         if prog != "fwd":  # the forward stream also holds the S~ rows
             assert n_rec >= sizes[f"prog_{prog}"]["rows"]
             assert n_ent == sizes[f"prog_{prog}"]["entries"]
         assert max(len(s) for s in subs) - 1 <= stats["max_barriers"]
         assert stats["max_barriers"] <= stats["max_levels"] * (1 + (st["rw"] < 16))
+        assert stats["max_steps"] <= stats["max_barriers"] + stats["max_scan_waves"]
         for s, stretches in enumerate(subs):
             assert hazards(stretches) == 0, (prog, s)
             ref = replay(stretches, "wave")
@@ -158,25 +200,46 @@ def test_stretches_are_race_free(ilu, name, cfg):
     h.close()
 
 
-def test_interface_chains_run_without_barriers(ilu):
-    """On 128 x 128 boxes of the 9-point problem the interface of a subdomain is a ring
-    walked as a few chains; the local Schur program keeps only a handful of barriers
-    where a plain level schedule needs one per level."""
+def test_interface_chains_run_as_warp_scans(ilu):
+    """On 128 x 128 boxes of the 9-point problem the interface of a subdomain is a ring of
+    chains (each row reads only the previous one of its side); the local Schur program and
+    the interface part of the forward program run them as scan waves, 32 rows per warp and
+    wave, with a handful of barriers where a plain level schedule needs one per level."""
     pr = P.aniso2d_boxes(256, 2, seed=0)
     h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
     st = h.stream_stats("s")
     assert st["max_levels"] > 250
-    assert st["max_barriers"] <= 8
+    assert st["chain_sections"] == pr.p and st["max_barriers"] <= 10
+    assert st["max_steps"] <= 48     # ~510 chained rows in <= 48 dependent steps
+    fw = h.stream_stats("fwd")
+    assert fw["chain_sections"] == pr.p and fw["max_scan_waves"] > 0
     h.close()
+
+
+def test_planted_link_errors_are_detected():
+    """the checker itself, on scan stretches: a read of a same-wave value that is not the
+    link, a link to a row that is not the previous one, and two warps sharing a slot"""
+    ok = [[[(0, 10, [], 0), (1, 11, [10], "col"), (2, 12, [11, 3], "col")]]]
+    assert hazards(ok) == 0
+    not_link = [[[(0, 10, [], 0), (1, 11, [], 0), (2, 12, [3, 10], "col")]]]  # reads lane 0's slot
+    assert hazards(not_link) >= 1
+    wrong_pred = [[[(0, 10, [], 0), (1, 11, [], 0), (2, 12, [10], "col")]]]   # linked to lane 0
+    assert hazards(wrong_pred) >= 1
+    self_link = [[[(0, 10, [3], 0), (1, 10, [4], "self")]]]                    # same slot, linked
+    assert hazards(self_link) == 0
+    cross_warp = [[[(0, 10, [], 0), (32, 13, [10], 0)]]]                      # warp 1 reads warp 0
+    assert hazards(cross_warp) == 1
+    later_wave = [[[(0, 10, [], 0)], [(1, 11, [10], 0)]]]                     # earlier wave, same warp
+    assert hazards(later_wave) == 0
 
 
 def test_planted_race_is_detected():
     """the checker itself: two threads touching one slot inside a stretch"""
-    raw = [[[(0, 5, [1]), (1, 6, [2])], [(1, 7, [5])]]]  # thread 1 reads slot 5 of thread 0
+    raw = [[[(0, 5, [1], None), (1, 6, [2], None)], [(1, 7, [5], None)]]]  # thread 1 reads slot 5 of thread 0
     assert hazards(raw) == 1
-    ok = [[[(0, 5, [1]), (1, 6, [2])]], [[(1, 7, [5])]]]  # a barrier in between
+    ok = [[[(0, 5, [1], None), (1, 6, [2], None)]], [[(1, 7, [5], None)]]]  # a barrier in between
     assert hazards(ok) == 0
-    war = [[[(0, 5, [3])], [(1, 3, [])]]]  # thread 1 overwrites what thread 0 read
+    war = [[[(0, 5, [3], None)], [(1, 3, [], None)]]]  # thread 1 overwrites what thread 0 read
     assert hazards(war) == 1
     a, b = replay(raw, "up"), replay(raw, "down")
     assert a != b or replay(raw, "wave") != a
