@@ -112,6 +112,12 @@ typedef struct {
     int32_t l1_block;     /* block Jacobi only (else ILU_ERR_ARG): 1 = l1-BJ (Sec. 4.3), every
                              diagonal entry of A_i increased by the sum of |a_ij| over the columns
                              of other subdomains before the factorisation. Default 0. */
+    int32_t chain_sched;  /* streamed path, schedule of the interface rows of each subdomain
+                             program (the forward program's W/E, L_S, U_S rows; the local Schur
+                             program): 0 = the cheaper of levels and chains by an estimate of
+                             consumer cycles (default), 1 = levels only, 2 = chains. Chains run
+                             rows that need only the previous row of their chain as warp scans
+                             (stream_layout.h); results agree with the level schedule to rounding. */
 } ilu_opts;
 
 typedef struct {

@@ -431,6 +431,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->ordering = ILU_ORDER_NATURAL;
     o->fill_level = 0;
     o->l1_block = 0;
+    o->chain_sched = 0;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -493,7 +494,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
         (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
-        (o.l1_block && o.variant != ILU_VARIANT_BJ)) {
+        (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2) {
         delete h;
         return ILU_ERR_ARG;
     }

@@ -59,8 +59,9 @@ void host_levels(Handle& h);
 
 // Builds the chunked stream of program P; false if a single row does not fit a chunk.
 // x_bytes: element size of the working vector (and of dinv); val_bytes: of the values.
+// chain_sched: ilu_opts.chain_sched (0 the cheaper of levels and chains, 1 levels, 2 chains).
 bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int val_bytes, uint32_t chunk,
-                  StreamHost& S);
+                  StreamHost& S, int chain_sched);
 
 struct ProgBufs {
     int32_t *sub_lvl = nullptr, *lvl_ptr = nullptr, *prow = nullptr, *pptr = nullptr,

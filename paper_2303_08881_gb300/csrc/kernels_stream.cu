@@ -270,6 +270,8 @@ __device__ __forceinline__ void run_segment(const RecU<T, RW, V>& first, const u
 // whose map no longer depends on lower lanes (b = 0) keeps its value, so an unlinked row
 // gives exactly the level formula's operations. Loads of the wave precede its stores
 // (the shuffles join them), so a row may overwrite a slot an earlier row of the wave read.
+// The lanes store in one instruction, so of two rows of a wave writing one slot (a row and
+// its successor linked through that slot) only the later stores.
 template <class T, int RW, class V>
 __device__ __forceinline__ void run_scan_segment(const RecU<T, RW, V>& first, const uint8_t* p, uint32_t stride,
                                                  uint32_t nw, uint8_t* xb) {
@@ -302,7 +304,10 @@ __device__ __forceinline__ void run_scan_segment(const RecU<T, RW, V>& first, co
                 be = be * bu;
             }
         }
-        if ((hd & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(hd)) = al;
+        // the lanes of a wave store together: a row whose successor (one lane up) is linked
+        // through the same slot leaves the slot to it
+        const bool succ_self = __shfl_down_sync(kFull, (hd & kRecLinkSelf) != 0 ? 1 : 0, 1) != 0 && lane < 31;
+        if ((hd & kRecSkip) == 0 && !succ_self) *reinterpret_cast<T*>(xb + row_byte<T>(hd)) = al;
         __syncwarp();
         a = b;
     }

@@ -629,7 +629,7 @@ void phase_schedule(const ProgHost& P, int32_t k0, int32_t k1, int32_t RW, uint3
 // chunked streams (stream_layout.h)
 
 bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int val_bytes, uint32_t chunk,
-                  StreamHost& S) {
+                  StreamHost& S, int chain_sched) {
     S.blob.clear();
     S.ch0.assign(1, 0);
     S.voff.clear();
@@ -809,7 +809,9 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
             int64_t nchunks = 0;
             F.max_levels_sub = std::max<int64_t>(F.max_levels_sub, P.sub_lvl[s + 1] - P.sub_lvl[s]);
             const int32_t e_end = P.sub_lvl[s + 1];
-            const int32_t e_sec = P.scan_lvl.empty() ? e_end : std::max(P.sub_lvl[s], std::min(P.scan_lvl[s], e_end));
+            const int32_t e_sec = (P.scan_lvl.empty() || chain_sched == 1)
+                                      ? e_end
+                                      : std::max(P.sub_lvl[s], std::min(P.scan_lvl[s], e_end));
             level_schedule(P.sub_lvl[s], e_sec);
             if (e_sec < e_end) {
                 // the chain section: both schedules after a barrier, the cheaper one kept
@@ -825,7 +827,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 waves.resize(w_mark);
                 phase_schedule(P, P.lvl_ptr[e_sec], P.lvl_ptr[e_end], RW, nt, ch_lw, ch_rd, pieces, waves);
                 const double c_chain = schedule_cost(waves, w_mark);
-                if (c_level <= c_chain) {
+                if (chain_sched != 2 && c_level <= c_chain) {
                     pieces.resize(p_mark);
                     waves.resize(w_mark);
                     pieces.insert(pieces.end(), alt_pieces.begin(), alt_pieces.end());
@@ -1563,7 +1565,7 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 break;
             }
         bool ok = true;
-        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, valb, h.chunk, h.sh[id]);
+        for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, valb, h.chunk, h.sh[id], h.o.chain_sched);
         if (!ok) h.stream_path = false;
     }
     return ILU_OK;

@@ -243,3 +243,73 @@ def test_planted_race_is_detected():
     assert hazards(war) == 1
     a, b = replay(raw, "up"), replay(raw, "down")
     assert a != b or replay(raw, "wave") != a
+
+
+def emulate(stretches):
+    """The device's semantics on hashed values: a plain wave's rows run one after another
+    (its threads are independent); in a scan wave each warp loads every operand of its 32
+    rows before any of them stores, and a linked row (lane > 0) takes its predecessor's new
+    value in place of the loaded one -- through col[0] or its own slot. A row's value
+    hashes its slot and the (slot, value) pairs it read, so two schedules of one program
+    give equal results exactly when every row sees the same inputs."""
+    x = {}
+
+    def val(c):
+        return x.get(c, ("in", c))
+
+    def row_hash(w, own, pairs):
+        return hash((w, own, tuple(sorted(pairs))))
+
+    for stretch in stretches:
+        for wave in stretch:
+            if not wave or wave[0][3] is None:
+                for t, w, cols, link in wave:
+                    x[w] = row_hash(w, val(w), [(c, val(c)) for c in cols])
+                continue
+            warps = {}
+            for rec in wave:
+                warps.setdefault(rec[0] // 32, []).append(rec)
+            for u, recs in warps.items():
+                snap = {c: val(c) for t, w, cols, link in recs for c in list(cols) + [w]}
+                res = {}
+                for t, w, cols, link in recs:
+                    lane = t % 32
+                    prev = res.get(lane - 1) if lane > 0 else None
+                    own = prev[1] if (link == "self" and lane > 0) else snap[w]
+                    pairs = [(c, prev[1] if (link == "col" and lane > 0 and qi == 0) else snap[c])
+                             for qi, c in enumerate(cols)]
+                    if link and lane > 0:
+                        assert prev is not None, "a linked row needs its predecessor one lane below"
+                    res[lane] = (w, row_hash(w, own, pairs))
+                # the lanes store in one instruction: a slot written by two lanes of the wave
+                # must be a row and its successor linked through that slot, whose lane stores
+                lanes_of = {}
+                for t, w, cols, link in recs:
+                    lanes_of.setdefault(w, []).append((t % 32, link))
+                for w, ls in lanes_of.items():
+                    ls.sort()
+                    for (la, _), (lb, lkb) in zip(ls, ls[1:]):
+                        assert lb == la + 1 and lkb == "self", f"slot {w} stored by lanes {la} and {lb}"
+                for lane, (w, v) in res.items():
+                    if lanes_of[w][-1][0] == lane:
+                        x[w] = v
+    return x
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("cfg", [c for c in CFGS if c["variant"] != "bj"], ids=lambda c: "-".join(map(str, c.values())))
+def test_chain_schedule_computes_the_level_program(ilu, name, cfg):
+    """Every subdomain program scheduled as chains (warp scans) computes, on the device's
+    semantics, exactly what its level schedule computes: each row reads the same inputs."""
+    pr = CASES[name]()
+    res = {}
+    for mode in ("levels", "chains"):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, chain_sched=mode, **cfg))
+        progs = ["fwd", "s"] if cfg["variant"] == "schur" else ["fwd"]
+        res[mode] = {prog: [emulate(st) for st in parse(h.stream(prog))] for prog in progs}
+        if mode == "chains":
+            assert sum(h.stream_stats(p)["chain_sections"] for p in progs) > 0 or name in ("rand", "p1")
+        h.close()
+    for prog in res["levels"]:
+        for s, (a, b) in enumerate(zip(res["levels"][prog], res["chains"][prog])):
+            assert a == b, (prog, s)
