@@ -313,6 +313,30 @@ __device__ __forceinline__ void run_scan_segment(const RecU<T, RW, V>& first, co
     }
 }
 
+// A run of levels (segment bit kSegSyncEach): wave w is one level, the group meets at its
+// barrier after every wave. Every consumer thread runs the loop (the barrier counts all of
+// them); a thread with a record in the waves (mine) loads its operands right after the
+// barrier -- the record's column offsets are already in registers -- forms the row, stores
+// it, and only then loads the record two levels ahead, so the dependent path of a level
+// is operand loads, the product, the store and the barrier.
+template <class T, int RW, class V>
+__device__ __forceinline__ void run_level_segment(const RecU<T, RW, V>& first, const uint8_t* p, uint32_t stride,
+                                                  uint32_t nw, uint8_t* xb, bool mine, int nt) {
+    RecU<T, RW, V> a = first, b;
+    if (mine) rec_load(b, p + (nw > 1 ? stride : 0u));
+    for (uint32_t w = 0; w < nw; w++) {
+        if (mine) {
+            T xc[RW], xr;
+            rec_operands(a, xb, xc, xr);
+            const T v = rec_value(a, xc, xr);
+            if ((a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(a.r.head)) = v;
+            a = b;
+            rec_load(b, p + (w + 2 < nw ? (w + 2) * stride : 0u));
+        }
+        group_sync(nt);
+    }
+}
+
 // The refill side of the ring (one thread outside the consumer group): chunk c >= nst
 // goes into stage c % nst once every consumer thread released chunk c - nst. Stops when
 // the consumers abort or a wait runs out, then waits (bounded) until every copy it or
@@ -390,13 +414,18 @@ __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const Rin
             const uint2 enn = tab[g + 2 < nseg ? g + 2 : 0];
             RecU<T, RW, V> rn;
             if (g + 1 < nseg && mine(en)) rec_load(rn, first_of(en));
-            if (mine(e)) {
-                if (e.y & kSegScan)
-                    run_scan_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
-                else
-                    run_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+            if (e.y & kSegSyncEach) {
+                run_level_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb, mine(e),
+                                            nt);
+            } else {
+                if (mine(e)) {
+                    if (e.y & kSegScan)
+                        run_scan_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+                    else
+                        run_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb);
+                }
+                if (e.y & kSegBarrier) group_sync(nt);
             }
-            if (e.y & kSegBarrier) group_sync(nt);
             e = en;
             en = enn;
             r = rn;

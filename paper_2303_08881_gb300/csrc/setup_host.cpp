@@ -851,6 +851,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 uint32_t width;
                 bool barrier;
                 bool scan;
+                bool each;  // a barrier after every wave
             };
             std::vector<Seg> segs;
             size_t wi = 0;
@@ -862,7 +863,11 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 };
                 while (wi < waves.size()) {
                     const uint32_t ww = (uint32_t)(waves[wi].p1 - waves[wi].p0);
-                    const bool join = !segs.empty() && !segs.back().barrier && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
+                    // a plain wave followed by a barrier starts a run of levels (a barrier after
+                    // every wave) that later such waves join; other segments end at a barrier
+                    const bool level = waves[wi].sync && !waves[wi].scan;
+                    const bool open = !segs.empty() && (segs.back().each ? level : !segs.back().barrier);
+                    const bool join = open && segs.back().w1 - segs.back().w0 < kSegMaxWaves &&
                                       segs.back().scan == waves[wi].scan &&
                                       (ww == segs.back().width || (ww < segs.back().width && segs.back().width <= 2 * ww));
                     if (join) {
@@ -871,10 +876,10 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                         recs += segs.back().width;
                     } else {
                         if (!fits(segs.size() + 1, recs + ww)) break;
-                        segs.push_back({wi, wi + 1, ww, false, waves[wi].scan});
+                        segs.push_back({wi, wi + 1, ww, false, waves[wi].scan, level});
                         recs += ww;
                     }
-                    if (waves[wi].sync) segs.back().barrier = true;
+                    if (waves[wi].sync && !segs.back().each) segs.back().barrier = true;
                     wi++;
                 }
                 if (segs.empty()) {  // a wave wider than a chunk (excluded by nt_fit)
@@ -891,7 +896,8 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                     const Seg& G = segs[g];
                     put(cb + kChunkHdr + kSegEntry * g, (uint32_t)(roff / 16) | (G.width << 16), 4);
                     put(cb + kChunkHdr + kSegEntry * g + 4,
-                        (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u) | (G.scan ? kSegScan : 0u), 4);
+                        (uint32_t)(G.w1 - G.w0) | (G.barrier ? kSegBarrier : 0u) | (G.scan ? kSegScan : 0u) |
+                            (G.each ? kSegSyncEach : 0u), 4);
                     for (size_t w = G.w0; w < G.w1; w++) {
                         const Wave& W = waves[w];
                         for (uint32_t t = 0; t < G.width; t++) {

@@ -8,6 +8,8 @@
 //       word 0: bits 0..15  offset of the segment's first record, in 16-byte units
 //               bits 16..24 width: records per wave (<= the consumer group's threads)
 //       word 1: bits 0..15  waves in the segment
+//               bit  29     synchronise the consumer group after every wave (a run of
+//                           levels, one wave each)
 //               bit  30     a scan segment (below)
 //               bit  31     synchronise the consumer group after the segment
 //   the records of every segment, wave after wave, each wave `width` records.
@@ -48,6 +50,7 @@ constexpr int kChunkHdr = 16;
 constexpr int kSegEntry = 8;
 constexpr uint32_t kSegBarrier = 1u << 31;
 constexpr uint32_t kSegScan = 1u << 30;
+constexpr uint32_t kSegSyncEach = 1u << 29;
 constexpr uint32_t kRecLinkCol = 1u << 30;   // linked through col[0]
 constexpr uint32_t kRecLinkSelf = 1u << 29;  // linked through the own slot
 constexpr uint32_t kRecNMask = 0x1Fu;        // (head >> 24) & kRecNMask = n (<= 16)

@@ -40,6 +40,7 @@ CFGS = [
 SKIP = 1 << 31
 BARRIER = 1 << 31
 SCAN = 1 << 30        # segment word 1: a scan segment
+EACH = 1 << 29        # segment word 1: a barrier after every wave
 LINK_COL = 1 << 30    # record head: linked to the previous row of the warp through col[0]
 LINK_SELF = 1 << 29   # record head: linked through the own slot
 
@@ -96,6 +97,10 @@ def parse(st):
                         assert all(x == row * xb for x in cols[n:]), "unused entries read the row's own slot"
                         wave.append((t, row, [x // xb for x in cols[:n]], link))
                     cur.append(wave)
+                    if w1 & EACH:
+                        assert not scan and not w1 & BARRIER
+                        stretches.append(cur)
+                        cur = []
                 if w1 & BARRIER:
                     stretches.append(cur)
                     cur = []
