@@ -315,7 +315,9 @@ __device__ __forceinline__ void run_scan_segment(const RecU<T, RW, V>& first, co
 
 // A run of levels (segment bit kSegSyncEach): wave w is one level, the group meets at its
 // barrier after every wave. Every consumer thread runs the loop (the barrier counts all of
-// them); a thread with a record in the waves (mine) loads its operands right after the
+// them), and without a branch: a thread beyond the segment's width works on a stand-in --
+// p points at the wave's first record -- and does not store (a divergent branch around
+// the row costs more than the row on GB300). A thread loads its operands right after the
 // barrier -- the record's column offsets are already in registers -- forms the row, stores
 // it, and only then loads the record two levels ahead, so the dependent path of a level
 // is operand loads, the product, the store and the barrier.
@@ -323,16 +325,14 @@ template <class T, int RW, class V>
 __device__ __forceinline__ void run_level_segment(const RecU<T, RW, V>& first, const uint8_t* p, uint32_t stride,
                                                   uint32_t nw, uint8_t* xb, bool mine, int nt) {
     RecU<T, RW, V> a = first, b;
-    if (mine) rec_load(b, p + (nw > 1 ? stride : 0u));
+    rec_load(b, p + (nw > 1 ? stride : 0u));
     for (uint32_t w = 0; w < nw; w++) {
-        if (mine) {
-            T xc[RW], xr;
-            rec_operands(a, xb, xc, xr);
-            const T v = rec_value(a, xc, xr);
-            if ((a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(a.r.head)) = v;
-            a = b;
-            rec_load(b, p + (w + 2 < nw ? (w + 2) * stride : 0u));
-        }
+        T xc[RW], xr;
+        rec_operands(a, xb, xc, xr);
+        const T v = rec_value(a, xc, xr);
+        if (mine && (a.r.head & kRecSkip) == 0) *reinterpret_cast<T*>(xb + row_byte<T>(a.r.head)) = v;
+        a = b;
+        rec_load(b, p + (w + 2 < nw ? (w + 2) * stride : 0u));
         group_sync(nt);
     }
 }
@@ -404,16 +404,18 @@ __device__ bool ring_run(const StreamDev<T>& S, int s, const Smem& sm, const Rin
         // Lookahead: while segment g runs, the table entry of g + 2 and the first record of
         // g + 1 are in flight, so a level costs its operand loads, arithmetic and barrier.
         // (Every chunk holds at least one segment; reads past the table's end re-read it.)
-        auto first_of = [&](uint2 e) { return cb + (e.x & 0xFFFFu) * 16u + (uint32_t)tid * RB; };
+        // a thread beyond a segment's width addresses its first record instead (loads stay
+        // in the chunk and need no branch; such a thread never stores)
         auto mine = [&](uint2 e) { return (uint32_t)tid < ((e.x >> 16) & 0x1FFu); };
+        auto first_of = [&](uint2 e) { return cb + (e.x & 0xFFFFu) * 16u + (mine(e) ? (uint32_t)tid * RB : 0u); };
         uint2 e = tab[0];
         uint2 en = tab[nseg > 1 ? 1 : 0];
         RecU<T, RW, V> r;
-        if (mine(e)) rec_load(r, first_of(e));
+        rec_load(r, first_of(e));
         for (uint32_t g = 0; g < nseg; g++) {
             const uint2 enn = tab[g + 2 < nseg ? g + 2 : 0];
             RecU<T, RW, V> rn;
-            if (g + 1 < nseg && mine(en)) rec_load(rn, first_of(en));
+            rec_load(rn, first_of(en));
             if (e.y & kSegSyncEach) {
                 run_level_segment<T, RW, V>(r, first_of(e), ((e.x >> 16) & 0x1FFu) * RB, e.y & 0xFFFFu, xb, mine(e),
                                             nt);
