@@ -93,8 +93,8 @@ struct InnerCtl {
     int32_t steps;                            // -1 while running, else the steps taken
     int32_t zero;                             // c == 0
     // grid barrier of the single-launch inner solve (cleared by the kernel that starts it)
-    uint32_t gbar_count;                      // CTAs arrived at the current barrier
-    uint32_t gbar_gen;                        // barriers completed (wraps)
+    uint32_t gbar_count;                      // arrivals at the grid barriers of the current launch
+    uint32_t gbar_gen;                        // (unused)
     int32_t gbar_abort;                       // a CTA gave up waiting: the others stop too
 };
 

@@ -629,37 +629,39 @@ __global__ void __launch_bounds__(256) k_inner_a_s(SubDev sd, StreamDev<T> S, Ri
 }
 
 // Grid-wide barrier of the single-launch inner solve (a cooperative launch guarantees
-// that every CTA is resident). Thread 0 of each CTA arrives on a counter; the last one
-// resets it and advances the generation the others wait for. Waits are bounded: a CTA
-// that gives up sets bit 2 of the device error word and the abort word, which ends the
-// others' waits too. Returns false (uniform over the CTA) after an abort.
-__device__ bool grid_sync(InnerCtl* ctl, uint32_t nblocks, uint64_t spin, int32_t* err) {
+// that every CTA is resident). The arrival counter only grows within a launch (the kernel
+// that starts the inner solve clears it): at its b-th barrier (b = 1, 2, ...) thread 0 of
+// each CTA adds 1 with release-acquire semantics -- publishing the CTA's partial sums,
+// ordered before it by the block barrier -- and waits, with acquire loads, until the
+// counter reaches b * nblocks. One atomic and one observed store per barrier; no fences.
+// Waits are bounded: a CTA that gives up sets bit 2 of the device error word and the abort
+// word, which ends the others' waits too. Returns false (uniform over the CTA) after an
+// abort.
+__device__ bool grid_sync(InnerCtl* ctl, uint32_t nblocks, uint32_t& epoch, uint64_t spin, int32_t* err) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile uint32_t* gen = &ctl->gbar_gen;
-        volatile int32_t* abort = &ctl->gbar_abort;
-        const uint32_t g = *gen;
-        __threadfence();
+        epoch++;
+        const uint32_t target = epoch * nblocks;
+        uint32_t v;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(&ctl->gbar_count) : "memory");
         int ok = 1;
-        if (atomicAdd(&ctl->gbar_count, 1u) == nblocks - 1) {
-            atomicExch(&ctl->gbar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->gbar_gen, 1u);
-        } else {
-            for (uint64_t i = 0; *gen == g; i++) {
+        if (v + 1 != target) {
+            volatile int32_t* abort = &ctl->gbar_abort;
+            for (uint64_t i = 0;; i++) {
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->gbar_count) : "memory");
+                if ((int32_t)(v - target) >= 0) break;
                 if (*abort || i >= spin) {
                     ok = 0;
                     break;
                 }
             }
         }
-        if (!ok || *abort) {
+        if (!ok || *(volatile int32_t*)&ctl->gbar_abort) {
             ok = 0;
             atomicOr(err, kErrTimeout);
-            *abort = 1;
+            *(volatile int32_t*)&ctl->gbar_abort = 1;
         }
-        __threadfence();
         ok_s = ok;
     }
     __syncthreads();
@@ -691,6 +693,7 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
     T* x = xvec<T, XS>(sm, xg + ni, q0);
     const double* nbank = in.part + ((size_t)2 * (kMaxInner + 1)) * p;
     double beta = 0.0;
+    uint32_t gepoch = 0;  // grid barriers passed (thread 0)
     for (int j = 0; j < in.k; j++) {
         // ---- A
         const double nrm = sqrt(warp_allsum_ldcg(nbank, p));
@@ -762,7 +765,7 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
                     for (int u = 0; u < 8 && i0 + u <= j; u++)
                         in.part[((size_t)(bank * (kMaxInner + 1) + i0 + u)) * p + s] = (double)acc[u];
             }
-            if (!grid_sync(ctl, (uint32_t)p, cfg.spin, cfg.err)) return;
+            if (!grid_sync(ctl, (uint32_t)p, gepoch, cfg.spin, cfg.err)) return;
             // ---- B (bank 0) / C (bank 1): coefficients, Hessenberg column, update
             {
                 const int lane = tid & 31, nw = blockDim.x >> 5;
@@ -791,7 +794,7 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
             if (bank) {
                 nacc = block_sum_t<T>(nacc, reinterpret_cast<T*>(red));
                 if (tid == 0) in.part[((size_t)2 * (kMaxInner + 1)) * p + s] = (double)nacc;
-                if (!grid_sync(ctl, (uint32_t)p, cfg.spin, cfg.err)) return;
+                if (!grid_sync(ctl, (uint32_t)p, gepoch, cfg.spin, cfg.err)) return;
             }
         }
     }
