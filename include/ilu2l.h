@@ -118,6 +118,12 @@ typedef struct {
                              consumer cycles (default), 1 = levels only, 2 = chains. Chains run
                              rows that need only the previous row of their chain as warp scans
                              (stream_layout.h); results agree with the level schedule to rounding. */
+    int32_t gs_first_fp32;/* gmres_solve: 1 (default) = the first of the two classical Gram-Schmidt
+                             passes forms its coefficients h1 = V^T w from FP32 copies of V and w;
+                             w -= V h1, the second pass h2 = V^T w, w -= V h2 and H = h1 + h2 stay
+                             FP64, so the Arnoldi relation A z_j = V H_j + w holds to FP64
+                             rounding and the second pass removes the first pass's FP32 error
+                             (about 6e-8 ||w||) from w. 0 = both passes in FP64. */
 } ilu_opts;
 
 typedef struct {

@@ -46,7 +46,8 @@ class ilu_opts(C.Structure):
                 ("pivot_eps", C.c_double), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
                 ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32),
-                ("fill_level", C.c_int32), ("l1_block", C.c_int32), ("chain_sched", C.c_int32)]
+                ("fill_level", C.c_int32), ("l1_block", C.c_int32), ("chain_sched", C.c_int32),
+                ("gs_first_fp32", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -147,6 +148,7 @@ class Opts:
     fill_level: int = 0             # k > 0: ILU(k) / MILU(k) in the level-k fill pattern
     l1_block: bool = False          # block Jacobi: l1-BJ diagonal augmentation
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
+    gs_first_fp32: bool = True      # FGMRES: first Gram-Schmidt pass's coefficients from FP32 copies
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -170,6 +172,7 @@ class Opts:
         o.fill_level = int(self.fill_level)
         o.l1_block = int(bool(self.l1_block))
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]
+        o.gs_first_fp32 = int(bool(self.gs_first_fp32))
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:

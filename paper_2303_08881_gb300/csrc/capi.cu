@@ -276,6 +276,13 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.ctl = h.alloc<FgCtl>(1, &e);
     if (!f.V || !f.Z || !f.w || !f.H || !f.cs || !f.sn || !f.g || !f.h2 || !f.hnext || !f.part || !f.ctl)
         return map_err(e);
+    f.V32 = nullptr;
+    f.w32 = nullptr;
+    if (h.o.gs_first_fp32) {
+        f.V32 = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
+        f.w32 = h.alloc<float>((size_t)f.ld, &e);
+        if (!f.V32 || !f.w32) return map_err(e);
+    }
     CK(cudaMemsetAsync(f.ctl, 0, sizeof(FgCtl), h.st));
     f.m = m;
     f.G = h.fg_G;
@@ -432,6 +439,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->fill_level = 0;
     o->l1_block = 0;
     o->chain_sched = 0;
+    o->gs_first_fp32 = 1;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -494,7 +502,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
         (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
-        (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2) {
+        (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
+        o.gs_first_fp32 < 0 || o.gs_first_fp32 > 1) {
         delete h;
         return ILU_ERR_ARG;
     }

@@ -138,6 +138,8 @@ struct FgDev {
     double* hnext;  // 1: norm of the next basis vector
     double* part;   // G x (m+1) partial sums
     FgCtl* ctl;
+    float* V32;     // (m+1) x ld: FP32 copy of V for the first Gram-Schmidt pass (null: FP64 pass)
+    float* w32;     // n: FP32 copy of w = A z_j for that pass
     int32_t m, G;
     int64_t ld;     // leading dimension of V and Z: n rounded up to 64 (512-byte rows)
 };

@@ -8,7 +8,8 @@
 // device: the host reads it once per cycle.
 //
 // One Arnoldi step j (after z_j = M^{-1} v_j):
-//   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w
+//   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w (FP32 copies
+//                  of V and w by default: the second pass corrects their error)
 //   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w
 //   k_fg_norm      w -= V h2, ||w||, Givens rotation, residual estimate, stop decision
 //   k_fg_next      v_{j+1} = w / ||w||
@@ -146,8 +147,11 @@ __global__ void k_fg_resid(CsrDev A, FgDev f, const double* __restrict__ b, cons
 __global__ void k_fg_scale0(FgDev f, int n) {
     if (f.ctl->cycle_done) return;
     const double inv = 1.0 / f.ctl->beta;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-        f.V[r] = f.V[r] * inv;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const double v = f.V[r] * inv;
+        f.V[r] = v;
+        if (f.V32) f.V32[r] = (float)v;
+    }
 }
 
 // Gram-Schmidt kernels. Each CTA owns a row slice (cta_rows). FP64 arithmetic is the
@@ -206,6 +210,56 @@ __device__ __forceinline__ void cta_dots(const double* __restrict__ V, int64_t l
     __syncthreads();
 }
 
+__device__ __forceinline__ float4 ld4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// The dots of the first Gram-Schmidt pass from the FP32 copies (FgDev::V32, w32): FP32
+// products summed per lane and warp in FP32, the CTA's partial per vector in FP64. The
+// second pass, in FP64, removes from w what this estimate leaves (about 6e-8 ||w||), so
+// only the coefficients' first ~7 digits matter here. Same task split as cta_dots, four
+// rows per lane and load (slices start at multiples of 64 rows: 16-byte aligned).
+__device__ __forceinline__ void cta_dots32(const float* __restrict__ V32, int64_t ld, const float* w32, int r0,
+                                           int r1, int j, double* spart, double* stask) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nsub = max(1, nw / (j + 1));
+    const int len = ((r1 - r0 + nsub - 1) / nsub + 127) / 128 * 128;
+    for (int task = warp; task < (j + 1) * nsub; task += nw) {
+        const int i = task / nsub, sb = task - i * nsub;
+        const int a = min(r1, r0 + sb * len), b = min(r1, a + len);
+        const float* __restrict__ v = V32 + (size_t)i * ld;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int r = a + 4 * lane;
+        for (; r + 131 < b; r += 256) {
+            const float4 x0 = ld4f(v + r), y0 = ld4f(w32 + r), x1 = ld4f(v + r + 128), y1 = ld4f(w32 + r + 128);
+            acc[0] += x0.x * y0.x;
+            acc[1] += x0.y * y0.y;
+            acc[2] += x0.z * y0.z;
+            acc[3] += x0.w * y0.w;
+            acc[4] += x1.x * y1.x;
+            acc[5] += x1.y * y1.y;
+            acc[6] += x1.z * y1.z;
+            acc[7] += x1.w * y1.w;
+        }
+        for (; r + 3 < b; r += 128) {
+            const float4 x0 = ld4f(v + r), y0 = ld4f(w32 + r);
+            acc[0] += x0.x * y0.x;
+            acc[1] += x0.y * y0.y;
+            acc[2] += x0.z * y0.z;
+            acc[3] += x0.w * y0.w;
+        }
+        for (int q = r; q < b && q < r + 4; q++) acc[0] += v[q] * w32[q];  // the slice's last rows
+        float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        t = warp_sum_t<float>(t);
+        if (lane == 0) stask[task] = (double)t;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double t = 0.0;
+        for (int sb = 0; sb < nsub; sb++) t += stask[i * nsub + sb];
+        spart[i] = t;
+    }
+    __syncthreads();
+}
+
 // w[r] -= sum_i h[i] V_i[r] over the CTA's rows (i = 0..j in order); optionally the
 // partial ||w||^2
 __device__ __forceinline__ void cta_update(const double* __restrict__ V, int64_t ld, double* w, const double* hh,
@@ -250,8 +304,8 @@ __device__ __forceinline__ void cta_partials(const double* spart, int j, double*
     for (int u = threadIdx.x; u <= j; u += blockDim.x) part[(size_t)u * G + blockIdx.x] = spart[u];
 }
 
-// w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w; the last CTA stores h1 in
-// column j of H
+// w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w (from the FP32 copies when they
+// exist); the last CTA stores h1 in column j of H
 template <int VL>
 __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
     __shared__ double stask[kMaxTasks];
@@ -265,10 +319,16 @@ __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
         const int r = base + sub;
         const bool valid = r < r1;
         const double s = row_dot<VL>(A, r, valid, zj, sl);
-        if (valid && sl == 0) f.w[r] = s;
+        if (valid && sl == 0) {
+            f.w[r] = s;
+            if (f.w32) f.w32[r] = (float)s;
+        }
     }
     __syncthreads();
-    cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
+    if (f.V32)
+        cta_dots32(f.V32, f.ld, f.w32, r0, r1, j, spart, stask);
+    else
+        cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
     cta_partials(spart, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, j + 1, f.H + (size_t)j * (f.m + 1));
@@ -357,8 +417,12 @@ __global__ void k_fg_next(FgDev f, int n, int j) {
     if (f.ctl->cycle_done) return;
     const double inv = 1.0 / __ldcg(f.hnext);
     double* vn = f.V + (size_t)(j + 1) * f.ld;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-        vn[r] = f.w[r] * inv;
+    float* vn32 = f.V32 ? f.V32 + (size_t)(j + 1) * f.ld : nullptr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const double v = f.w[r] * inv;
+        vn[r] = v;
+        if (vn32) vn32[r] = (float)v;
+    }
 }
 
 // y = R^{-1} g (every CTA, redundantly); x += Z y on the CTA's rows

@@ -581,6 +581,31 @@ def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):
     h.close()
 
 
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "cuts3d", "rand"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gs_first_pass_in_fp32_keeps_fp64_fgmres(ilu, name, prec):
+    """The first Gram-Schmidt pass's coefficients from FP32 copies of V and w, corrected by
+    the FP64 second pass: the same iteration count as both passes in FP64 (+-1), the same
+    solution within 1e-6, and with the FP64 preconditioner the oracle's count within +-1."""
+    pr = _prob(name)
+    cfg = CONFIGS[2]
+    b = _dev(pr.b)
+    out = {}
+    for mode in (True, False):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, gs_first_fp32=mode, **cfg))
+        x = torch.zeros_like(b)
+        info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=3000)
+        assert info["status"] == 0 and info["rel_res_true"] <= 1e-8, info
+        out[mode] = (info["iters"], x.cpu().numpy())
+        h.close()
+    (i32, x32), (i64, x64) = out[True], out[False]
+    assert abs(i32 - i64) <= 1, (i32, i64)
+    assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64)
+    if prec == "fp64":
+        ref = O.Oracle.from_problem(pr, **cfg).fgmres(pr.b, rtol=1e-8, restart=30, maxit=3000)
+        assert abs(i32 - ref["iters"]) <= 1, (i32, ref["iters"])
+
+
 def test_restart_limit(ilu):
     pr = _prob("poisson64")
     h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp64", **CONFIGS[0]))
