@@ -118,12 +118,16 @@ typedef struct {
                              consumer cycles (default), 1 = levels only, 2 = chains. Chains run
                              rows that need only the previous row of their chain as warp scans
                              (stream_layout.h); results agree with the level schedule to rounding. */
-    int32_t gs_first_fp32;/* gmres_solve: 1 (default) = the first of the two classical Gram-Schmidt
-                             passes forms its coefficients h1 = V^T w from FP32 copies of V and w;
-                             w -= V h1, the second pass h2 = V^T w, w -= V h2 and H = h1 + h2 stay
-                             FP64, so the Arnoldi relation A z_j = V H_j + w holds to FP64
-                             rounding and the second pass removes the first pass's FP32 error
-                             (about 6e-8 ||w||) from w. 0 = both passes in FP64. */
+    int32_t gs_precision; /* gmres_solve, arithmetic of the two classical Gram-Schmidt passes of
+                             each Arnoldi step (Sec. 4.1.1): 0 = both in FP64; 1 = the first
+                             pass's coefficients h1 = V^T w from FP32 copies of V and w, then
+                             w -= V h1 and the second pass in FP64 (the second pass removes the
+                             ~6e-8 ||w|| the estimate leaves); 2 (default) = as 1, and the second
+                             pass's update w -= V h2 from the FP32 copy of V with FP32 products:
+                             h2 is then ~6e-8 ||w||, so the update's error, ~1e-7 ||V h2||, is
+                             ~1e-14 ||w||, the size of FP64 rounding in the full update. The
+                             coefficients H = h1 + h2, w itself, ||w||, the Givens rotations,
+                             the solution update and the true residual are FP64 in every mode. */
 } ilu_opts;
 
 typedef struct {
@@ -256,6 +260,13 @@ ilu_status ilu_get_stats(void* h, int64_t* out);
    capturing and instantiating the cycle graph (0 when the handle's graph was reused).
    out must hold 4 values. Errors: ILU_ERR_ARG for a null pointer. */
 ilu_status ilu_get_times(void* h, double* out);
+
+/* The Krylov basis of the handle's last gmres_solve (its last cycle): which = 0 the
+   orthonormal vectors v_0..v_{k-1} (k <= restart + 1), which = 1 the preconditioned
+   vectors z_0..z_{k-1} (k <= restart); out: HOST double[k * n], vector i at out + i * n, in
+   the original ordering. Vectors past the cycle's last step hold stale values. Synchronises
+   the stream. Errors: ILU_ERR_ARG (null pointers, which or k out of range, no solve yet). */
+ilu_status ilu_get_krylov(void* h, int32_t which, int32_t k, double* out);
 
 /* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device
    consumes it): program 0 = block Jacobi, 1 = forward (L_B, the W rows and S~), 2 = local

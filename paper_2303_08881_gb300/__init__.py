@@ -47,7 +47,7 @@ class ilu_opts(C.Structure):
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
                 ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32),
                 ("fill_level", C.c_int32), ("l1_block", C.c_int32), ("chain_sched", C.c_int32),
-                ("gs_first_fp32", C.c_int32)]
+                ("gs_precision", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -90,6 +90,7 @@ def lib():
             "ilu_get_stream": (I, [P, I, P, P, P]),
             "ilu_inner_solve_noalloc": (I, [P, P, P]),
             "ilu_measure_fp64_peak": (I, [P, P]),
+            "ilu_get_krylov": (I, [P, I, I, P]),
             "ilu_measure_level_latency": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
@@ -148,7 +149,7 @@ class Opts:
     fill_level: int = 0             # k > 0: ILU(k) / MILU(k) in the level-k fill pattern
     l1_block: bool = False          # block Jacobi: l1-BJ diagonal augmentation
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
-    gs_first_fp32: bool = True      # FGMRES: first Gram-Schmidt pass's coefficients from FP32 copies
+    gs_precision: str = "mixed2"    # FGMRES Gram-Schmidt: "fp64", "mixed1" (FP32 first-pass dots), "mixed2" (+ FP32 second update)
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -172,7 +173,7 @@ class Opts:
         o.fill_level = int(self.fill_level)
         o.l1_block = int(bool(self.l1_block))
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]
-        o.gs_first_fp32 = int(bool(self.gs_first_fp32))
+        o.gs_precision = {"fp64": 0, "mixed1": 1, "mixed2": 2}[self.gs_precision]
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:
@@ -313,6 +314,13 @@ class Handle:
                                     meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
         return dict(blob=blob, ch0=ch0, chunk=int(meta[1]), rw=int(meta[2]), val_bytes=int(meta[3]),
                     threads=int(meta[4]), x_bytes=int(meta[5]))
+
+    def krylov(self, which: str, k: int) -> np.ndarray:
+        """The last solve's basis vectors v_0..v_{k-1} ("V") or z_0..z_{k-1} ("Z"), k x n."""
+        out = np.empty((k, self.n))
+        _check(lib().ilu_get_krylov(self.ptr, {"V": 0, "Z": 1}[which], int(k), out.ctypes.data_as(C.c_void_p)),
+               "ilu_get_krylov")
+        return out
 
     def inner_solve_noalloc(self, gp, y):
         """ilu_inner_solve with the library's fixed workspace instead of the handle's

@@ -278,7 +278,8 @@ ilu_status ensure_fgmres(Handle& h, int m) {
         return map_err(e);
     f.V32 = nullptr;
     f.w32 = nullptr;
-    if (h.o.gs_first_fp32) {
+    f.upd32 = h.o.gs_precision == 2 ? 1 : 0;
+    if (h.o.gs_precision > 0) {
         f.V32 = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
         f.w32 = h.alloc<float>((size_t)f.ld, &e);
         if (!f.V32 || !f.w32) return map_err(e);
@@ -439,7 +440,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->fill_level = 0;
     o->l1_block = 0;
     o->chain_sched = 0;
-    o->gs_first_fp32 = 1;
+    o->gs_precision = 2;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -503,7 +504,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
         (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
-        o.gs_first_fp32 < 0 || o.gs_first_fp32 > 1) {
+        o.gs_precision < 0 || o.gs_precision > 2) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -843,6 +844,17 @@ ilu_status ilu_get_times(void* hp, double* out) {
     out[1] = h->device_ms;
     out[2] = h->solve_ms_last;
     out[3] = h->graph_ms_last;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_krylov(void* hp, int32_t which, int32_t k, double* out) {
+    if (!hp || !out || which < 0 || which > 1 || k < 1) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->o.analysis_only || !h->fg.V || k > (which == 0 ? h->fg_m + 1 : h->fg_m)) return ILU_ERR_ARG;
+    const double* src = which == 0 ? h->fg.V : h->fg.Z;
+    CK(cudaMemcpy2DAsync(out, (size_t)h->n * sizeof(double), src, (size_t)h->fg.ld * sizeof(double),
+                         (size_t)h->n * sizeof(double), (size_t)k, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
     return ILU_OK;
 }
 

@@ -140,6 +140,7 @@ struct FgDev {
     FgCtl* ctl;
     float* V32;     // (m+1) x ld: FP32 copy of V for the first Gram-Schmidt pass (null: FP64 pass)
     float* w32;     // n: FP32 copy of w = A z_j for that pass
+    int32_t upd32;  // the second pass's update w -= V h2 from V32 with FP32 products
     int32_t m, G;
     int64_t ld;     // leading dimension of V and Z: n rounded up to 64 (512-byte rows)
 };

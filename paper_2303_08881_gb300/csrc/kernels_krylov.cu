@@ -11,7 +11,8 @@
 //   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w (FP32 copies
 //                  of V and w by default: the second pass corrects their error)
 //   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w
-//   k_fg_norm      w -= V h2, ||w||, Givens rotation, residual estimate, stop decision
+//   k_fg_norm      w -= V h2 (from the FP32 copy of V by default: h2 is then small), ||w||,
+//                  Givens rotation, residual estimate, stop decision
 //   k_fg_next      v_{j+1} = w / ||w||
 #include <algorithm>
 
@@ -299,6 +300,60 @@ __device__ __forceinline__ void cta_update(const double* __restrict__ V, int64_t
     if (nrm2) *nrm2 = acc;
 }
 
+// w[r] -= sum_i hf[i] V32_i[r] with FP32 products summed in FP32 (i = 0..j in order), the
+// correction subtracted from w in FP64; optionally the partial ||w||^2 in FP64. For the second
+// Gram-Schmidt pass only, whose coefficients are ~6e-8 ||w|| after an FP32 first pass: the
+// correction's own error, ~1e-7 of it, is then ~1e-14 ||w||. Four rows per thread (float4 of
+// the copy, two double2 of w; slices start at multiples of 64 rows).
+__device__ __forceinline__ void cta_update32(const float* __restrict__ V32, int64_t ld, double* w, const float* hf,
+                                             int r0, int r1, int j, double* nrm2) {
+    double acc2 = 0.0;
+    for (int r = r0 + 4 * threadIdx.x; r < r1; r += 4 * blockDim.x) {
+        if (r + 3 < r1) {
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            int i = 0;
+            for (; i + 8 <= j + 1; i += 8) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) v[u] = ld4f(V32 + (size_t)(i + u) * ld + r);
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float hv = hf[i + u];
+                    c.x += hv * v[u].x;
+                    c.y += hv * v[u].y;
+                    c.z += hv * v[u].z;
+                    c.w += hv * v[u].w;
+                }
+            }
+            for (; i <= j; i++) {
+                const float4 v = ld4f(V32 + (size_t)i * ld + r);
+                const float hv = hf[i];
+                c.x += hv * v.x;
+                c.y += hv * v.y;
+                c.z += hv * v.z;
+                c.w += hv * v.w;
+            }
+            double2 a = ld2(w + r), b = ld2(w + r + 2);
+            a.x -= (double)c.x;
+            a.y -= (double)c.y;
+            b.x -= (double)c.z;
+            b.y -= (double)c.w;
+            *reinterpret_cast<double2*>(w + r) = a;
+            *reinterpret_cast<double2*>(w + r + 2) = b;
+            acc2 += (a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y);
+        } else {
+            for (int q = r; q < r1; q++) {
+                float c = 0.f;
+                for (int i = 0; i <= j; i++) c += hf[i] * V32[(size_t)i * ld + q];
+                const double x = w[q] - (double)c;
+                w[q] = x;
+                acc2 += x * x;
+            }
+        }
+    }
+    if (nrm2) *nrm2 = acc2;
+}
+
 // the CTA's partials of coefficients 0..j into part[u * G + cta]
 __device__ __forceinline__ void cta_partials(const double* spart, int j, double* part, int G) {
     for (int u = threadIdx.x; u <= j; u += blockDim.x) part[(size_t)u * G + blockIdx.x] = spart[u];
@@ -363,14 +418,21 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
 __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     __shared__ double red[32];
     __shared__ double hh[kMaxJ + 1];
+    __shared__ float hf[kMaxJ + 1];
     __shared__ double tot[1];
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
-    for (int u = threadIdx.x; u <= j; u += blockDim.x) hh[u] = __ldcg(f.h2 + u);
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) {
+        hh[u] = __ldcg(f.h2 + u);
+        hf[u] = (float)hh[u];
+    }
     __syncthreads();
     double acc = 0.0;
-    cta_update(f.V, f.ld, f.w, hh, r0, r1, j, &acc);
+    if (f.upd32)
+        cta_update32(f.V32, f.ld, f.w, hf, r0, r1, j, &acc);
+    else
+        cta_update(f.V, f.ld, f.w, hh, r0, r1, j, &acc);
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
     if (!last_cta(&f.ctl->counter)) return;

@@ -583,27 +583,54 @@ def test_fgmres_matches_oracle(ilu, name, cfg, prec, restart, graphs):
 
 @pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d", "cuts3d", "rand"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_gs_first_pass_in_fp32_keeps_fp64_fgmres(ilu, name, prec):
-    """The first Gram-Schmidt pass's coefficients from FP32 copies of V and w, corrected by
-    the FP64 second pass: the same iteration count as both passes in FP64 (+-1), the same
-    solution within 1e-6, and with the FP64 preconditioner the oracle's count within +-1."""
+def test_gs_mixed_precision_keeps_fp64_fgmres(ilu, name, prec):
+    """The first Gram-Schmidt pass's coefficients from FP32 copies of V and w (corrected by the
+    FP64 second pass), and the second pass's small update from the FP32 copy of V: the same
+    iteration count as both passes in FP64 (+-1), the same solution within 1e-6, and with the
+    FP64 preconditioner the oracle's count within +-1."""
     pr = _prob(name)
     cfg = CONFIGS[2]
     b = _dev(pr.b)
     out = {}
-    for mode in (True, False):
-        h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, gs_first_fp32=mode, **cfg))
+    for mode in ("mixed2", "mixed1", "fp64"):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, gs_precision=mode, **cfg))
         x = torch.zeros_like(b)
         info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=3000)
         assert info["status"] == 0 and info["rel_res_true"] <= 1e-8, info
         out[mode] = (info["iters"], x.cpu().numpy())
         h.close()
-    (i32, x32), (i64, x64) = out[True], out[False]
-    assert abs(i32 - i64) <= 1, (i32, i64)
-    assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64)
+    i64, x64 = out["fp64"]
+    for mode in ("mixed1", "mixed2"):
+        i32, x32 = out[mode]
+        assert abs(i32 - i64) <= 1, (mode, i32, i64)
+        assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64), mode
     if prec == "fp64":
         ref = O.Oracle.from_problem(pr, **cfg).fgmres(pr.b, rtol=1e-8, restart=30, maxit=3000)
-        assert abs(i32 - ref["iters"]) <= 1, (i32, ref["iters"])
+        for mode in out:
+            assert abs(out[mode][0] - ref["iters"]) <= 1, (mode, out[mode][0], ref["iters"])
+
+
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "conv3d"])
+def test_gs_mixed_precision_keeps_the_basis_orthonormal(ilu, name):
+    """One FGMRES(40) cycle (FP32 preconditioner), then the basis v_1..v_39 from the device (the
+    end of a cycle leaves the new true residual in v_0): the loss of orthogonality
+    max |V V^T - I| of the mixed-precision Gram-Schmidt forms stays at the level of the
+    all-FP64 form (FP64 rounding, well below 1e-12)."""
+    pr = _prob(name)
+    b = _dev(pr.b)
+    m = 40
+    loss = {}
+    for mode in ("fp64", "mixed1", "mixed2"):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(gs_precision=mode, **CONFIGS[2]))
+        x = torch.zeros_like(b)
+        info = ilu.gmres_solve(h, b, x, rtol=1e-30, restart=m, maxit=m)
+        assert info["iters"] == m
+        V = h.krylov("V", m)[1:]
+        loss[mode] = np.abs(V @ V.T - np.eye(m - 1)).max()
+        h.close()
+    assert loss["fp64"] < 1e-13, loss
+    for mode in ("mixed1", "mixed2"):
+        assert loss[mode] <= max(10 * loss["fp64"], 1e-14) and loss[mode] < 1e-12, loss
 
 
 def test_restart_limit(ilu):
