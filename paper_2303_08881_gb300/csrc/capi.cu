@@ -163,6 +163,7 @@ ilu_status device_setup_t(Handle& h) {
             StreamBufs& B = h.sb[id];
             CK(upload(h, &B.blob, S.blob));
             CK(upload(h, &B.ch0, S.ch0));
+            CK(upload(h, &B.order, S.order));
             B.chunk = S.chunk;
             B.nt = S.nt;
             B.rw = S.rw;

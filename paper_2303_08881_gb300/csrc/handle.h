@@ -44,11 +44,14 @@ struct StreamHost {
     int64_t max_scan_waves = 0;                 // scan waves of the subdomain program with most
     int64_t max_steps = 0;                      // barriers + scan waves, largest over the subdomains
     int64_t chain_sections = 0;                 // subdomains whose chain section runs as chains
+    std::vector<int32_t> order;                 // p: subdomains by descending estimated cost (the
+                                                // launch order of the apply kernels)
 };
 
 struct StreamBufs {
     uint8_t* blob = nullptr;
     int32_t* ch0 = nullptr;
+    int32_t* order = nullptr;
     uint32_t chunk = 8192;
     int nt = 32;
     int rw = 4;

@@ -30,9 +30,20 @@ template <class T>
 struct StreamDev {
     const uint8_t* blob;
     const int32_t* ch0;
+    const int32_t* order;  // p: subdomains by descending estimated cost
     uint32_t chunk;
     int nt;
 };
+
+// The subdomain of this CTA in the block-Jacobi, forward and backward kernels: the CTAs take
+// the subdomains most expensive first. When there are more subdomains than resident CTAs,
+// the block scheduler hands out CTAs in index order as SMs free up, so this is longest-first
+// list scheduling of uneven subdomains onto the SMs (the kernels of the inner solve keep one
+// CTA per subdomain in index order: its grid barriers need every CTA resident anyway).
+template <class T>
+__device__ __forceinline__ int sub_of_cta(const StreamDev<T>& S) {
+    return S.order ? S.order[blockIdx.x] : (int)blockIdx.x;
+}
 
 struct RingCfg {
     int nst;              // stages
@@ -501,7 +512,7 @@ template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_bj_s(SubDev sd, StreamDev<T> S, RingCfg cfg, const double* __restrict__ r,
                                               double* __restrict__ z, T* xg, const int32_t* done) {
     if (done && *done) return;
-    const int s = blockIdx.x;
+    const int s = sub_of_cta(S);
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0;
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     ring_start(S, s, sm, cfg.nst);
@@ -519,7 +530,7 @@ __global__ void __launch_bounds__(256) k_fwd_s(SubDev sd, StreamDev<T> S, RingCf
                                                const int32_t* done) {
     __shared__ double red[32];
     if (done && *done) return;
-    const int s = blockIdx.x;
+    const int s = sub_of_cta(S);
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     ring_start(S, s, sm, cfg.nst);
@@ -923,7 +934,7 @@ __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCf
                                                double* __restrict__ z, T* xg, const int32_t* done) {
     __shared__ double tt[kMaxInner];
     if (done && *done) return;
-    const int s = blockIdx.x;
+    const int s = sub_of_cta(S);
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     ring_start(S, s, sm, cfg.nst);
@@ -1012,6 +1023,7 @@ static StreamDev<T> sdev(const Handle& h, int id) {
     StreamDev<T> d;
     d.blob = h.sb[id].blob;
     d.ch0 = h.sb[id].ch0;
+    d.order = h.sb[id].order;
     d.chunk = h.sb[id].chunk;
     d.nt = h.sb[id].nt;
     return d;

@@ -389,6 +389,8 @@ constexpr uint8_t kLinkCol = 1, kLinkSelf = 2;
 // the rest of a level. (Measured on GB300: a 48-row level with its barrier takes ~400
 // cycles, a chained row ~70.)
 constexpr double kCostWave = 70.0, kCostScanWave = 260.0, kCostBarrier = 330.0;
+// a chunk of the ring: its copy and its hand-over (used to order the subdomains by cost)
+constexpr double kCostChunk = 1500.0;
 // the shortest chain worth a scan phase
 constexpr int32_t kMinChain = 3;
 
@@ -679,6 +681,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
         rawvec<int32_t> vsrc, dsrc;
         int64_t waves = 0, segments = 0, records = 0, skips = 0, max_barriers = 0, max_levels_sub = 0;
         int64_t max_scan_waves = 0, max_steps = 0, chain_sections = 0;
+        std::vector<double> cost;  // estimated consumer cycles of each subdomain of the range
         bool ok = true;
     };
     std::vector<Frag> frag(16);
@@ -934,6 +937,7 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
                 }
             }
             F.nch.push_back((int32_t)nchunks);
+            F.cost.push_back(schedule_cost(waves, 0) + kCostChunk * (double)nchunks);
         }
     });
     // the fragments one after the other: arrays sized once, one host thread per fragment
@@ -956,6 +960,13 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
         S.max_scan_waves = std::max(S.max_scan_waves, F.max_scan_waves);
         S.max_steps = std::max(S.max_steps, F.max_steps);
         S.chain_sections += F.chain_sections;
+    }
+    {   // launch order: the most expensive subdomain first (ties: lower index)
+        std::vector<double> cost;
+        for (int t = 0; t < nfrag; t++) cost.insert(cost.end(), frag[t].cost.begin(), frag[t].cost.end());
+        S.order.resize(cost.size());
+        for (size_t i = 0; i < cost.size(); i++) S.order[i] = (int32_t)i;
+        std::stable_sort(S.order.begin(), S.order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
     }
     S.blob.resize(nb[nfrag]);
     S.voff.resize(nv[nfrag]);
