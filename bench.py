@@ -468,6 +468,8 @@ def main():
                     help="preconditioner precision (bf16: bfloat16 factor values, FP32 arithmetic)")
     ap.add_argument("--threads", type=int, default=0, help="consumer-group threads override (0 = auto)")
     ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="measure the consumer-group size of each streamed program at setup (1) or use the rule (0)")
     ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_leg:
@@ -515,9 +517,11 @@ def main():
 
     sol["block_threads"] = args.threads
     sol["kernel_path"] = args.kernel_path
+    sol["autotune"] = bool(args.autotune) and not args.threads
     t0 = time.perf_counter()
     h = ilu.ilu_setup_problem(pr, ilu.Opts(**sol))
     setup_s = time.perf_counter() - t0
+    tuning = h.tuning()
     b = torch.from_numpy(pr.b).to(dev)
     x = torch.zeros_like(b)
     if args.mode == "apply":
@@ -690,7 +694,7 @@ def main():
             "config": bench_config(cfg, dict(sol, restart=restart), pr, world),
             "roofline": roofline, "roofline_pc_apply": roofline_pc,
             "time_to_rtol_s": time_to_rtol, "iters": info["iters"], "rel_res_true": relres,
-            "err_vs_x_true": err_true, "setup_s": setup_s, "fp64_peak_tflops": fp64_peak,
+            "err_vs_x_true": err_true, "setup_s": setup_s, "tuning": tuning, "fp64_peak_tflops": fp64_peak,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
             "clocks": clk.summary(), "mixed_vs_fp64": mixed, "pc_apply": pc_apply, "latency": latency,
             "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in c.items()}

@@ -128,6 +128,13 @@ typedef struct {
                              ~1e-14 ||w||, the size of FP64 rounding in the full update. The
                              coefficients H = h1 + h2, w itself, ||w||, the Givens rotations,
                              the solution update and the true residual are FP64 in every mode. */
+    int32_t autotune;     /* streamed path: 1 = ilu_setup measures, for each streamed program, the
+                             apply time with consumer groups of 32, 64, 96 and 128 threads
+                             (CUDA events on opts.stream, the program rebuilt for each) and keeps
+                             the fastest; the choice is remembered for the process, keyed by the
+                             structure of the problem, so a later setup of the same structure
+                             builds it directly. 0 (default) = the level-width rule. Ignored with
+                             block_threads != 0. See ilu_get_tuning. */
 } ilu_opts;
 
 typedef struct {
@@ -267,6 +274,13 @@ ilu_status ilu_get_times(void* h, double* out);
    the original ordering. Vectors past the cycle's last step hold stale values. Synchronises
    the stream. Errors: ILU_ERR_ARG (null pointers, which or k out of range, no solve yet). */
 ilu_status ilu_get_krylov(void* h, int32_t which, int32_t k, double* out);
+
+/* What ilu_setup chose for the streamed programs (0 block Jacobi, 1 forward, 2 local Schur,
+   3 backward): nt[i] consumer threads of program i (0 if unused); ms[4 * i + c] the apply
+   time measured with candidate c = 0..3 (32, 64, 96, 128 threads; 0 where not measured);
+   *state = 0 level-width rule, 1 measured by this setup, 2 taken from an earlier setup of
+   the same structure. Host-side only. Errors: ILU_ERR_ARG for a null pointer. */
+ilu_status ilu_get_tuning(void* h, int32_t* nt, double* ms, int32_t* state);
 
 /* Shape of one TMA-streamed level program (the level schedule of Sec. 3.1 as the device
    consumes it): program 0 = block Jacobi, 1 = forward (L_B, the W rows and S~), 2 = local

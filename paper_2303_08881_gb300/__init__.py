@@ -47,7 +47,7 @@ class ilu_opts(C.Structure):
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
                 ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32),
                 ("fill_level", C.c_int32), ("l1_block", C.c_int32), ("chain_sched", C.c_int32),
-                ("gs_precision", C.c_int32)]
+                ("gs_precision", C.c_int32), ("autotune", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -91,6 +91,7 @@ def lib():
             "ilu_inner_solve_noalloc": (I, [P, P, P]),
             "ilu_measure_fp64_peak": (I, [P, P]),
             "ilu_get_krylov": (I, [P, I, I, P]),
+            "ilu_get_tuning": (I, [P, P, P, P]),
             "ilu_measure_level_latency": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
@@ -150,6 +151,7 @@ class Opts:
     l1_block: bool = False          # block Jacobi: l1-BJ diagonal augmentation
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
     gs_precision: str = "mixed2"    # FGMRES Gram-Schmidt: "fp64", "mixed1" (FP32 first-pass dots), "mixed2" (+ FP32 second update)
+    autotune: bool = False          # measure the consumer-group size of each streamed program at setup
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -174,6 +176,7 @@ class Opts:
         o.l1_block = int(bool(self.l1_block))
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]
         o.gs_precision = {"fp64": 0, "mixed1": 1, "mixed2": 2}[self.gs_precision]
+        o.autotune = int(bool(self.autotune))
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:
@@ -314,6 +317,20 @@ class Handle:
                                     meta.ctypes.data_as(C.c_void_p)), "ilu_get_stream")
         return dict(blob=blob, ch0=ch0, chunk=int(meta[1]), rw=int(meta[2]), val_bytes=int(meta[3]),
                     threads=int(meta[4]), x_bytes=int(meta[5]))
+
+    def tuning(self) -> dict:
+        """Consumer threads chosen per streamed program, the measured apply times of the
+        candidates (32, 64, 96, 128 threads; 0 = not measured) and how they were chosen."""
+        nt = np.zeros(4, np.int32)
+        ms = np.zeros(16)
+        st = C.c_int32(0)
+        _check(lib().ilu_get_tuning(self.ptr, nt.ctypes.data_as(C.c_void_p), ms.ctypes.data_as(C.c_void_p),
+                                    C.byref(st)), "ilu_get_tuning")
+        names = ["bj", "fwd", "s", "bwd"]
+        return {"state": ["rule", "measured", "remembered"][st.value],
+                "threads": {names[i]: int(nt[i]) for i in range(4) if nt[i]},
+                "apply_ms": {names[i]: {c: float(ms[4 * i + k]) for k, c in enumerate((32, 64, 96, 128))
+                                        if ms[4 * i + k] > 0} for i in range(4) if nt[i]}}
 
     def krylov(self, which: str, k: int) -> np.ndarray:
         """The last solve's basis vectors v_0..v_{k-1} ("V") or z_0..z_{k-1} ("Z"), k x n."""

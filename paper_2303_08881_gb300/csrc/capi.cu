@@ -108,6 +108,41 @@ ilu_status upload_prog(Handle& h, int id) {
     return ILU_OK;
 }
 
+// Device copy of the streamed program id built on the host (h.sh[id]): the chunks, the
+// per-subdomain chunk offsets and launch order, and the values and pivot inverses packed
+// into the chunks from the FP64 factors on the device. Replaces (and frees) an earlier copy;
+// the host chunks are freed once packed.
+template <class T>
+ilu_status upload_stream(Handle& h, int id) {
+    StreamHost& S = h.sh[id];
+    if (S.ch0.empty()) return ILU_OK;
+    StreamBufs& B = h.sb[id];
+    for (void* q : {(void*)B.blob, (void*)B.ch0, (void*)B.order})
+        if (q) h.release(q);
+    B = StreamBufs{};
+    CK(upload(h, &B.blob, S.blob));
+    CK(upload(h, &B.ch0, S.ch0));
+    CK(upload(h, &B.order, S.order));
+    B.chunk = S.chunk;
+    B.nt = S.nt;
+    B.rw = S.rw;
+    int64_t *dvoff = nullptr, *ddoff = nullptr;
+    int32_t *dvsrc = nullptr, *ddsrc = nullptr;
+    CK(upload(h, &dvoff, S.voff));
+    CK(upload(h, &dvsrc, S.vsrc));
+    CK(upload(h, &ddoff, S.doff));
+    CK(upload(h, &ddsrc, S.dsrc));
+    CK(launch_pack_stream<T>(S, dvoff, dvsrc, ddoff, ddsrc, h.d_vals, B.blob, h.st));
+    CK(cudaStreamSynchronize(h.st));
+    for (void* q : {(void*)dvoff, (void*)dvsrc, (void*)ddoff, (void*)ddsrc}) h.release(q);
+    decltype(S.blob)().swap(S.blob);
+    decltype(S.voff)().swap(S.voff);
+    decltype(S.doff)().swap(S.doff);
+    decltype(S.vsrc)().swap(S.vsrc);
+    decltype(S.dsrc)().swap(S.dsrc);
+    return ILU_OK;
+}
+
 template <class T>
 ilu_status device_setup_t(Handle& h) {
     cudaError_t e = cudaSuccess;
@@ -158,29 +193,8 @@ ilu_status device_setup_t(Handle& h) {
         h.d_tbuf = h.alloc<T>((size_t)std::max(h.n2, 1), &e);
         if (!h.d_tbuf) return map_err(e);
         for (int id = 0; id < PR_COUNT; id++) {
-            StreamHost& S = h.sh[id];
-            if (S.ch0.empty()) continue;
-            StreamBufs& B = h.sb[id];
-            CK(upload(h, &B.blob, S.blob));
-            CK(upload(h, &B.ch0, S.ch0));
-            CK(upload(h, &B.order, S.order));
-            B.chunk = S.chunk;
-            B.nt = S.nt;
-            B.rw = S.rw;
-            int64_t *dvoff = nullptr, *ddoff = nullptr;
-            int32_t *dvsrc = nullptr, *ddsrc = nullptr;
-            CK(upload(h, &dvoff, S.voff));
-            CK(upload(h, &dvsrc, S.vsrc));
-            CK(upload(h, &ddoff, S.doff));
-            CK(upload(h, &ddsrc, S.dsrc));
-            CK(launch_pack_stream<T>(S, dvoff, dvsrc, ddoff, ddsrc, h.d_vals, B.blob, h.st));
-            CK(cudaStreamSynchronize(h.st));
-            for (void* q : {(void*)dvoff, (void*)dvsrc, (void*)ddoff, (void*)ddsrc}) h.release(q);
-            decltype(S.blob)().swap(S.blob);
-            decltype(S.voff)().swap(S.voff);
-            decltype(S.doff)().swap(S.doff);
-            decltype(S.vsrc)().swap(S.vsrc);
-            decltype(S.dsrc)().swap(S.dsrc);
+            ilu_status us = upload_stream<T>(h, id);
+            if (us != ILU_OK) return us;
         }
     }
     if (h.variant == ILU_VARIANT_BJ) {
@@ -384,6 +398,84 @@ cudaError_t apply_any(Handle& h, const double* r, double* z, const int32_t* done
                                      : apply_t<double>(h, r, z, done, st, cap);
 }
 
+// The autotuner (ilu_opts.autotune). For each streamed program in turn, the program is
+// rebuilt with consumer groups of 32, 64, 96 and 128 threads; each version is timed as the
+// mean of five applies (after one untimed apply) with CUDA events on the handle's stream,
+// and the fastest is kept (a candidate replaces the current one only when at least 2 %
+// faster). The programs of the handle's variant: block Jacobi; forward, local Schur and
+// backward; or, for the multiplicative variant, the smoother, forward and backward.
+template <class T>
+ilu_status autotune_t(Handle& h) {
+    std::vector<int> ids;
+    for (int id = 0; id < PR_COUNT; id++)
+        if (!h.sh[id].ch0.empty()) ids.push_back(id);
+    if (ids.empty()) return ILU_OK;
+    cudaError_t e = cudaSuccess;
+    double* r = h.alloc<double>((size_t)std::max(h.n, 1), &e);
+    double* z = h.alloc<double>((size_t)std::max(h.n, 1), &e);
+    if (!r || !z) return map_err(e);
+    CK(cudaMemsetAsync(r, 0x3F, (size_t)std::max(h.n, 1) * sizeof(double), h.st));  // 0.49...
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timed = [&](double* ms) -> cudaError_t {
+        cudaError_t err = apply_any(h, r, z, nullptr, h.st);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, h.st);
+        for (int i = 0; i < 5 && err == cudaSuccess; i++) err = apply_any(h, r, z, nullptr, h.st);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, h.st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float f = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&f, e0, e1);
+        *ms = f / 5.0;
+        return err;
+    };
+    const int vb = (h.prec == ILU_PREC_FP64) ? 8 : 4;
+    const int valb = (h.prec == ILU_PREC_BF16_STORE) ? 2 : vb;
+    ilu_status st = ILU_OK;
+    int32_t chosen[PR_COUNT] = {0, 0, 0, 0, 0};
+    auto rebuild = [&](int id, int nt) -> bool {
+        StreamHost S;
+        S.nt = nt;
+        if (!build_stream(h.prog[id], h.p, h.idx_bytes, vb, valb, h.chunk, S, h.o.chain_sched) || S.nt != nt)
+            return false;
+        h.sh[id] = std::move(S);
+        st = upload_stream<T>(h, id);
+        return st == ILU_OK;
+    };
+    for (int id : ids) {
+        int best = h.sh[id].nt;
+        double best_ms = 0.0;
+        if ((e = timed(&best_ms)) != cudaSuccess) break;
+        for (int c = 0; c < kTuneCands; c++)
+            if (kTuneNt[c] == best) h.tune_ms[id][c] = best_ms;
+        int built = best;
+        for (int c = 0; c < kTuneCands && st == ILU_OK; c++) {
+            if (kTuneNt[c] == built || h.tune_ms[id][c] > 0.0) continue;
+            if (!rebuild(id, kTuneNt[c])) continue;
+            built = kTuneNt[c];
+            double ms = 0.0;
+            if ((e = timed(&ms)) != cudaSuccess) break;
+            h.tune_ms[id][c] = ms;
+            if (ms < 0.98 * best_ms) {
+                best_ms = ms;
+                best = kTuneNt[c];
+            }
+        }
+        if (e != cudaSuccess || st != ILU_OK) break;
+        if (built != best && !rebuild(id, best)) break;
+        chosen[id] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h.release(r);
+    h.release(z);
+    if (e != cudaSuccess) return map_err(e);
+    if (st != ILU_OK) return st;
+    tune_store(h.tune_key_v, chosen);
+    h.tune_state = 1;
+    return ILU_OK;
+}
+
 #define ILU2L_SCOPED(cls, nk, call)              \
     do {                                        \
         Scope sc_(h, cls, nk, st, cap);          \
@@ -442,6 +534,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->l1_block = 0;
     o->chain_sched = 0;
     o->gs_precision = 2;
+    o->autotune = 0;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -505,7 +598,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
         (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
-        o.gs_precision < 0 || o.gs_precision > 2) {
+        o.gs_precision < 0 || o.gs_precision > 2 || o.autotune < 0 || o.autotune > 1) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -564,6 +657,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
             }
         }
     }
+    if (s == ILU_OK && o.autotune && h->stream_path && !o.block_threads && h->tune_state == 0)
+        s = (h->prec != ILU_PREC_FP64) ? autotune_t<float>(*h) : autotune_t<double>(*h);
     if (s != ILU_OK) {
         ilu_free(h);
         return s;
@@ -845,6 +940,19 @@ ilu_status ilu_get_times(void* hp, double* out) {
     out[1] = h->device_ms;
     out[2] = h->solve_ms_last;
     out[3] = h->graph_ms_last;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_tuning(void* hp, int32_t* nt, double* ms, int32_t* state) {
+    if (!hp || !nt || !ms || !state) return ILU_ERR_ARG;
+    const Handle* h = (const Handle*)hp;
+    const int ids[4] = {PR_BJ, PR_FWDS, PR_S, PR_BWD};
+    for (int i = 0; i < 4; i++) {
+        const StreamHost& S = h->sh[ids[i]];
+        nt[i] = S.ch0.empty() ? 0 : S.nt;
+        for (int c = 0; c < kTuneCands; c++) ms[4 * i + c] = h->tune_ms[ids[i]][c];
+    }
+    *state = h->tune_state;
     return ILU_OK;
 }
 

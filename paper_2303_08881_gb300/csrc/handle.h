@@ -60,6 +60,14 @@ struct StreamBufs {
 // The introspection level sets (Handle::lev / nlev), built on the first call.
 void host_levels(Handle& h);
 
+// Process-wide record of the consumer-group sizes the autotuner measured, keyed by a
+// fingerprint of the problem's structure and options (taken once the programs are built).
+uint64_t tune_key(const Handle& h);
+bool tune_lookup(uint64_t key, int32_t (&nt)[PR_COUNT]);
+void tune_store(uint64_t key, const int32_t (&nt)[PR_COUNT]);
+constexpr int kTuneCands = 4;
+constexpr int kTuneNt[kTuneCands] = {32, 64, 96, 128};
+
 // Builds the chunked stream of program P; false if a single row does not fit a chunk.
 // x_bytes: element size of the working vector (and of dinv); val_bytes: of the values.
 // chain_sched: ilu_opts.chain_sched (0 the cheaper of levels and chains, 1 levels, 2 chains).
@@ -127,6 +135,9 @@ struct Handle {
     StreamHost sh[PR_COUNT];          // chunked streams (fast path)
     StreamBufs sb[PR_COUNT];
     bool stream_path = true;          // TMA-streamed level programs (else generic kernels)
+    uint64_t tune_key_v = 0;          // structural fingerprint (autotune)
+    int tune_state = 0;               // 0 rule, 1 measured, 2 from the process-wide record
+    double tune_ms[PR_COUNT][kTuneCands] = {};
     int idx_bytes = 2;                // local index width of the streams
     int nst = 4;                      // ring stages
     uint32_t chunk = 8192;            // bytes per chunk / ring stage

@@ -10,6 +10,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <thread>
 
 #include "handle.h"
@@ -990,6 +992,61 @@ bool build_stream(const ProgHost& P, int32_t p, int idx_bytes, int x_bytes, int 
 
 // ====================================================================================
 
+// ---- the autotuner's process-wide record ---------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<uint64_t, std::array<int32_t, PR_COUNT>> g_tune;
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(uint64_t v) {
+        for (int b = 0; b < 8; b++) {
+            h ^= (v >> (8 * b)) & 0xFF;
+            h *= 1099511628211ull;
+        }
+    }
+};
+}  // namespace
+
+// Options that shape the programs, the problem's sizes, each program's level structure, the
+// subdomains' row ranges and the local patterns (row pointers, every 64th column index).
+uint64_t tune_key(const Handle& h) {
+    Fnv f;
+    const ilu_opts& o = h.o;
+    for (int64_t v : {(int64_t)h.n, h.nnz, (int64_t)h.p, (int64_t)h.variant, (int64_t)h.form, (int64_t)h.prec,
+                      (int64_t)h.kB, (int64_t)h.kS, (int64_t)o.fill_level, (int64_t)o.ordering, (int64_t)o.l1_block,
+                      (int64_t)o.chain_sched, (int64_t)o.inner_iters, (int64_t)h.chunk, (int64_t)h.idx_bytes,
+                      (int64_t)o.ilut_p})
+        f.add((uint64_t)v);
+    f.add((uint64_t)(o.ilut_tau * 1e12));
+    for (int id = 0; id < PR_COUNT; id++) {
+        const ProgHost& P = h.prog[id];
+        f.add(P.lvl_ptr.size());
+        f.add(P.prow.size());
+        f.add(P.pcol.size());
+    }
+    for (int32_t v : h.qoff) f.add((uint64_t)(uint32_t)v);
+    for (int32_t v : h.nint) f.add((uint64_t)(uint32_t)v);
+    for (int32_t v : h.q_rp) f.add((uint64_t)(uint32_t)v);
+    for (size_t i = 0; i < h.q_ci.size(); i += 64) f.add((uint64_t)(uint32_t)h.q_ci[i]);
+    return f.h;
+}
+
+bool tune_lookup(uint64_t key, int32_t (&nt)[PR_COUNT]) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    for (int i = 0; i < PR_COUNT; i++) nt[i] = it->second[i];
+    return true;
+}
+
+void tune_store(uint64_t key, const int32_t (&nt)[PR_COUNT]) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::array<int32_t, PR_COUNT> a;
+    for (int i = 0; i < PR_COUNT; i++) a[i] = nt[i];
+    g_tune[key] = a;
+}
+
 // Level sets of the six factor windows (A or L_A, U_A; L_B, U_B; L_S, U_S) in the global
 // interior-first numbering, for introspection (Sec. 3.1); built on the first request.
 void host_levels(Handle& h) {
@@ -1581,6 +1638,17 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 h.chunk = c;
                 break;
             }
+        // a consumer-group size the autotuner measured for this structure earlier in the process
+        h.tune_state = 0;
+        if (h.o.autotune && !h.o.block_threads) {
+            h.tune_key_v = tune_key(h);
+            int32_t nt[PR_COUNT];
+            if (tune_lookup(h.tune_key_v, nt)) {
+                for (int id : ids)
+                    if (nt[id] > 0) h.sh[id].nt = nt[id];
+                h.tune_state = 2;
+            }
+        }
         bool ok = true;
         for (int id : ids) ok = ok && build_stream(h.prog[id], p, h.idx_bytes, vb, valb, h.chunk, h.sh[id], h.o.chain_sched);
         if (!ok) h.stream_path = false;

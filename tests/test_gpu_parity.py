@@ -463,6 +463,34 @@ def test_wide_consumer_groups(ilu, threads):
     h.close()
 
 
+@pytest.mark.parametrize("name,cfg", [("aniso2d_ragged", CONFIGS[2]), ("cuts3d", CONFIGS[6]), ("poisson64", CONFIGS[0])])
+def test_autotune_measures_and_remembers(ilu, name, cfg):
+    """ilu_opts.autotune: the setup times each streamed program with the candidate consumer
+    groups and keeps the fastest; the apply still matches the oracle; a second setup of the
+    same structure takes the remembered choice without measuring and gives the same bits."""
+    pr = _prob(name)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp32", autotune=True, **cfg))
+    t = h.tuning()
+    assert t["state"] in ("measured", "remembered")
+    for prog, nt in t["threads"].items():
+        assert nt in (32, 64, 96, 128)
+        if t["state"] == "measured":
+            assert len(t["apply_ms"][prog]) >= 2 and nt in t["apply_ms"][prog]
+    r = np.random.default_rng(31).standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ilu.ilu_apply(h, _dev(r), z)
+    h2 = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp32", autotune=True, **cfg))
+    t2 = h2.tuning()
+    assert t2["state"] == "remembered" and t2["threads"] == t["threads"]
+    z2 = torch.empty_like(z)
+    ilu.ilu_apply(h2, _dev(r), z2)
+    torch.cuda.synchronize()
+    _assert_close32(z.cpu().numpy(), O.Oracle.from_problem(pr, **cfg).apply(r), f"autotuned {name}")
+    assert torch.equal(z, z2)
+    h.close()
+    h2.close()
+
+
 def test_device_wait_timeout_is_reported(ilu):
     """A bound of one poll on every mbarrier wait makes the streamed apply give up; the
     device error word reports it, the call returns, and the context stays usable."""
