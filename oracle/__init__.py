@@ -20,7 +20,7 @@ _LIB = os.path.join(_HERE, "liborc.so")
 ILU0, MILU0, ILUT, EXACT, PMILU0 = 0, 1, 2, 3, 4
 BJ, SCHUR, RAP = 0, 1, 2
 FORM_AUTO, FORM_WZ, FORM_EF = 0, 1, 2
-ORDER_NATURAL, ORDER_RCM = 0, 1
+ORDER_NATURAL, ORDER_RCM, ORDER_COLOR = 0, 1, 2
 OK, ERR_ARG, ERR_CSR, ERR_OOM, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 
 _FACT = {"ilu0": ILU0, "milu0": MILU0, "ilut": ILUT, "exact": EXACT, "pmilu0": PMILU0}
@@ -69,6 +69,7 @@ def lib():
             "orc_classify": (I, [I, P, P, P, I, P]),
             "orc_permutation": (I, [I, P, I, P, P, P, P, P]),
             "orc_rcm": (I, [I, P, P, P]),
+            "orc_color": (I, [I, P, P, P, P]),
             "orc_round_bf16": (D, [D]),
             "orc_iluk_pattern": (P, [I, P, P, P, I, P]),
             "orc_opts_default": (None, [P]),
@@ -202,6 +203,19 @@ def round_bf16(x: float) -> float:
     return lib().orc_round_bf16(float(x))
 
 
+def color(n, rowptr, colind):
+    """Greedy multicolouring of the symmetrised graph of a square pattern (ascending index,
+    smallest colour free among the earlier neighbours): (colour of each node, the nodes
+    listed by (colour, index), number of colours)."""
+    rowptr, colind = _i32(rowptr), _i32(colind)
+    col = np.empty(max(n, 1), np.int32)
+    order = np.empty(max(n, 1), np.int32)
+    nc = lib().orc_color(int(n), _p(rowptr), _p(colind), _p(col), _p(order))
+    if nc < 0:
+        raise RuntimeError(f"color status {nc}")
+    return col[:n], order[:n], nc
+
+
 def rcm(n, rowptr, colind):
     """Reverse Cuthill-McKee order of the symmetrised graph of a square pattern:
     order[k] = the node placed k-th."""
@@ -257,7 +271,7 @@ class Oracle:
         o.ilut_p = int(ilut_p)
         o.inner_iters = int(inner_iters)
         o.pivot_eps = pivot_eps
-        o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM}[local_order]
+        o.local_order = {"natural": ORDER_NATURAL, "rcm": ORDER_RCM, "color": ORDER_COLOR}[local_order]
         o.fill_level = int(fill_level)
         o.l1_block = int(bool(l1_block))
         o.store_bf16 = int(bool(store_bf16))

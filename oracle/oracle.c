@@ -752,6 +752,124 @@ done:
     return st;
 }
 
+/* Sec. 3.1 schedules the triangular solves by levels; listing the nodes of a group colour
+   class by colour class, with no edge inside a class, leaves a lower factor in the pattern
+   of A one level per colour. The colouring: nodes in ascending index, each taking the
+   smallest colour that no neighbour coloured before it has. */
+int orc_color(int n, const int* rp, const int* ci, int* color, int* order) {
+    if (n <= 0) return 0;
+    int* cnt = (int*)calloc((size_t)n + 1, sizeof(int));
+    int* pos = (int*)malloc(((size_t)n + 1) * sizeof(int));
+    int* used = (int*)malloc(((size_t)n + 1) * sizeof(int));
+    int* adj = NULL;
+    int ncol = 0;
+    if (!cnt || !pos || !used) {
+        ncol = ORC_ERR_OOM;
+        goto done;
+    }
+    /* adjacency of the symmetrised graph (duplicates are harmless here) */
+    for (int i = 0; i < n; i++)
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+            if (ci[q] != i) {
+                cnt[i + 1]++;
+                cnt[ci[q] + 1]++;
+            }
+    for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    adj = (int*)malloc(((size_t)cnt[n] + 1) * sizeof(int));
+    if (!adj) {
+        ncol = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int i = 0; i < n; i++) pos[i] = cnt[i];
+    for (int i = 0; i < n; i++)
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+            if (ci[q] != i) {
+                adj[pos[i]++] = ci[q];
+                adj[pos[ci[q]]++] = i;
+            }
+    for (int i = 0; i <= n; i++) used[i] = -1;
+    for (int i = 0; i < n; i++) {
+        /* colours of the neighbours already coloured (index below i) */
+        for (int t = cnt[i]; t < cnt[i + 1]; t++)
+            if (adj[t] < i) used[color[adj[t]]] = i;
+        int c = 0;
+        while (used[c] == i) c++;
+        color[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    /* list by (colour, index): a counting sort, stable in the index */
+    {
+        int* start = (int*)calloc((size_t)ncol + 1, sizeof(int));
+        if (!start) {
+            ncol = ORC_ERR_OOM;
+            goto done;
+        }
+        for (int i = 0; i < n; i++) start[color[i] + 1]++;
+        for (int c = 0; c < ncol; c++) start[c + 1] += start[c];
+        for (int i = 0; i < n; i++) order[start[color[i]]++] = i;
+        free(start);
+    }
+done:
+    free(cnt);
+    free(pos);
+    free(used);
+    free(adj);
+    return ncol;
+}
+
+/* Put the nodes perm[g0 .. g0 + m) of one group in colour order of the graph they induce
+   (the pattern of A restricted to the group, with local labels in the current order). */
+static int color_group(const csr_t* A, int* perm, int* iperm, int g0, int m, int* lab) {
+    if (m <= 1) return ORC_OK;
+    int st = ORC_OK;
+    int* grp = (int*)malloc((size_t)m * sizeof(int));
+    int* srp = (int*)calloc((size_t)m + 1, sizeof(int));
+    int* ord = (int*)malloc((size_t)m * sizeof(int));
+    int* col = (int*)malloc((size_t)m * sizeof(int));
+    int* sci = NULL;
+    if (!grp || !srp || !ord || !col) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int k = 0; k < m; k++) {
+        grp[k] = perm[g0 + k];
+        lab[grp[k]] = k;
+    }
+    for (int k = 0; k < m; k++) {
+        int i = grp[k], c = 0;
+        for (int q = A->rp[i]; q < A->rp[i + 1]; q++)
+            if (lab[A->ci[q]] >= 0) c++;
+        srp[k + 1] = srp[k] + c;
+    }
+    sci = (int*)malloc(((size_t)srp[m] + 1) * sizeof(int));
+    if (!sci) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int k = 0, at = 0; k < m; k++) {
+        int i = grp[k];
+        for (int q = A->rp[i]; q < A->rp[i + 1]; q++)
+            if (lab[A->ci[q]] >= 0) sci[at++] = lab[A->ci[q]];
+    }
+    if (orc_color(m, srp, sci, col, ord) < 0) {
+        st = ORC_ERR_OOM;
+        goto done;
+    }
+    for (int k = 0; k < m; k++) {
+        perm[g0 + k] = grp[ord[k]];
+        iperm[grp[ord[k]]] = g0 + k;
+    }
+done:
+    if (grp)
+        for (int k = 0; k < m; k++) lab[grp[k]] = -1;
+    free(grp);
+    free(srp);
+    free(ord);
+    free(col);
+    free(sci);
+    return st;
+}
+
 /* Put the nodes perm[g0 .. g0 + m) of one group in RCM order of the graph they induce
    (the pattern of A restricted to the group, with local labels in the current order). */
 static int rcm_group(const csr_t* A, int* perm, int* iperm, int g0, int m, int* lab) {
@@ -993,7 +1111,8 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
     /* Sec. 2.2.1: classify and relabel. Block Jacobi (Sec. 2.1, Algorithm "Block Jacobi
        ILU on GPU") factors the whole A_s: it has no interface, every node of a subdomain
        is in one group. */
-    if (h->o.local_order != ORC_ORDER_NATURAL && h->o.local_order != ORC_ORDER_RCM) {
+    if (h->o.local_order != ORC_ORDER_NATURAL && h->o.local_order != ORC_ORDER_RCM &&
+        h->o.local_order != ORC_ORDER_COLOR) {
         st = ORC_ERR_ARG;
         goto fail;
     }
@@ -1005,16 +1124,18 @@ void* orc_setup(int n, const int* rp, const int* ci, const double* val, const in
     h->n2 = n - h->n1;
     /* Sec. 3.1: RCM order inside each group (BJ: all of A_s; two-level: the interior
        nodes, then the interface nodes, so that A_s keeps its [B F; E C] form) */
-    if (h->o.local_order == ORC_ORDER_RCM) {
+    if (h->o.local_order == ORC_ORDER_RCM || h->o.local_order == ORC_ORDER_COLOR) {
         int* lab = (int*)malloc(((size_t)n + 1) * sizeof(int));
         if (!lab) {
             st = ORC_ERR_OOM;
             goto fail;
         }
         for (int i = 0; i < n; i++) lab[i] = -1;
+        int (*reorder)(const csr_t*, int*, int*, int, int, int*) =
+            (h->o.local_order == ORC_ORDER_RCM) ? rcm_group : color_group;
         for (int s = 0; s < p && !st; s++) {
-            st = rcm_group(&h->A, h->perm, h->iperm, h->int_ptr[s], nint_of(h, s), lab);
-            if (!st) st = rcm_group(&h->A, h->perm, h->iperm, h->n1 + h->if_ptr[s], nif_of(h, s), lab);
+            st = reorder(&h->A, h->perm, h->iperm, h->int_ptr[s], nint_of(h, s), lab);
+            if (!st) st = reorder(&h->A, h->perm, h->iperm, h->n1 + h->if_ptr[s], nif_of(h, s), lab);
         }
         free(lab);
         if (st) goto fail;

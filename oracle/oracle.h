@@ -48,6 +48,8 @@ extern "C" {
 /* local order of each group of a subdomain (Sec. 3.1) */
 #define ORC_ORDER_NATURAL 0   /* ascending original index */
 #define ORC_ORDER_RCM 1       /* reverse Cuthill-McKee of the group's graph */
+#define ORC_ORDER_COLOR 2     /* greedy multicolouring of the group's graph, colour classes
+                                 one after the other (Sec. 3.1: fewer levels) */
 
 typedef struct orc_opts {
     int variant;        /* ORC_BJ, ORC_SCHUR or ORC_RAP */
@@ -107,6 +109,12 @@ double orc_round_bf16(double x);
 /* Reverse Cuthill-McKee order of the symmetrised graph of a square pattern (i ~ j when
    a_ij or a_ji is stored, i != j): order[k] = the node placed k-th. */
 int orc_rcm(int n, const int* rowptr, const int* colind, int* order);
+/* Greedy multicolouring of the symmetrised graph of a square pattern (i ~ j when a_ij or
+   a_ji is stored, i != j): nodes in ascending index take the smallest colour none of their
+   already coloured neighbours has. color[i] = the colour of node i; order[k] = the node
+   placed k-th when the nodes are listed by (colour, index). Returns the number of colours
+   (negative status on error). */
+int orc_color(int n, const int* rowptr, const int* colind, int* color, int* order);
 /* Level-k fill pattern of ILU(k) of a square CSR matrix with sorted rows and its diagonal
    stored: returns the pattern as a new CSR (values: the matrix's, 0 at fill positions) via
    orc_factor_* (opaque handle); NULL with *status set on error. */

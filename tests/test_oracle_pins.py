@@ -663,6 +663,83 @@ def test_two_level_rcm_orders_each_group_and_stays_exact(kind):
 
 
 # --------------------------------------------------------------------------------------
+# Multicolour local order (Sec. 3.1: fewer levels in the triangular solves)
+
+
+def test_color_of_grids_is_the_checkerboard():
+    """Greedy colouring in natural order: the 5-point grid gets the red-black colouring
+    (x + y) mod 2, the 9-point grid the four colours (x mod 2) + 2 (y mod 2)."""
+    side = 17
+    x, y = np.arange(side * side) % side, np.arange(side * side) // side
+    p5 = P.poisson2d_boxes(side, 1, seed=0)
+    c5, o5, n5 = O.color(p5.n, p5.rowptr, p5.colind)
+    assert n5 == 2 and np.array_equal(c5, (x + y) % 2)
+    p9 = P.aniso2d_boxes(side, 1, seed=0)
+    c9, o9, n9 = O.color(p9.n, p9.rowptr, p9.colind)
+    assert n9 == 4 and np.array_equal(c9, (x % 2) + 2 * (y % 2))
+    assert np.array_equal(o9, np.lexsort((np.arange(p9.n), c9)))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_color_is_proper_and_first_fit(seed):
+    """On random graphs: no edge joins two nodes of one colour, every node of colour c has an
+    earlier neighbour of each colour below c (it took the smallest free one), and the order
+    lists the nodes by (colour, index)."""
+    rng = np.random.default_rng(seed)
+    n = 60
+    edges = [tuple(rng.choice(n, 2, replace=False)) for _ in range(150)]
+    G = _sym_pattern(n, edges)
+    col, order, nc = O.color(n, G.indptr, G.indices)
+    assert nc == col.max() + 1
+    for i in range(n):
+        nb = G.indices[G.indptr[i]:G.indptr[i + 1]]
+        nb = nb[nb != i]
+        assert not np.any(col[nb] == col[i])
+        earlier = set(col[nb[nb < i]].tolist())
+        assert set(range(col[i])) <= earlier
+    assert np.array_equal(order, np.lexsort((np.arange(n), col)))
+
+
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "rand"])
+def test_color_order_gives_one_level_per_colour(kind):
+    """Block Jacobi with one subdomain in colour order: the lower factor of ILU(0) (pattern of
+    A) has as many levels as colours, the colour classes being independent sets."""
+    pr = {"aniso2d": lambda: P.aniso2d_boxes(20, 1, seed=2), "conv3d": lambda: P.convdiff3d_boxes(7, 1, seed=2),
+          "rand": lambda: P.randsparse(300, 1, mean_k=4.0, seed=2)}[kind]()
+    o = O.Oracle.from_problem(pr, variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="color")
+    _, _, nc = O.color(pr.n, pr.rowptr, pr.colind)
+    assert o.levels(0)[1] == nc
+    perm = o.perm()["perm"]
+    col, order, _ = O.color(pr.n, pr.rowptr, pr.colind)
+    assert np.array_equal(perm, order)
+
+
+@pytest.mark.parametrize("kind", ["aniso2d", "conv3d", "rand"])
+def test_two_level_color_orders_each_group_and_stays_exact(kind):
+    """Two-level with the colour order: each interior and interface group is the colour order
+    of the graph it induces, the split is unchanged, and with exact local factors and n2
+    inner steps the apply is A^{-1} (Eq. blockldusolve)."""
+    pr = _small_dd(kind)
+    A = pr.scipy()
+    nat = O.Oracle.from_problem(pr).perm()
+    o = O.Oracle.from_problem(pr, factor_B="exact", factor_S="exact", local_order="color",
+                              inner_iters=max(nat["n2"], 1))
+    pm = o.perm()
+    for k in ("int_ptr", "if_ptr", "iface"):
+        assert np.array_equal(pm[k], nat[k])
+    n1 = pm["n1"]
+    groups = [(pm["int_ptr"][s], pm["int_ptr"][s + 1]) for s in range(pr.p)]
+    groups += [(n1 + pm["if_ptr"][s], n1 + pm["if_ptr"][s + 1]) for s in range(pr.p)]
+    for a, b in groups:
+        g = np.sort(nat["perm"][a:b])
+        G = A[g][:, g].tocsr()
+        G.sort_indices()
+        assert np.array_equal(pm["perm"][a:b], g[O.color(g.size, G.indptr, G.indices)[1]])
+    r = np.random.default_rng(5).standard_normal(pr.n)
+    np.testing.assert_allclose(o.apply(r), np.linalg.solve(A.toarray(), r), rtol=1e-9, atol=1e-10)
+
+
+# --------------------------------------------------------------------------------------
 # ILU(k) (level of fill; the paper runs ILU(1) and ILU(2) in Sec. 4.2-4.4)
 
 
