@@ -468,6 +468,8 @@ def main():
                     help="preconditioner precision (bf16: bfloat16 factor values, FP32 arithmetic)")
     ap.add_argument("--threads", type=int, default=0, help="consumer-group threads override (0 = auto)")
     ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
+    ap.add_argument("--order", default="natural", choices=["natural", "rcm", "color"],
+                    help="local order inside each group of a subdomain")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="measure the consumer-group size of each streamed program at setup (1) or use the rule (0)")
     ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
@@ -518,6 +520,8 @@ def main():
     sol["block_threads"] = args.threads
     sol["kernel_path"] = args.kernel_path
     sol["autotune"] = bool(args.autotune) and not args.threads
+    if args.order != "natural":
+        sol["local_order"] = args.order
     t0 = time.perf_counter()
     h = ilu.ilu_setup_problem(pr, ilu.Opts(**sol))
     setup_s = time.perf_counter() - t0

@@ -75,8 +75,11 @@ typedef enum { ILU_PREC_FP64 = 0, ILU_PREC_FP32 = 1, ILU_PREC_BF16_STORE = 2 } i
    [B F; E C] form. NATURAL: ascending original index. RCM: reverse Cuthill-McKee of the
    graph the group induces in A + A^T (Sec. 3.1, Algorithm "Block Jacobi ILU on GPU"); each
    component starts at its unplaced node of least (degree, index), neighbours are appended
-   by (degree, index), the sequence is then reversed. */
-typedef enum { ILU_ORDER_NATURAL = 0, ILU_ORDER_RCM = 1 } ilu_order;
+   by (degree, index), the sequence is then reversed. COLOR: greedy multicolouring of that
+   graph (nodes in ascending index take the smallest colour none of their earlier neighbours
+   has), listed colour by colour, ascending index inside a colour: a lower factor in the
+   pattern of A then has one level per colour (Sec. 3.1), at the cost of a weaker ILU. */
+typedef enum { ILU_ORDER_NATURAL = 0, ILU_ORDER_RCM = 1, ILU_ORDER_COLOR = 2 } ilu_order;
 
 typedef struct {
     int32_t variant;      /* ilu_variant */

@@ -146,7 +146,7 @@ class Opts:
     analysis_only: bool = False
     kernel_path: str = "stream"     # "stream" (TMA-streamed level programs) or "generic"
     inner_launch: str = "single"    # inner Schur GMRES: "single" cooperative launch or "per_step"
-    local_order: str = "natural"    # order inside each group of a subdomain: "natural" or "rcm"
+    local_order: str = "natural"    # order inside each group of a subdomain: "natural", "rcm" or "color"
     fill_level: int = 0             # k > 0: ILU(k) / MILU(k) in the level-k fill pattern
     l1_block: bool = False          # block Jacobi: l1-BJ diagonal augmentation
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
@@ -171,7 +171,7 @@ class Opts:
         o.analysis_only = int(bool(self.analysis_only))
         o.kernel_path = {"stream": 0, "generic": 1}[self.kernel_path]
         o.inner_launch = {"single": 0, "per_step": 1}[self.inner_launch]
-        o.ordering = {"natural": 0, "rcm": 1}[self.local_order]
+        o.ordering = {"natural": 0, "rcm": 1, "color": 2}[self.local_order]
         o.fill_level = int(self.fill_level)
         o.l1_block = int(bool(self.l1_block))
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]

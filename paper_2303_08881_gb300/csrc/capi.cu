@@ -595,7 +595,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         (o.factor_B == ILU_FACT_ILUT && (o.ilut_p < 0 || o.ilut_tau < 0.0)) ||
         (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > 1024)) ||
         o.kernel_path < 0 || o.kernel_path > 1 || o.inner_launch < 0 || o.inner_launch > 1 ||
-        (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM) || o.fill_level < 0 ||
+        (o.ordering != ILU_ORDER_NATURAL && o.ordering != ILU_ORDER_RCM && o.ordering != ILU_ORDER_COLOR) ||
+        o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
         (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
         o.gs_precision < 0 || o.gs_precision > 2 || o.autotune < 0 || o.autotune > 1) {

@@ -1152,6 +1152,60 @@ static void rcm_group(const ilu_csr* A, const int32_t* part, int32_t s, std::vec
     grp.swap(out);
 }
 
+// Greedy multicolour order of the group `grp` (original indices of subdomain s, ascending):
+// in that order each node takes the smallest colour that none of its earlier neighbours in
+// the group (a ~ b when a_ab or a_ba is stored, a != b) has; the group is then listed colour
+// by colour, ascending index inside a colour (Sec. 3.1: a lower factor in the pattern of A
+// gets one level per colour). `slot` as for rcm_group.
+static void color_group(const ilu_csr* A, const int32_t* part, int32_t s, std::vector<int32_t>& grp,
+                        int32_t* slot) {
+    const int32_t m = (int32_t)grp.size();
+    if (m <= 1) return;
+    for (int32_t k = 0; k < m; k++) slot[grp[k]] = k;
+    // neighbour lists of the symmetrised graph, both directions of every stored entry
+    std::vector<int32_t> deg(m + 1, 0);
+    for (int32_t k = 0; k < m; k++) {
+        const int32_t i = grp[k];
+        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+            if (part[A->colind[q]] != s) continue;
+            const int32_t t = slot[A->colind[q]];
+            if (t >= 0 && t != k) {
+                deg[k + 1]++;
+                deg[t + 1]++;
+            }
+        }
+    }
+    for (int32_t k = 0; k < m; k++) deg[k + 1] += deg[k];
+    std::vector<int32_t> nb(deg[m]), fill(deg.begin(), deg.end() - 1);
+    for (int32_t k = 0; k < m; k++) {
+        const int32_t i = grp[k];
+        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+            if (part[A->colind[q]] != s) continue;
+            const int32_t t = slot[A->colind[q]];
+            if (t >= 0 && t != k) {
+                nb[fill[k]++] = t;
+                nb[fill[t]++] = k;
+            }
+        }
+    }
+    std::vector<int32_t> colour(m, 0), seen(m + 1, -1);
+    int32_t ncol = 0;
+    for (int32_t k = 0; k < m; k++) {  // labels ascend with the original index
+        for (int32_t e = deg[k]; e < deg[k + 1]; e++)
+            if (nb[e] < k) seen[colour[nb[e]]] = k;
+        int32_t c = 0;
+        while (seen[c] == k) c++;
+        colour[k] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    std::vector<int32_t> start(ncol + 1, 0), out(m);
+    for (int32_t k = 0; k < m; k++) start[colour[k] + 1]++;
+    for (int32_t c = 0; c < ncol; c++) start[c + 1] += start[c];
+    for (int32_t k = 0; k < m; k++) out[start[colour[k]]++] = grp[k];
+    for (int32_t k = 0; k < m; k++) slot[grp[k]] = -1;
+    grp.swap(out);
+}
+
 // Level-k fill pattern of ILU(k) of one local block: rows [q0, q0 + ns) of the Q-order CSR
 // (rp, ci; local column indices, sorted, diagonal stored). Stored entries have level 0;
 // row r is eliminated with its pivots m < r in ascending order, fill included, and every
@@ -1258,11 +1312,12 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         }
     }
 
-    // ---- RCM inside each group (Sec. 3.1; Algorithm "Block Jacobi ILU on GPU"): block
-    //      Jacobi orders all of A_s, the two-level variants its interior nodes and its
-    //      interface nodes separately, so A_s keeps its [B F; E C] form
-    if (h.o.ordering == ILU_ORDER_RCM) {
+    // ---- RCM or colour order inside each group (Sec. 3.1; Algorithm "Block Jacobi ILU on
+    //      GPU"): block Jacobi orders all of A_s, the two-level variants its interior nodes
+    //      and its interface nodes separately, so A_s keeps its [B F; E C] form
+    if (h.o.ordering == ILU_ORDER_RCM || h.o.ordering == ILU_ORDER_COLOR) {
         std::vector<int32_t> slot(n, -1);
+        const bool rcm = h.o.ordering == ILU_ORDER_RCM;
         auto work = [&](int32_t s0, int32_t s1) {
             std::vector<int32_t> grp;
             for (int32_t s = s0; s < s1; s++)
@@ -1270,7 +1325,10 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                     const int32_t g0 = side ? h.n1 + h.if_ptr[s] : h.int_ptr[s];
                     const int32_t g1 = side ? h.n1 + h.if_ptr[s + 1] : h.int_ptr[s + 1];
                     grp.assign(h.perm.begin() + g0, h.perm.begin() + g1);
-                    rcm_group(A, part, s, grp, slot.data());
+                    if (rcm)
+                        rcm_group(A, part, s, grp, slot.data());
+                    else
+                        color_group(A, part, s, grp, slot.data());
                     for (int32_t k = 0; k < g1 - g0; k++) {
                         h.perm[g0 + k] = grp[k];
                         h.iperm[grp[k]] = g0 + k;

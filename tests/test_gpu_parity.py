@@ -75,6 +75,9 @@ CONFIGS = [
     dict(variant="bj", factor_B="ilu0", factor_S="ilu0", l1_block=True),
     # MILU(0) of the partial-ILU(0) Schur complement (Sec. 3.2)
     dict(variant="schur", factor_B="ilu0", factor_S="pmilu0"),
+    # greedy multicolour local order (fewer levels, Sec. 3.1)
+    dict(variant="schur", factor_B="ilu0", factor_S="milu0", local_order="color"),
+    dict(variant="bj", factor_B="ilu0", factor_S="ilu0", local_order="color"),
 ]
 
 
