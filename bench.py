@@ -464,8 +464,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests of the serving sample in the default run (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving trace in the default run (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--variant", default=None, choices=[None, "bj", "schur", "rap"],
                     help="preconditioner variant override (rap: ILU(0) smoother, MILU(0) transfer)")

@@ -170,6 +170,7 @@ class Record:
     host_ms: float = 0.0     # the handle's host analysis, device setup and graph build (library clocks)
     device_ms: float = 0.0
     graph_ms: float = 0.0
+    escalations: int = 0     # continuations with a longer restart after maxit (see serve)
     x: object = None         # the solution (host numpy) when serve(keep_solutions=True)
 
 
@@ -187,8 +188,13 @@ class Report:
 
 def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int = 50, rtol: float = 1e-8,
           maxit: int = 5000, opts: dict | None = None, check_residual: bool = True,
-          keep_solutions: bool = False) -> Report:
-    """Run the requests (sorted by arrival) in real time and return per-request records."""
+          keep_solutions: bool = False, escalate: tuple = (200, 256)) -> Report:
+    """Run the requests (sorted by arrival) in real time and return per-request records.
+
+    A solve that reaches maxit without meeting rtol continues from its last iterate with
+    each restart length in `escalate` in turn (a longer Krylov space per cycle for the
+    hardest, most anisotropic requests), each with a fresh maxit; a request that still does
+    not converge is reported with status ILU_ERR_NOT_CONVERGED."""
     import torch
     import paper_2303_08881_gb300 as ilu
 
@@ -240,6 +246,14 @@ def serve(requests, workers: int = 8, cap_bytes: int = 120 << 30, restart: int =
                 # a reused handle solves on the stream it was created with
                 stream.synchronize()
                 info = ilu.gmres_solve(h, b, x, rtol=rtol, restart=restart, maxit=maxit)
+                iters = info["iters"]
+                for m in escalate:
+                    if info["status"] != ilu.ILU_ERR_NOT_CONVERGED:
+                        break
+                    rec.escalations += 1
+                    info = ilu.gmres_solve(h, b, x, rtol=rtol, restart=m, maxit=maxit)  # x: the last iterate
+                    iters += info["iters"]
+                info["iters"] = iters
                 xs = x.cpu().numpy()
                 rec.done = now()
                 rec.solve_s = time.perf_counter() - ts
@@ -298,6 +312,8 @@ def summarize(records, wall: float) -> dict:
         "reused": sum(r.reused for r in ok),
         "max_rel_res": float(max((r.rel_res for r in ok if r.rel_res == r.rel_res), default=float("nan"))),
         "converged": sum(r.status == 0 for r in ok),
+        "escalated": sum(r.escalations > 0 for r in ok),
+        "max_iters": int(max((r.iters for r in ok), default=0)),
         "mean_wait_ms": float(np.mean([r.start - r.arrival for r in ok]) * 1e3) if ok else 0.0,
         "mean_setup_ms": float(np.mean([r.setup_s for r in ok if not r.reused]) * 1e3) if ok else 0.0,
         "mean_solve_ms": float(np.mean([r.solve_s for r in ok]) * 1e3) if ok else 0.0,

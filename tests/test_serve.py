@@ -175,3 +175,31 @@ def test_results_are_the_same_alone_and_in_the_mix():
         h.close()
         assert info["iters"] == rec.iters
         assert np.array_equal(x.cpu().numpy(), rec.x), rec.rid
+
+
+@pytest.mark.gpu
+def test_unconverged_request_continues_with_a_longer_restart():
+    """A solve that reaches maxit continues from its last iterate with a longer restart. On an
+    anisotropic request (eps = 1e-3), FGMRES(256) from zero needs n_full steps; with a budget
+    of n_full + 10 steps FGMRES(2) does not converge and is reported as not converged, and
+    with the escalation to FGMRES(256) (a fresh budget, from the FGMRES(2) iterate) it does."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2303_08881_gb300 as ilu
+    spec = P.RequestSpec(0, 0.0, "c", "2d", 96, 1e-3, 1.0, 2, 4)
+    pr = P.problem_of_request(spec)
+    h = ilu.ilu_setup_problem(pr, ilu.Opts())
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros_like(b)
+    full = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=256, maxit=2000)
+    h.close()
+    assert full["status"] == 0
+    budget = full["iters"] + 10
+    reqs = [S.Request(spec.rid, spec.arrival, spec.key, pr)]
+    plain = S.serve(reqs, workers=1, restart=2, maxit=budget, escalate=())
+    assert plain.records[0].status == 5 and plain.records[0].escalations == 0
+    esc = S.serve(reqs, workers=1, restart=2, maxit=budget, escalate=(256,))
+    r = esc.records[0]
+    assert r.escalations == 1 and r.status == 0 and r.rel_res <= 1e-8, (r.status, r.rel_res, r.iters)
+    assert r.iters > budget
