@@ -138,6 +138,13 @@ typedef struct {
                              structure of the problem, so a later setup of the same structure
                              builds it directly. 0 (default) = the level-width rule. Ignored with
                              block_threads != 0. See ilu_get_tuning. */
+    int32_t ilut_setup;   /* factor_B = ILUT: 0 (default) = the numeric factorisation on the device
+                             (one warp per row, rows handed out in order, each waiting on the
+                             rows of its pivots), the host's result bit for bit; the host
+                             factorisation when ilut_p > 32, a row touches more columns than
+                             the device's per-warp table holds, or the handle is analysis-only.
+                             1 = on the host (threads over subdomains). ilu_get_times reports
+                             which ran and its time. */
 } ilu_opts;
 
 typedef struct {
@@ -267,9 +274,22 @@ ilu_status ilu_get_stats(void* h, int64_t* out);
 /* Wall-clock times of a handle, in ms: out[0] = host analysis of ilu_setup (classification,
    ordering, patterns, level programs, streams), out[1] = its device part (uploads, numeric
    factorisation, packing), out[2] = the last gmres_solve, out[3] = the part of it spent
-   capturing and instantiating the cycle graph (0 when the handle's graph was reused).
-   out must hold 4 values. Errors: ILU_ERR_ARG for a null pointer. */
+   capturing and instantiating the cycle graph (0 when the handle's graph was reused),
+   out[4] = the ILUT factorisation of factor_B = ILUT (part of out[0]; 0 otherwise), out[5] =
+   1 when that factorisation ran on the device, 0 when on the host or not ILUT.
+   out must hold 6 values. Errors: ILU_ERR_ARG for a null pointer. */
 ilu_status ilu_get_times(void* h, double* out);
+
+/* The ILUT factor of local block s (factor_B = ILUT): B_s for SCHUR and RAP (the interior rows
+   with their interior columns), A_s for block Jacobi, as combined L\U rows in the local order,
+   columns ascending, the pivot stored in every row. rowptr: host int32[rows of the block + 1]
+   (from 0); colind: host int32[*nnz]; val: host double[*nnz] (FP64, as factorised). Any of the
+   three arrays may be NULL; *nnz (required) receives the entry count. On a device handle the
+   values are read back from the device (synchronises the stream); on an analysis-only handle
+   they are the host factorisation's. Errors: ILU_ERR_ARG (null handle or nnz, s out of
+   range, factor_B not ILUT), ILU_ERR_CUDA. */
+ilu_status ilu_get_ilut_factor(void* h, int32_t s, int32_t* rowptr, int32_t* colind, double* val,
+                               int32_t* nnz);
 
 /* The Krylov basis of the handle's last gmres_solve (its last cycle): which = 0 the
    orthonormal vectors v_0..v_{k-1} (k <= restart + 1), which = 1 the preconditioned

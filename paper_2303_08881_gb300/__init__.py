@@ -47,7 +47,7 @@ class ilu_opts(C.Structure):
                 ("use_graphs", C.c_int32), ("block_threads", C.c_int32),
                 ("analysis_only", C.c_int32), ("kernel_path", C.c_int32), ("inner_launch", C.c_int32),
                 ("fill_level", C.c_int32), ("l1_block", C.c_int32), ("chain_sched", C.c_int32),
-                ("gs_precision", C.c_int32), ("autotune", C.c_int32)]
+                ("gs_precision", C.c_int32), ("autotune", C.c_int32), ("ilut_setup", C.c_int32)]
 
 
 class ilu_solve_info(C.Structure):
@@ -93,6 +93,7 @@ def lib():
             "ilu_get_krylov": (I, [P, I, I, P]),
             "ilu_get_tuning": (I, [P, P, P, P]),
             "ilu_measure_level_latency": (I, [P, I, P]),
+            "ilu_get_ilut_factor": (I, [P, I, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -152,6 +153,7 @@ class Opts:
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
     gs_precision: str = "mixed2"    # FGMRES Gram-Schmidt: "fp64", "mixed1" (FP32 first-pass dots), "mixed2" (+ FP32 second update)
     autotune: bool = False          # measure the consumer-group size of each streamed program at setup
+    ilut_setup: str = "device"      # factor_B = "ilut": numeric factorisation on the "device" or the "host"
 
     def to_c(self) -> ilu_opts:
         o = ilu_opts()
@@ -177,6 +179,7 @@ class Opts:
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]
         o.gs_precision = {"fp64": 0, "mixed1": 1, "mixed2": 2}[self.gs_precision]
         o.autotune = int(bool(self.autotune))
+        o.ilut_setup = {"device": 0, "host": 1}[self.ilut_setup]
         if self.analysis_only:
             o.stream = None
         elif self.stream is None:
@@ -267,6 +270,23 @@ class Handle:
                "ilu_get_local_factor")
         return v
 
+    def ilut_factor(self, s: int):
+        """ILUT factor of local block s (B_s, or A_s for block Jacobi): combined L\\U CSR rows
+        (rowptr, colind, FP64 values) in the local order."""
+        nnz = C.c_int32(0)
+        _check(lib().ilu_get_ilut_factor(self.ptr, int(s), None, None, None, C.byref(nnz)), "ilu_get_ilut_factor")
+        pm = self.perm()
+        rows = int(pm["int_ptr"][s + 1] - pm["int_ptr"][s])
+        if self.opts.variant == "bj":
+            rows += int(pm["if_ptr"][s + 1] - pm["if_ptr"][s])
+        rp = np.empty(rows + 1, np.int32)
+        ci = np.empty(nnz.value, np.int32)
+        v = np.empty(nnz.value)
+        _check(lib().ilu_get_ilut_factor(self.ptr, int(s), rp.ctypes.data_as(C.c_void_p),
+                                         ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                                         C.byref(nnz)), "ilu_get_ilut_factor")
+        return rp, ci, v
+
     def spmv(self, x, y):
         _check(lib().ilu_spmv(self.ptr, _ptr(x, self.n, self.device), _ptr(y, self.n, self.device)), "ilu_spmv")
 
@@ -287,10 +307,11 @@ class Handle:
 
     def times(self) -> dict:
         """Wall-clock ms: host analysis and device part of the setup, the last solve and
-        its graph build."""
-        out = np.zeros(4)
+        its graph build, the ILUT factorisation (inside the host analysis) and where it ran."""
+        out = np.zeros(6)
         _check(lib().ilu_get_times(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_times")
-        return dict(host_ms=float(out[0]), device_ms=float(out[1]), solve_ms=float(out[2]), graph_ms=float(out[3]))
+        return dict(host_ms=float(out[0]), device_ms=float(out[1]), solve_ms=float(out[2]), graph_ms=float(out[3]),
+                    ilut_ms=float(out[4]), ilut_on_device=bool(out[5]))
 
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,

@@ -17,7 +17,7 @@ OUT = os.path.join(PKG, "libilu2l.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["capi.cu", "kernels_apply.cu", "kernels_ilu.cu", "kernels_krylov.cu", "kernels_stream.cu", "noalloc.cu",
-      "probes.cu"]
+      "probes.cu", "kernels_ilut.cu"]
 CPP = ["setup_host.cpp"]
 
 

@@ -535,6 +535,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->chain_sched = 0;
     o->gs_precision = 2;
     o->autotune = 0;
+    o->ilut_setup = 0;
     o->pivot_eps = 1e-8;
     o->stream = nullptr;
     o->spin_limit = 0;
@@ -599,7 +600,8 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
         (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
-        o.gs_precision < 0 || o.gs_precision > 2 || o.autotune < 0 || o.autotune > 1) {
+        o.gs_precision < 0 || o.gs_precision > 2 || o.autotune < 0 || o.autotune > 1 || o.ilut_setup < 0 ||
+        o.ilut_setup > 1) {
         delete h;
         return ILU_ERR_ARG;
     }
@@ -941,6 +943,34 @@ ilu_status ilu_get_times(void* hp, double* out) {
     out[1] = h->device_ms;
     out[2] = h->solve_ms_last;
     out[3] = h->graph_ms_last;
+    out[4] = h->kB == ILU_FACT_ILUT ? h->ilut_ms : 0.0;
+    out[5] = (h->kB == ILU_FACT_ILUT && h->ilut_device) ? 1.0 : 0.0;
+    return ILU_OK;
+}
+
+ilu_status ilu_get_ilut_factor(void* hp, int32_t s, int32_t* rowptr, int32_t* colind, double* val,
+                               int32_t* nnz) {
+    if (!hp || !nnz) return ILU_ERR_ARG;
+    Handle* h = (Handle*)hp;
+    if (h->kB != ILU_FACT_ILUT || s < 0 || s >= h->p) return ILU_ERR_ARG;
+    const int32_t q0 = h->qoff[s];
+    const int32_t m = (h->variant != ILU_VARIANT_BJ) ? h->nint[s] : (h->qoff[s + 1] - q0);
+    const int32_t e0 = h->f1_rp[q0], e1 = h->f1_rp[q0 + m];
+    *nnz = e1 - e0;
+    if (rowptr)
+        for (int32_t r = 0; r <= m; r++) rowptr[r] = h->f1_rp[q0 + r] - e0;
+    if (colind)
+        for (int32_t k = e0; k < e1; k++) colind[k - e0] = h->f1_ci[k];
+    if (val && e1 > e0) {
+        if (h->o.analysis_only) {
+            for (int32_t k = e0; k < e1; k++) val[k - e0] = h->f1_host_vals[k];
+        } else {
+            cudaError_t e = cudaMemcpyAsync(val, h->d_vals + h->f1.base + e0, (size_t)(e1 - e0) * sizeof(double),
+                                            cudaMemcpyDeviceToHost, h->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            if (e != cudaSuccess) return ILU_ERR_CUDA;
+        }
+    }
     return ILU_OK;
 }
 

@@ -89,6 +89,8 @@ struct Handle {
     int64_t nnz = 0, nnz_coff = 0;
     int variant = 1, form = 1, prec = 1, kB = 0, kS = 1;
     bool f2_alias = false, f1_device = true;
+    bool ilut_device = false;  // the ILUT factor F1 was computed by the device kernel
+    double ilut_ms = 0.0;      // wall time of the ILUT factorisation (part of host_ms)
     int npert = 0;
     double setup_ms = 0.0;
     double host_ms = 0.0, device_ms = 0.0;        // the two parts of setup_ms
@@ -262,7 +264,12 @@ struct Handle {
 };
 
 // host setup (setup_host.cpp): validation, classification, permutation, local blocks,
-// C_off, factor patterns (ILUT values on the host), level sets and level programs.
+// C_off, factor patterns (ILUT values from device_ilut or on the host), level sets and
+// level programs.
 ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t p);
+
+// ILUT of the local blocks on the device (kernels_ilut.cu), called by host_setup; fills the
+// host pattern and values of F1 as the host factorisation does.
+ilu_status device_ilut(Handle& h);
 
 }  // namespace ilu2l

@@ -6,6 +6,7 @@
 // scheduling analysis, L\U stored in the pattern), Sec. 3.2 (local blocks Eq. localA,
 // factor extraction L_B, U_B, L_S, U_S, W, Z, the off-diagonal blocks of S, Eq. SS).
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <array>
 #include <cmath>
@@ -1480,58 +1481,68 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
         h.f1 = apat;
         h.f1.base = 0;
     } else {
-        // ILUT of B_s (two-level) or of A_s (block Jacobi), on the host, per subdomain
-        std::vector<std::vector<IlutRow>> res(p);
-        std::vector<int> stat(p, ILU_OK), pert(p, 0);
-        const double tau = h.o.ilut_tau;
-        const int32_t pk = h.o.ilut_p;
-        const double eps = h.o.pivot_eps;
-        auto work = [&](int32_t s0, int32_t s1) {
-            std::vector<int32_t> brp, bci;
-            std::vector<double> bv;
-            for (int32_t s = s0; s < s1; s++) {
-                const int32_t q0 = h.qoff[s];
-                const int32_t m = schur ? h.nint[s] : (h.qoff[s + 1] - q0);
-                brp.assign(m + 1, 0);
-                bci.clear();
-                bv.clear();
-                for (int32_t r = 0; r < m; r++) {
-                    for (int32_t k = h.q_rp[q0 + r]; k < h.q_rp[q0 + r + 1]; k++)
-                        if (h.q_ci[k] < m) {
-                            bci.push_back(h.q_ci[k]);
-                            bv.push_back(h.q_v[k]);
-                        }
-                    brp[r + 1] = (int32_t)bci.size();
-                }
-                stat[s] = ilut_local(brp.data(), bci.data(), bv.data(), m, tau, pk, eps, res[s],
-                                     &pert[s]);
-            }
-        };
-        for_ranges(p, [&](int, int32_t s0, int32_t s1) { work(s0, s1); });
-        for (int32_t s = 0; s < p; s++) {
-            if (stat[s] != ILU_OK) return (ilu_status)stat[s];
-            h.npert += pert[s];
-        }
-        h.f1_rp.assign(n + 1, 0);
-        h.f1_dpos.assign(n, -1);
-        h.f1_ci.clear();
-        h.f1_host_vals.clear();
-        for (int32_t s = 0; s < p; s++) {
-            const int32_t q0 = h.qoff[s];
-            const int32_t ns = h.qoff[s + 1] - q0;
-            for (int32_t r = 0; r < ns; r++) {
-                const int32_t q = q0 + r;
-                if (r < (int32_t)res[s].size()) {
-                    const IlutRow& ro = res[s][r];
-                    for (size_t t = 0; t < ro.ci.size(); t++) {
-                        if (ro.ci[t] == r) h.f1_dpos[q] = (int32_t)h.f1_ci.size();
-                        h.f1_ci.push_back(ro.ci[t]);
-                        h.f1_host_vals.push_back(ro.v[t]);
+        // ILUT of B_s (two-level) or of A_s (block Jacobi): on the device (kernels_ilut.cu)
+        // unless the handle is analysis-only or asks for the host; the host factorisation
+        // below when the device one cannot take the rows (p > 32, a row wider than its table)
+        const auto t_ilut = std::chrono::steady_clock::now();
+        ilu_status ds = ILU_ERR_UNSUPPORTED;
+        if (!h.o.analysis_only && h.o.ilut_setup == 0) ds = device_ilut(h);
+        if (ds != ILU_OK && ds != ILU_ERR_UNSUPPORTED) return ds;
+        h.ilut_device = (ds == ILU_OK);
+        if (!h.ilut_device) {
+            std::vector<std::vector<IlutRow>> res(p);
+            std::vector<int> stat(p, ILU_OK), pert(p, 0);
+            const double tau = h.o.ilut_tau;
+            const int32_t pk = h.o.ilut_p;
+            const double eps = h.o.pivot_eps;
+            auto work = [&](int32_t s0, int32_t s1) {
+                std::vector<int32_t> brp, bci;
+                std::vector<double> bv;
+                for (int32_t s = s0; s < s1; s++) {
+                    const int32_t q0 = h.qoff[s];
+                    const int32_t m = schur ? h.nint[s] : (h.qoff[s + 1] - q0);
+                    brp.assign(m + 1, 0);
+                    bci.clear();
+                    bv.clear();
+                    for (int32_t r = 0; r < m; r++) {
+                        for (int32_t k = h.q_rp[q0 + r]; k < h.q_rp[q0 + r + 1]; k++)
+                            if (h.q_ci[k] < m) {
+                                bci.push_back(h.q_ci[k]);
+                                bv.push_back(h.q_v[k]);
+                            }
+                        brp[r + 1] = (int32_t)bci.size();
                     }
+                    stat[s] = ilut_local(brp.data(), bci.data(), bv.data(), m, tau, pk, eps, res[s],
+                                         &pert[s]);
                 }
-                h.f1_rp[q + 1] = (int32_t)h.f1_ci.size();
+            };
+            for_ranges(p, [&](int, int32_t s0, int32_t s1) { work(s0, s1); });
+            for (int32_t s = 0; s < p; s++) {
+                if (stat[s] != ILU_OK) return (ilu_status)stat[s];
+                h.npert += pert[s];
+            }
+            h.f1_rp.assign(n + 1, 0);
+            h.f1_dpos.assign(n, -1);
+            h.f1_ci.clear();
+            h.f1_host_vals.clear();
+            for (int32_t s = 0; s < p; s++) {
+                const int32_t q0 = h.qoff[s];
+                const int32_t ns = h.qoff[s + 1] - q0;
+                for (int32_t r = 0; r < ns; r++) {
+                    const int32_t q = q0 + r;
+                    if (r < (int32_t)res[s].size()) {
+                        const IlutRow& ro = res[s][r];
+                        for (size_t t = 0; t < ro.ci.size(); t++) {
+                            if (ro.ci[t] == r) h.f1_dpos[q] = (int32_t)h.f1_ci.size();
+                            h.f1_ci.push_back(ro.ci[t]);
+                            h.f1_host_vals.push_back(ro.v[t]);
+                        }
+                    }
+                    h.f1_rp[q + 1] = (int32_t)h.f1_ci.size();
+                }
             }
         }
+        h.ilut_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_ilut).count();
         h.f1.rp = h.f1_rp.data();
         h.f1.ci = h.f1_ci.data();
         h.f1.dpos = h.f1_dpos.data();

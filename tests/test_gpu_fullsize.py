@@ -120,3 +120,31 @@ def test_fullsize_fgmres_matches_oracle_record(ilu, key, prec):
     ref = np.array(gold["x_sample"])
     assert np.abs(samp - ref).max() <= 1e-6 * gold["x_absmax"], np.abs(samp - ref).max()
     h.close()
+
+
+def test_fullsize_device_ilut_matches_host_and_oracle(ilu):
+    """The ILUT workload's B factor (256 interior blocks, ILUT(1e-3, 10)) computed on the device
+    equals the host factorisation in every block and the oracle's ILUT in 8 sampled blocks, bit
+    for bit (the bar of test_gpu_ilut: the same operations in the same order)."""
+    import scipy.sparse as sp
+    key = "aniso3d_cuts_128_p256"
+    pr = _workload(key)
+    sol, _ = _solver(key, "fp32")
+    hd = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp32", **sol))
+    hh = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision="fp32", ilut_setup="host", **sol))
+    assert hd.times()["ilut_on_device"] and not hh.times()["ilut_on_device"]
+    for s in range(pr.p):
+        for a, b in zip(hd.ilut_factor(s), hh.ilut_factor(s)):
+            assert np.array_equal(a, b), f"block {s}"
+    hh.close()
+    orc = O.Oracle.from_problem(pr, **sol)
+    pm = orc.perm()
+    for s in np.linspace(0, pr.p - 1, 8).round().astype(int):
+        rp, ci, v = orc.local_csr(int(s))
+        nr, m = len(rp) - 1, int(pm["int_ptr"][s + 1] - pm["int_ptr"][s])
+        B = sp.csr_matrix((v, ci, rp), shape=(nr, nr))[:m, :m]
+        B.sort_indices()
+        ref = O.ilut(m, B.indptr, B.indices, B.data, tau=sol["ilut_tau"], p=sol["ilut_p"])
+        for a, b in zip(hd.ilut_factor(int(s)), ref):
+            assert np.array_equal(a, b), f"block {s}"
+    hd.close()

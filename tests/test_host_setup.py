@@ -2,6 +2,7 @@
 classification, interior-first permutation, level sets of every factor pattern (ILUT's
 included) match the oracle bit for bit."""
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 import oracle as O
@@ -232,3 +233,40 @@ def test_input_checks_find_every_bad_row(ilu, kind, status, where):
     with pytest.raises(ilu.IluError) as ei:
         ilu.ilu_setup(n, rp, ci, val, part, pr.p, ilu.Opts(analysis_only=True))
     assert ei.value.status == getattr(ilu, status)
+
+
+@pytest.mark.parametrize("name", ["aniso2d_ragged", "cuts3d", "dense_rows"])
+@pytest.mark.parametrize("cfg", [dict(variant="schur", factor_S="milu0", ilut_tau=1e-3, ilut_p=10),
+                                 dict(variant="bj", factor_S="ilu0", ilut_tau=0.0, ilut_p=32),
+                                 dict(variant="schur", factor_S="milu0", ilut_tau=1e-3, ilut_p=0)],
+                         ids=lambda c: "-".join(map(str, c.values())))
+def test_host_ilut_factor_matches_oracle(ilu, name, cfg):
+    """The host ILUT of each B_s (A_s for block Jacobi), read through ilu_get_ilut_factor,
+    equals the oracle's ILUT of the same block bit for bit; analysis-only handles factorise
+    on the host."""
+    pr = CASES[name]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True, factor_B="ilut", **cfg))
+    t = h.times()
+    assert not t["ilut_on_device"] and t["ilut_ms"] > 0.0
+    orc = O.Oracle.from_problem(pr, factor_B="ilut", **cfg)
+    pm = orc.perm()
+    for s in range(pr.p):
+        rp, ci, v = orc.local_csr(s)
+        nr = len(rp) - 1
+        m = nr if cfg["variant"] == "bj" else int(pm["int_ptr"][s + 1] - pm["int_ptr"][s])
+        B = sp.csr_matrix((v, ci, rp), shape=(nr, nr))[:m, :m]
+        B.sort_indices()
+        ref = O.ilut(m, B.indptr, B.indices, B.data, tau=cfg["ilut_tau"], p=cfg["ilut_p"])
+        for a, b in zip(h.ilut_factor(s), ref):
+            assert np.array_equal(a, b), f"block {s}"
+    h.close()
+
+
+def test_ilut_factor_needs_ilut(ilu):
+    pr = CASES["p1"]()
+    h = ilu.ilu_setup_problem(pr, ilu.Opts(analysis_only=True))
+    with pytest.raises(ilu.IluError) as ei:
+        h.ilut_factor(0)
+    assert ei.value.status == ilu.ILU_ERR_ARG
+    assert h.times()["ilut_ms"] == 0.0
+    h.close()
