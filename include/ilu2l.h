@@ -276,8 +276,8 @@ ilu_status ilu_get_stats(void* h, int64_t* out);
    factorisation, packing), out[2] = the last gmres_solve, out[3] = the part of it spent
    capturing and instantiating the cycle graph (0 when the handle's graph was reused),
    out[4] = the ILUT factorisation of factor_B = ILUT (part of out[0]; 0 otherwise), out[5] =
-   1 when that factorisation ran on the device, 0 when on the host or not ILUT.
-   out must hold 6 values. Errors: ILU_ERR_ARG for a null pointer. */
+   1 when that factorisation ran on the device, 0 when on the host or not ILUT, out[6] = the
+   device kernels of it (CUDA events; 0 on the host). out must hold 7 values. Errors: ILU_ERR_ARG for a null pointer. */
 ilu_status ilu_get_times(void* h, double* out);
 
 /* The ILUT factor of local block s (factor_B = ILUT): B_s for SCHUR and RAP (the interior rows

@@ -308,10 +308,10 @@ class Handle:
     def times(self) -> dict:
         """Wall-clock ms: host analysis and device part of the setup, the last solve and
         its graph build, the ILUT factorisation (inside the host analysis) and where it ran."""
-        out = np.zeros(6)
+        out = np.zeros(7)
         _check(lib().ilu_get_times(self.ptr, out.ctypes.data_as(C.c_void_p)), "ilu_get_times")
         return dict(host_ms=float(out[0]), device_ms=float(out[1]), solve_ms=float(out[2]), graph_ms=float(out[3]),
-                    ilut_ms=float(out[4]), ilut_on_device=bool(out[5]))
+                    ilut_ms=float(out[4]), ilut_on_device=bool(out[5]), ilut_kernel_ms=float(out[6]))
 
     def stream_stats(self, program: str) -> dict:
         """Shape of a streamed level program ("bj", "fwd", "s", "bwd"): record width,

@@ -220,8 +220,8 @@ ilu_status device_setup(Handle& h) {
     CK(upload(h, &h.d_nint, h.nint));
     CK(upload(h, &h.d_if_ptr, h.if_ptr));
     CK(upload(h, &h.d_q_orig, h.q_orig));
-    CK(upload(h, &h.d_q_rp, h.q_rp));
-    CK(upload(h, &h.d_q_ci, h.q_ci));
+    if (!h.d_q_rp) CK(upload(h, &h.d_q_rp, h.q_rp));  // the device ILUT may have uploaded both
+    if (!h.d_q_ci) CK(upload(h, &h.d_q_ci, h.q_ci));
     CK(upload(h, &h.d_q_dpos, h.q_dpos));
     // value array [F1 | F2 | A_local]
     h.d_vals = h.alloc<double>((size_t)h.nvals, &e);
@@ -229,9 +229,16 @@ ilu_status device_setup(Handle& h) {
     if (!h.q_v.empty())
         CK(cudaMemcpyAsync(h.d_vals + h.a_base, h.q_v.data(), h.q_v.size() * sizeof(double),
                            cudaMemcpyHostToDevice, h.st));
-    if (!h.f1_device && !h.f1_host_vals.empty())
+    if (h.d_f1_stage) {  // ILUT values factorised on the device
+        if (h.f1.nnz)
+            CK(cudaMemcpyAsync(h.d_vals + h.f1.base, h.d_f1_stage, (size_t)h.f1.nnz * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h.st));
+        h.release(h.d_f1_stage);
+        h.d_f1_stage = nullptr;
+    } else if (!h.f1_device && !h.f1_host_vals.empty()) {
         CK(cudaMemcpyAsync(h.d_vals + h.f1.base, h.f1_host_vals.data(),
                            h.f1_host_vals.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    }
     h.d_err = h.alloc<int32_t>(1, &e);
     h.d_npert = h.alloc<int32_t>(1, &e);
     if (!h.d_err || !h.d_npert) return map_err(e);
@@ -945,6 +952,7 @@ ilu_status ilu_get_times(void* hp, double* out) {
     out[3] = h->graph_ms_last;
     out[4] = h->kB == ILU_FACT_ILUT ? h->ilut_ms : 0.0;
     out[5] = (h->kB == ILU_FACT_ILUT && h->ilut_device) ? 1.0 : 0.0;
+    out[6] = (h->kB == ILU_FACT_ILUT && h->ilut_device) ? h->ilut_kernel_ms : 0.0;
     return ILU_OK;
 }
 

@@ -91,6 +91,8 @@ struct Handle {
     bool f2_alias = false, f1_device = true;
     bool ilut_device = false;  // the ILUT factor F1 was computed by the device kernel
     double ilut_ms = 0.0;      // wall time of the ILUT factorisation (part of host_ms)
+    double ilut_kernel_ms = 0.0;  // of it, the device kernels (CUDA events)
+    double* d_f1_stage = nullptr;  // device ILUT values in f1 order until the device setup
     int npert = 0;
     double setup_ms = 0.0;
     double host_ms = 0.0, device_ms = 0.0;        // the two parts of setup_ms
@@ -116,7 +118,8 @@ struct Handle {
     FPat apat;             // pattern of the local blocks A_s themselves
     bool lev_ready = false;  // lev / nlev computed (on the first introspection call)
     std::vector<double> f1_host_vals;  // ILUT values (host-computed factor F1)
-    std::vector<int32_t> f1_rp, f1_ci, f1_dpos;  // its pattern (f1 views it)
+    std::vector<int32_t> f1_rp, f1_dpos;  // its pattern (f1 views it)
+    rawvec<int32_t> f1_ci;
     int64_t a_base = 0;    // region of the original local values in the value array
     int64_t nvals = 0;
     ProgHost prog[PR_COUNT];
