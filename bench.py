@@ -83,11 +83,12 @@ def measured_traffic(workload, kernel):
     return rec["bytes"], "ncu capture of this source (sha256 prefix " + rec["sha256"] + ")"
 
 
-def class_bytes(sz, prec, iters, m, k, gs="mixed2"):
+def class_bytes(sz, prec, iters, m, k, gs="mixed3"):
     """Algorithmic bytes summed over the working launches of every kernel class of one
     solve with `iters` Arnoldi steps in cycles of m, inner GMRES of k steps; gs = the
     Gram-Schmidt arithmetic (ilu_opts.gs_precision: the first pass's dots and, with
-    mixed2, the second pass's update read the FP32 copy of the basis)."""
+    mixed2 and mixed3, the second pass's update read the FP32 copy of the basis; mixed3
+    reads the basis for the first update and the second pass's dots as two FP32 parts)."""
     n, nnz, n1, n2, ncoff = sz["n"], sz["nnz"], sz["n1"], sz["n2"], sz["nnz_coff"]
     sv = 8 if prec == "fp64" else 4
     svv = 2 if prec == "bf16" else sv  # stored factor values
@@ -97,13 +98,16 @@ def class_bytes(sz, prec, iters, m, k, gs="mixed2"):
     cycles = len(steps)
     b = {}
     spmv = 12 * nnz + 4 * (n + 1)
-    v1 = 4 if gs in ("mixed1", "mixed2") else 8    # bytes per basis element read by the first pass's dots
-    v2 = 4 if gs == "mixed2" else 8                 # ... by the second pass's update
-    w32 = 8 * n if gs in ("mixed1", "mixed2") else 0  # the FP32 copy of w written and read
+    mixed = gs in ("mixed1", "mixed2", "mixed3")
+    v1 = 4 if mixed else 8                          # bytes per basis element read by the first pass's dots
+    v2 = 4 if gs in ("mixed2", "mixed3") else 8     # ... by the second pass's update
+    w32 = 8 * n if mixed else 0                     # the FP32 copy of w written and read
+    vlo = 4 * n if gs == "mixed3" else 0            # the low FP32 part of each new basis vector
     b["fg_spmv_dot"] = sum(spmv + 16 * n + w32 + v1 * (j + 1) * n for j in js)
+    # the first update and the second pass's dots: FP64 basis, or its two FP32 parts (8 bytes either way)
     b["fg_cgs"] = sum(8 * (j + 1) * n + 16 * n for j in js)
     b["fg_norm"] = sum(v2 * (j + 1) * n + 16 * n for j in js)
-    b["fg_next"] = sum((16 + (4 if w32 else 0)) * n for j in js if j + 1 < m)
+    b["fg_next"] = sum((16 + (4 if w32 else 0)) * n + vlo for j in js if j + 1 < m)
     b["fg_update"] = sum(8 * s * n + 16 * n for s in steps)
     b["fg_resid"] = (cycles + 1) * (spmv + 24 * n)
     b["fg_scale0"] = (cycles + 1) * 16 * n
@@ -131,7 +135,7 @@ def class_bytes(sz, prec, iters, m, k, gs="mixed2"):
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def class_flops64(sz, iters, m, gs="mixed2"):
+def class_flops64(sz, iters, m, gs="mixed3"):
     """FP64 flops per class (the FP32 arithmetic of the mixed Gram-Schmidt forms is not
     counted: it does not load the FP64 pipe)."""
     n, nnz = sz["n"], sz["nnz"]
@@ -140,9 +144,11 @@ def class_flops64(sz, iters, m, gs="mixed2"):
     js = [j for s in steps for j in range(s)]
     cycles = len(steps)
     f = {}
-    f["fg_spmv_dot"] = sum(2 * nnz + (0 if gs in ("mixed1", "mixed2") else 2 * (j + 1) * n) for j in js)
-    f["fg_cgs"] = sum(4 * (j + 1) * n for j in js)
-    f["fg_norm"] = sum((3 * n if gs == "mixed2" else 2 * (j + 1) * n + 2 * n) for j in js)
+    mixed = gs in ("mixed1", "mixed2", "mixed3")
+    f["fg_spmv_dot"] = sum(2 * nnz + (0 if mixed else 2 * (j + 1) * n) for j in js)
+    # mixed3: the update and the dots in double-float (FP32) arithmetic, one FP64 subtraction per row
+    f["fg_cgs"] = sum((n if gs == "mixed3" else 4 * (j + 1) * n) for j in js)
+    f["fg_norm"] = sum((3 * n if gs in ("mixed2", "mixed3") else 2 * (j + 1) * n + 2 * n) for j in js)
     f["fg_next"] = sum(n for j in js if j + 1 < m)
     f["fg_update"] = sum(2 * s * n for s in steps)
     f["fg_resid"] = (cycles + 1) * (2 * nnz + 3 * n)
@@ -477,6 +483,8 @@ def main():
     ap.add_argument("--kernel-path", default="stream", choices=["stream", "generic"])
     ap.add_argument("--order", default="natural", choices=["natural", "rcm", "color"],
                     help="local order inside each group of a subdomain")
+    ap.add_argument("--gs", default=None, choices=[None, "fp64", "mixed1", "mixed2", "mixed3"],
+                    help="arithmetic of the outer Gram-Schmidt passes (ilu_opts.gs_precision)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="measure the consumer-group size of each streamed program at setup (1) or use the rule (0)")
     ap.add_argument("--side", type=int, default=0, help="grid side override (smaller cases for profiling)")
@@ -532,6 +540,8 @@ def main():
     sol["autotune"] = bool(args.autotune) and not args.threads
     if args.order != "natural":
         sol["local_order"] = args.order
+    if args.gs:
+        sol["gs_precision"] = args.gs
     t0 = time.perf_counter()
     h = ilu.ilu_setup_problem(pr, ilu.Opts(**sol))
     setup_s = time.perf_counter() - t0
@@ -603,7 +613,7 @@ def main():
     pinfo = solve(h)
     prof = h.profile_read()
     h.profile(False)
-    gs = sol.get("gs_precision", "mixed2")
+    gs = sol.get("gs_precision", "mixed3")
     cbytes = class_bytes(sz, prec, pinfo["iters"], restart, k_inner, gs)
     cflops = class_flops64(sz, pinfo["iters"], restart, gs)
     classes = {}

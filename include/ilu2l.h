@@ -125,10 +125,17 @@ typedef struct {
                              each Arnoldi step (Sec. 4.1.1): 0 = both in FP64; 1 = the first
                              pass's coefficients h1 = V^T w from FP32 copies of V and w, then
                              w -= V h1 and the second pass in FP64 (the second pass removes the
-                             ~6e-8 ||w|| the estimate leaves); 2 (default) = as 1, and the second
+                             ~6e-8 ||w|| the estimate leaves); 2 = as 1, and the second
                              pass's update w -= V h2 from the FP32 copy of V with FP32 products:
                              h2 is then ~6e-8 ||w||, so the update's error, ~1e-7 ||V h2||, is
-                             ~1e-14 ||w||, the size of FP64 rounding in the full update. The
+                             ~1e-14 ||w||, the size of FP64 rounding in the full update;
+                             3 (default) = as 2, and the first update w -= V h1 and the second
+                             pass's dots V^T w in double-float arithmetic (pairs of FP32 numbers,
+                             ~48 significant bits, error-free products and sums) from a two-term
+                             FP32 split of every basis vector kept beside V (4 more bytes per
+                             basis entry): no FP64 operation per basis entry, one FP64
+                             subtraction per row. All FP32 forms need the entries of w within
+                             the FP32 range. The
                              coefficients H = h1 + h2, w itself, ||w||, the Givens rotations,
                              the solution update and the true residual are FP64 in every mode. */
     int32_t autotune;     /* streamed path: 1 = ilu_setup measures, for each streamed program, the

@@ -151,7 +151,8 @@ class Opts:
     fill_level: int = 0             # k > 0: ILU(k) / MILU(k) in the level-k fill pattern
     l1_block: bool = False          # block Jacobi: l1-BJ diagonal augmentation
     chain_sched: str = "auto"       # interface rows: "auto" (cheaper of levels / chains), "levels", "chains"
-    gs_precision: str = "mixed2"    # FGMRES Gram-Schmidt: "fp64", "mixed1" (FP32 first-pass dots), "mixed2" (+ FP32 second update)
+    gs_precision: str = "mixed3"    # FGMRES Gram-Schmidt: "fp64", "mixed1" (FP32 first-pass dots), "mixed2" (+ FP32 second update),
+    #                                 "mixed3" (+ the first update and second-pass dots in double-float from a split basis)
     autotune: bool = False          # measure the consumer-group size of each streamed program at setup
     ilut_setup: str = "device"      # factor_B = "ilut": numeric factorisation on the "device" or the "host"
 
@@ -177,7 +178,7 @@ class Opts:
         o.fill_level = int(self.fill_level)
         o.l1_block = int(bool(self.l1_block))
         o.chain_sched = {"auto": 0, "levels": 1, "chains": 2}[self.chain_sched]
-        o.gs_precision = {"fp64": 0, "mixed1": 1, "mixed2": 2}[self.gs_precision]
+        o.gs_precision = {"fp64": 0, "mixed1": 1, "mixed2": 2, "mixed3": 3}[self.gs_precision]
         o.autotune = int(bool(self.autotune))
         o.ilut_setup = {"device": 0, "host": 1}[self.ilut_setup]
         if self.analysis_only:

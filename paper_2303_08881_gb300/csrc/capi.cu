@@ -294,17 +294,23 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.g = h.alloc<double>((size_t)m + 1, &e);
     f.h2 = h.alloc<double>((size_t)m + 1, &e);
     f.hnext = h.alloc<double>(1, &e);
+    f.y = h.alloc<double>((size_t)m + 1, &e);
     f.part = h.alloc<double>((size_t)(m + 2) * h.fg_G, &e);
     f.ctl = h.alloc<FgCtl>(1, &e);
-    if (!f.V || !f.Z || !f.w || !f.H || !f.cs || !f.sn || !f.g || !f.h2 || !f.hnext || !f.part || !f.ctl)
+    if (!f.V || !f.Z || !f.w || !f.H || !f.cs || !f.sn || !f.g || !f.h2 || !f.hnext || !f.y || !f.part || !f.ctl)
         return map_err(e);
     f.V32 = nullptr;
     f.w32 = nullptr;
-    f.upd32 = h.o.gs_precision == 2 ? 1 : 0;
+    f.Vlo = nullptr;
+    f.upd32 = h.o.gs_precision >= 2 ? 1 : 0;
     if (h.o.gs_precision > 0) {
         f.V32 = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
         f.w32 = h.alloc<float>((size_t)f.ld, &e);
         if (!f.V32 || !f.w32) return map_err(e);
+    }
+    if (h.o.gs_precision == 3) {
+        f.Vlo = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
+        if (!f.Vlo) return map_err(e);
     }
     CK(cudaMemsetAsync(f.ctl, 0, sizeof(FgCtl), h.st));
     f.m = m;
@@ -540,7 +546,7 @@ void ilu_opts_default(ilu_opts* o) {
     o->fill_level = 0;
     o->l1_block = 0;
     o->chain_sched = 0;
-    o->gs_precision = 2;
+    o->gs_precision = 3;
     o->autotune = 0;
     o->ilut_setup = 0;
     o->pivot_eps = 1e-8;
@@ -607,7 +613,7 @@ ilu_status ilu_setup(const ilu_csr* A, const int32_t* part, int32_t p, const ilu
         o.fill_level < 0 ||
         (o.fill_level > 0 && o.factor_B == ILU_FACT_ILUT) || o.l1_block < 0 || o.l1_block > 1 ||
         (o.l1_block && o.variant != ILU_VARIANT_BJ) || o.chain_sched < 0 || o.chain_sched > 2 ||
-        o.gs_precision < 0 || o.gs_precision > 2 || o.autotune < 0 || o.autotune > 1 || o.ilut_setup < 0 ||
+        o.gs_precision < 0 || o.gs_precision > 3 || o.autotune < 0 || o.autotune > 1 || o.ilut_setup < 0 ||
         o.ilut_setup > 1) {
         delete h;
         return ILU_ERR_ARG;

@@ -136,11 +136,14 @@ struct FgDev {
     double* g;      // m+1
     double* h2;     // m+1: reorthogonalisation coefficients of the current step
     double* hnext;  // 1: norm of the next basis vector
+    double* y;      // m: the least-squares solution R y = g of the cycle, written when it ends
     double* part;   // G x (m+1) partial sums
     FgCtl* ctl;
     float* V32;     // (m+1) x ld: FP32 copy of V for the first Gram-Schmidt pass (null: FP64 pass)
     float* w32;     // n: FP32 copy of w = A z_j for that pass
     int32_t upd32;  // the second pass's update w -= V h2 from V32 with FP32 products
+    float* Vlo;     // (m+1) x ld: V - V32 rounded to FP32, so V32 + Vlo carries ~48 bits of V;
+                    // non-null: w -= V h1 and the second pass's dots in double-float arithmetic
     int32_t m, G;
     int64_t ld;     // leading dimension of V and Z: n rounded up to 64 (512-byte rows)
 };

@@ -10,7 +10,8 @@
 // One Arnoldi step j (after z_j = M^{-1} v_j):
 //   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w (FP32 copies
 //                  of V and w by default: the second pass corrects their error)
-//   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w
+//   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w (FP64, or double-float
+//                  from a two-term FP32 split of V: k_fg_cgs_df)
 //   k_fg_norm      w -= V h2 (from the FP32 copy of V by default: h2 is then small), ||w||,
 //                  Givens rotation, residual estimate, stop decision
 //   k_fg_next      v_{j+1} = w / ||w||
@@ -63,14 +64,28 @@ __device__ __forceinline__ bool last_cta(uint32_t* counter) {
     return last;
 }
 
-// In the last CTA: out[i] = sum_c part[i*G + c] for i < m, fixed order.
-__device__ __forceinline__ void reduce_partials(const double* part, int G, int m, double* out) {
+// In the last CTA: out[i] = sum_c part[i*G + c] for i < m, fixed order. Lane l of the warp
+// that takes coefficient i sums partials l, l + 32, ... in groups of eight loads issued
+// together (one L2 round trip per group instead of one per partial), then the warp adds its
+// lanes. With addto, the sum is also added to addto[i] (by the same lane, in parallel).
+__device__ __forceinline__ void reduce_partials(const double* part, int G, int m, double* out,
+                                                double* addto = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < m; i += nw) {
+        const double* p = part + (size_t)i * G;
         double s = 0.0;
-        for (int c = lane; c < G; c += 32) s += __ldcg(part + (size_t)i * G + c);
+        for (int c0 = lane; c0 < G; c0 += 256) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = (c0 + 32 * u < G) ? __ldcg(p + c0 + 32 * u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; u++) s += v[u];
+        }
         s = warp_sum(s);
-        if (lane == 0) out[i] = s;
+        if (lane == 0) {
+            out[i] = s;
+            if (addto) addto[i] += s;
+        }
     }
     __syncthreads();
 }
@@ -145,13 +160,68 @@ __global__ void k_fg_resid(CsrDev A, FgDev f, const double* __restrict__ b, cons
     }
 }
 
+// ---- double-float arithmetic (Dekker 1971): a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi) / 2, about 48 significant bits. Every operation below is
+// an explicitly rounded intrinsic, so the compiler cannot contract a product into a sum and
+// break the error-free transformations.
+
+// x ~ hi + lo: hi = fl32(x), lo = fl32(x - hi) (x - hi is exact in FP64)
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+// Knuth's TwoSum: s + e = a + b exactly, s = fl(a + b)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (sh, sl) += (ah + al) * (bh + bl). The leading product ah * bh is split exactly into
+// p + e with one FMA (the TwoProduct of Ogita, Rump and Oishi, 2005); the cross terms
+// ah * bl + al * bh join e in FP32 (they are 2^-24 of the product, so their rounding is
+// 2^-48 of it) and al * bl is below that and left out. p goes into sh by TwoSum; its error
+// and e accumulate in sl, which df_renorm folds back from time to time.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    float t, err;
+    two_sum(sh, p, t, err);
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// restore |sl| <= ulp(sh) / 2 (TwoSum: no assumption on the sizes)
+__device__ __forceinline__ void df_renorm(float& sh, float& sl) {
+    float t, e;
+    two_sum(sh, sl, t, e);
+    sh = t;
+    sl = e;
+}
+
+// basis entry i (offset into V) in its FP32 forms: the rounded copy V32 and, with the
+// double-float second pass, the remainder Vlo
+__device__ __forceinline__ void store_basis32(const FgDev& f, size_t i, double v) {
+    if (f.Vlo) {
+        float hi, lo;
+        df_split(v, hi, lo);
+        f.V32[i] = hi;
+        f.Vlo[i] = lo;
+    } else {
+        f.V32[i] = (float)v;
+    }
+}
+
 __global__ void k_fg_scale0(FgDev f, int n) {
     if (f.ctl->cycle_done) return;
     const double inv = 1.0 / f.ctl->beta;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double v = f.V[r] * inv;
         f.V[r] = v;
-        if (f.V32) f.V32[r] = (float)v;
+        if (f.V32) store_basis32(f, r, v);
     }
 }
 
@@ -407,19 +477,165 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
     cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
     cta_partials(spart, j, f.part, f.G);
     if (!last_cta(&f.ctl->counter)) return;
-    reduce_partials(f.part, f.G, j + 1, f.h2);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i <= j; i++) f.H[(size_t)j * (f.m + 1) + i] += f.h2[i];
-        f.ctl->counter = 0;
-    }
+    reduce_partials(f.part, f.G, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
+    if (threadIdx.x == 0) f.ctl->counter = 0;
 }
 
-// w -= V h2; ||w||; Givens; estimate; stop decision
+// k_fg_cgs in double-float arithmetic from the split basis V32 + Vlo (gs_precision 3):
+// w -= V h1 and the reorthogonalisation dots V^T w without FP64 operations per basis entry
+// (GB300 issues FP32 at 64 times its FP64 rate, so the kernel is bound by reading the basis
+// once, 8 bytes per entry, instead of by FP64 fused multiply-adds). The CTA walks its row
+// slice in sub-slices of NT rows:
+//  * update: thread t takes row t of the sub-slice, sums h1_i (V32 + Vlo)_ir over i = 0..j
+//    in double-float (renormalised every 8 terms; 32 loads in flight per thread), subtracts
+//    the sum from w_r in FP64, and leaves w_r split in shared memory;
+//  * dots: vector i goes to warp i % (NT / 32); lane l adds the rows l, l + 32, ... of the
+//    sub-slice into its own double-float accumulator for i (shared memory), renormalised
+//    after each sub-slice; a warp takes two vectors per pass. The sub-slice's basis entries
+//    are read again here, from L1/L2.
+// At the end the 32 lane accumulators of a vector are added in FP64 by its warp, and the
+// CTA partials are combined in a fixed order by the last CTA, as in k_fg_cgs. Error: every
+// operation rounds at 2^-48 instead of FP64's 2^-53, so the update and the dots carry
+// errors ~(terms) * 2^-48 of the magnitudes summed: ~1e-13 ||w|| for 50 basis vectors,
+// far below the ~6e-8 ||w|| the second pass removes.
+// Dynamic shared memory: (j + 1) * 32 float2 accumulators.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int j) {
+    extern __shared__ float2 sacc[];
+    __shared__ float hh[kMaxJ + 1], hl[kMaxJ + 1];
+    __shared__ float wh[NT], wl[NT];
+    if (f.ctl->cycle_done) return;
+    int r0, r1;
+    cta_rows(n, r0, r1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    const double* Hj = f.H + (size_t)j * (f.m + 1);
+    for (int u = threadIdx.x; u <= j; u += NT) df_split(__ldcg(Hj + u), hh[u], hl[u]);
+    for (int u = threadIdx.x; u < (j + 1) * 32; u += NT) sacc[u] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const float* __restrict__ Vh = f.V32;
+    const float* __restrict__ Vl = f.Vlo;
+    const int64_t ld = f.ld;
+    for (int base = r0; base < r1; base += NT) {
+        const int r = base + threadIdx.x;
+        float whi = 0.f, wlo = 0.f;
+        if (r < r1) {
+            float sh = 0.f, sl = 0.f;
+            int i = 0;
+            for (; i + 16 <= j + 1; i += 16) {
+                float vh[16], vl[16];
+#pragma unroll
+                for (int u = 0; u < 16; u++) {
+                    vh[u] = Vh[(size_t)(i + u) * ld + r];
+                    vl[u] = Vl[(size_t)(i + u) * ld + r];
+                }
+#pragma unroll
+                for (int u = 0; u < 16; u++) {
+                    df_mac(sh, sl, hh[i + u], hl[i + u], vh[u], vl[u]);
+                    if (u == 7) df_renorm(sh, sl);
+                }
+                df_renorm(sh, sl);
+            }
+            if (i + 8 <= j + 1) {
+                float vh[8], vl[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    vh[u] = Vh[(size_t)(i + u) * ld + r];
+                    vl[u] = Vl[(size_t)(i + u) * ld + r];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) df_mac(sh, sl, hh[i + u], hl[i + u], vh[u], vl[u]);
+                df_renorm(sh, sl);
+                i += 8;
+            }
+            for (; i <= j; i++) df_mac(sh, sl, hh[i], hl[i], Vh[(size_t)i * ld + r], Vl[(size_t)i * ld + r]);
+            const double w1 = __dsub_rn(f.w[r], __dadd_rn((double)sh, (double)sl));
+            f.w[r] = w1;
+            df_split(w1, whi, wlo);
+        }
+        wh[threadIdx.x] = whi;
+        wl[threadIdx.x] = wlo;
+        __syncthreads();
+        // rows past the slice's end (the last sub-slice) read as zero: their w parts are zero
+        // and their basis entries are not loaded
+        const int cnt = min(NT, r1 - base);
+        for (int i = warp; i <= j; i += 2 * NW) {
+            // two vectors per pass (i and i + NW) so that twice the loads are in flight
+            const int i2 = i + NW;
+            const bool two = i2 <= j;
+            const float* __restrict__ ph = Vh + (size_t)i * ld + base;
+            const float* __restrict__ pl = Vl + (size_t)i * ld + base;
+            const float* __restrict__ qh = Vh + (size_t)(two ? i2 : i) * ld + base;
+            const float* __restrict__ ql = Vl + (size_t)(two ? i2 : i) * ld + base;
+            float xh[NT / 32], xl[NT / 32], yh[NT / 32], yl[NT / 32];
+#pragma unroll
+            for (int k = 0; k < NT / 32; k++) {
+                const int q = lane + 32 * k;
+                const bool in = q < cnt;
+                xh[k] = in ? ph[q] : 0.f;
+                xl[k] = in ? pl[q] : 0.f;
+                yh[k] = in ? qh[q] : 0.f;
+                yl[k] = in ? ql[q] : 0.f;
+            }
+            float2 a = sacc[i * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < NT / 32; k++) df_mac(a.x, a.y, xh[k], xl[k], wh[lane + 32 * k], wl[lane + 32 * k]);
+            df_renorm(a.x, a.y);
+            sacc[i * 32 + lane] = a;
+            if (two) {
+                float2 c = sacc[i2 * 32 + lane];
+#pragma unroll
+                for (int k = 0; k < NT / 32; k++)
+                    df_mac(c.x, c.y, yh[k], yl[k], wh[lane + 32 * k], wl[lane + 32 * k]);
+                df_renorm(c.x, c.y);
+                sacc[i2 * 32 + lane] = c;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = warp; i <= j; i += NW) {
+        const float2 a = sacc[i * 32 + lane];
+        const double t = warp_sum(__dadd_rn((double)a.x, (double)a.y));
+        if (lane == 0) f.part[(size_t)i * f.G + blockIdx.x] = t;
+    }
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
+    if (threadIdx.x == 0) f.ctl->counter = 0;
+}
+
+constexpr int kCgsDfThreads = 256;
+
+// Back substitution R y = g for the cycle's `steps` coefficients, by the whole CTA (one
+// thread per row, steps <= blockDim.x): column i of R (contiguous in H) is applied as soon as
+// y_i is known, and every thread prefetches its entry of the next column while the current
+// one is applied, so each of the `steps` rounds costs a block barrier, not a global-memory
+// round trip. rlast: column steps - 1 (held in shared memory by the caller); g: shared.
+__device__ __forceinline__ void solve_upper(const FgDev& f, int steps, const double* rlast, const double* g,
+                                            double* ys) {
+    const int l = threadIdx.x;
+    double gl = (l < steps) ? g[l] : 0.0;
+    double rnext = (l < steps) ? rlast[l] : 0.0;
+    for (int i = steps - 1; i >= 0; i--) {
+        const double rc = rnext;  // R[l][i], the entry of column i in row l
+        if (i > 0 && l < i) rnext = __ldcg(f.H + (size_t)(i - 1) * (f.m + 1) + l);
+        if (l == i) ys[i] = gl / rc;
+        __syncthreads();
+        if (l < i) gl -= rc * ys[i];
+    }
+    __syncthreads();
+}
+
+// w -= V h2; ||w||; Givens; estimate; stop decision. The last CTA loads the new Hessenberg
+// column, the earlier rotations and g into shared memory in parallel, thread 0 applies the
+// rotations there, and the results go back in parallel; when the cycle ends, the CTA also
+// solves R y = g for k_fg_update.
 __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     __shared__ double red[32];
     __shared__ double hh[kMaxJ + 1];
     __shared__ float hf[kMaxJ + 1];
     __shared__ double tot[1];
+    __shared__ double scol[kMaxJ + 2], scs[kMaxJ + 1], ssn[kMaxJ + 1], sg[kMaxJ + 2];
+    __shared__ int done_s;
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
@@ -437,72 +653,83 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
     if (!last_cta(&f.ctl->counter)) return;
     reduce_partials(f.part, f.G, 1, tot);
+    const int m1 = f.m + 1;
+    double* col = f.H + (size_t)j * m1;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        scol[i] = __ldcg(col + i);
+        sg[i] = __ldcg(f.g + i);
+        if (i < j) {
+            scs[i] = __ldcg(f.cs + i);
+            ssn[i] = __ldcg(f.sn + i);
+        }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         FgCtl* c = f.ctl;
         c->counter = 0;
         const double hn = sqrt(tot[0]);
-        const int m1 = f.m + 1;
-        double* col = f.H + (size_t)j * m1;
-        col[j + 1] = hn;
+        scol[j + 1] = hn;
         for (int i = 0; i < j; i++) {
-            const double a = f.cs[i] * col[i] + f.sn[i] * col[i + 1];
-            col[i + 1] = -f.sn[i] * col[i] + f.cs[i] * col[i + 1];
-            col[i] = a;
+            const double a = scs[i] * scol[i] + ssn[i] * scol[i + 1];
+            scol[i + 1] = -ssn[i] * scol[i] + scs[i] * scol[i + 1];
+            scol[i] = a;
         }
-        const double d = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+        const double d = sqrt(scol[j] * scol[j] + scol[j + 1] * scol[j + 1]);
         double cj, sj;
         if (d == 0.0) {
             cj = 1.0;
             sj = 0.0;
         } else {
-            cj = col[j] / d;
-            sj = col[j + 1] / d;
+            cj = scol[j] / d;
+            sj = scol[j + 1] / d;
         }
         f.cs[j] = cj;
         f.sn[j] = sj;
-        col[j] = cj * col[j] + sj * col[j + 1];
-        col[j + 1] = 0.0;
-        f.g[j + 1] = -sj * f.g[j];
-        f.g[j] = cj * f.g[j];
+        scol[j] = cj * scol[j] + sj * scol[j + 1];
+        scol[j + 1] = 0.0;
+        sg[j + 1] = -sj * sg[j];
+        sg[j] = cj * sg[j];
+        f.g[j + 1] = sg[j + 1];
+        f.g[j] = sg[j];
         c->total += 1;
         c->steps = j + 1;
-        c->est = fabs(f.g[j + 1]);
+        c->est = fabs(sg[j + 1]);
         *f.hnext = hn;  // norm of the new basis vector, for k_fg_next
+        int done = 0;
         if (c->est <= c->target || hn == 0.0 || c->total >= c->maxit || j + 1 == f.m) {
             c->cycle_done = 1;
+            done = 1;
             if (hn == 0.0) c->breakdown = 1;
         }
+        done_s = done;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = scol[i];
+    if (done_s) {
+        __shared__ double ys[kMaxJ + 1];
+        solve_upper(f, j + 1, scol, sg, ys);
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) f.y[i] = ys[i];
     }
 }
 
 __global__ void k_fg_next(FgDev f, int n, int j) {
     if (f.ctl->cycle_done) return;
     const double inv = 1.0 / __ldcg(f.hnext);
-    double* vn = f.V + (size_t)(j + 1) * f.ld;
-    float* vn32 = f.V32 ? f.V32 + (size_t)(j + 1) * f.ld : nullptr;
+    const size_t off = (size_t)(j + 1) * f.ld;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double v = f.w[r] * inv;
-        vn[r] = v;
-        if (vn32) vn32[r] = (float)v;
+        f.V[off + r] = v;
+        if (f.V32) store_basis32(f, off + r, v);
     }
 }
 
-// y = R^{-1} g (every CTA, redundantly); x += Z y on the CTA's rows
+// x += Z y on the CTA's rows (y = R^{-1} g, solved by k_fg_norm when the cycle ended)
 __global__ void k_fg_update(FgDev f, int n, double* __restrict__ x) {
     __shared__ double y[kMaxRestart];
-    __shared__ int steps_s;
-    if (threadIdx.x == 0) {
-        const int steps = f.ctl->steps;
-        for (int i = steps - 1; i >= 0; i--) {
-            double s = f.g[i];
-            for (int l = i + 1; l < steps; l++) s -= f.H[(size_t)l * (f.m + 1) + i] * y[l];
-            y[i] = s / f.H[(size_t)i * (f.m + 1) + i];
-        }
-        steps_s = steps;
-    }
-    __syncthreads();
-    const int steps = steps_s;
+    const int steps = f.ctl->steps;
     if (steps == 0) return;
+    for (int i = threadIdx.x; i < steps; i += blockDim.x) y[i] = __ldcg(f.y + i);
+    __syncthreads();
     int r0, r1;
     cta_rows(n, r0, r1);
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
@@ -606,7 +833,12 @@ cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t configure_krylov() { return cudaSuccess; }
+// the double-float k_fg_cgs takes up to (kMaxJ + 1) * 32 float2 of dynamic shared memory
+// (set on the current device whenever a handle sizes its FGMRES workspace)
+cudaError_t configure_krylov() {
+    return cudaFuncSetAttribute(k_fg_cgs_df<kCgsDfThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (kMaxJ + 1) * 32 * (int)sizeof(float2));
+}
 
 cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
     const int vl = pick_vl(h);
@@ -615,7 +847,10 @@ cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
 }
 
 cudaError_t launch_fg_cgs(const Handle& h, int j, cudaStream_t st) {
-    k_fg_cgs<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
+    if (h.fg.Vlo)
+        k_fg_cgs_df<kCgsDfThreads><<<h.fg_G, kCgsDfThreads, (size_t)(j + 1) * 32 * sizeof(float2), st>>>(h.fg, h.n, j);
+    else
+        k_fg_cgs<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
     return cudaGetLastError();
 }
 

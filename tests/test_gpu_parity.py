@@ -623,7 +623,7 @@ def test_gs_mixed_precision_keeps_fp64_fgmres(ilu, name, prec):
     cfg = CONFIGS[2]
     b = _dev(pr.b)
     out = {}
-    for mode in ("mixed2", "mixed1", "fp64"):
+    for mode in ("mixed3", "mixed2", "mixed1", "fp64"):
         h = ilu.ilu_setup_problem(pr, ilu.Opts(pc_precision=prec, gs_precision=mode, **cfg))
         x = torch.zeros_like(b)
         info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=3000)
@@ -631,7 +631,7 @@ def test_gs_mixed_precision_keeps_fp64_fgmres(ilu, name, prec):
         out[mode] = (info["iters"], x.cpu().numpy())
         h.close()
     i64, x64 = out["fp64"]
-    for mode in ("mixed1", "mixed2"):
+    for mode in ("mixed1", "mixed2", "mixed3"):
         i32, x32 = out[mode]
         assert abs(i32 - i64) <= 1, (mode, i32, i64)
         assert np.linalg.norm(x32 - x64) <= 1e-6 * np.linalg.norm(x64), mode
@@ -651,7 +651,7 @@ def test_gs_mixed_precision_keeps_the_basis_orthonormal(ilu, name):
     b = _dev(pr.b)
     m = 40
     loss = {}
-    for mode in ("fp64", "mixed1", "mixed2"):
+    for mode in ("fp64", "mixed1", "mixed2", "mixed3"):
         h = ilu.ilu_setup_problem(pr, ilu.Opts(gs_precision=mode, **CONFIGS[2]))
         x = torch.zeros_like(b)
         info = ilu.gmres_solve(h, b, x, rtol=1e-30, restart=m, maxit=m)
@@ -660,8 +660,34 @@ def test_gs_mixed_precision_keeps_the_basis_orthonormal(ilu, name):
         loss[mode] = np.abs(V @ V.T - np.eye(m - 1)).max()
         h.close()
     assert loss["fp64"] < 1e-13, loss
-    for mode in ("mixed1", "mixed2"):
+    for mode in ("mixed1", "mixed2", "mixed3"):
         assert loss[mode] <= max(10 * loss["fp64"], 1e-14) and loss[mode] < 1e-12, loss
+
+
+@pytest.mark.parametrize("restart", [50, 256])
+def test_gs_double_float_pass_on_full_row_slices(ilu, restart):
+    """The double-float second pass (mixed3) on a 512^2 grid, where every CTA's row slice holds
+    whole 256-row sub-slices and a ragged rest (the small problems above take only the ragged
+    path), and at the largest restart (the most shared-memory accumulators): the solve takes
+    the FP64 form's iteration count +-1 and reaches the same solution within 1e-6, and after
+    one FGMRES(40) cycle the basis is as orthonormal as the FP64 one."""
+    pr = P.aniso2d_boxes(512, 4, seed=7)
+    b = _dev(pr.b)
+    res = {}
+    for mode in ("fp64", "mixed3"):
+        h = ilu.ilu_setup_problem(pr, ilu.Opts(gs_precision=mode, **CONFIGS[2]))
+        x = torch.zeros_like(b)
+        info = ilu.gmres_solve(h, b, x, rtol=1e-8, restart=restart, maxit=4000)
+        assert info["status"] == 0 and info["rel_res_true"] <= 1e-8, (mode, info)
+        x1 = torch.zeros_like(b)
+        ilu.gmres_solve(h, b, x1, rtol=1e-30, restart=40, maxit=40)
+        V = h.krylov("V", 40)[1:]
+        res[mode] = (info["iters"], x.cpu().numpy(), np.abs(V @ V.T - np.eye(39)).max())
+        h.close()
+    (i64, x64, l64), (idf, xdf, ldf) = res["fp64"], res["mixed3"]
+    assert abs(idf - i64) <= 1, (idf, i64)
+    assert np.linalg.norm(xdf - x64) <= 1e-6 * np.linalg.norm(x64)
+    assert ldf <= max(10 * l64, 1e-14) and ldf < 1e-12, (ldf, l64)
 
 
 def test_restart_limit(ilu):
