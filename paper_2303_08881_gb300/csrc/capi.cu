@@ -295,6 +295,11 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.h2 = h.alloc<double>((size_t)m + 1, &e);
     f.hnext = h.alloc<double>(1, &e);
     f.y = h.alloc<double>((size_t)m + 1, &e);
+    const int ng = (h.fg_G + kRedGroup - 1) / kRedGroup;
+    f.gpart = h.alloc<double>((size_t)(m + 2) * ng, &e);
+    f.gcount = h.alloc<uint32_t>((size_t)ng, &e);
+    if (!f.gpart || !f.gcount) return map_err(e);
+    CK(cudaMemsetAsync(f.gcount, 0, sizeof(uint32_t) * ng, h.st));
     f.part = h.alloc<double>((size_t)(m + 2) * h.fg_G, &e);
     f.ctl = h.alloc<FgCtl>(1, &e);
     if (!f.V || !f.Z || !f.w || !f.H || !f.cs || !f.sn || !f.g || !f.h2 || !f.hnext || !f.y || !f.part || !f.ctl)

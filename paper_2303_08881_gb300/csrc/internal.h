@@ -137,6 +137,8 @@ struct FgDev {
     double* h2;     // m+1: reorthogonalisation coefficients of the current step
     double* hnext;  // 1: norm of the next basis vector
     double* y;      // m: the least-squares solution R y = g of the cycle, written when it ends
+    double* gpart;  // (m+2) x ng: partial sums of the groups of kRedGroup CTAs
+    uint32_t* gcount;  // ng: arrival counters of the groups (zero between launches)
     double* part;   // G x (m+1) partial sums
     FgCtl* ctl;
     float* V32;     // (m+1) x ld: FP32 copy of V for the first Gram-Schmidt pass (null: FP64 pass)
@@ -147,6 +149,9 @@ struct FgDev {
     int32_t m, G;
     int64_t ld;     // leading dimension of V and Z: n rounded up to 64 (512-byte rows)
 };
+
+// CTAs per first-level group of the two-level reductions of the FGMRES kernels
+constexpr int kRedGroup = 32;
 
 struct CsrDev {
     const int32_t* rp;

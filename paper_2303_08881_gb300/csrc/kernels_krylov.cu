@@ -90,6 +90,51 @@ __device__ __forceinline__ void reduce_partials(const double* part, int G, int m
     __syncthreads();
 }
 
+// Two-level form of last_cta + reduce_partials for the Gram-Schmidt kernels. The last CTA to
+// arrive in each group of kRedGroup consecutive CTAs sums the group's partials (lane c of the
+// warp that takes coefficient i adds CTA c of the group, then the warp's lanes), and the last
+// group to finish sums the group sums in group order. GB300 issues FP64 adds at 1/64 of its
+// FP32 rate, so one CTA summing every partial (m x G adds on one SM) was the kernels' tail;
+// here each level is a few FP64 adds per lane. Returns true in every thread of the CTA that
+// holds the final sums (out[i], and addto[i] += out[i] when addto is given); the counters are
+// back at zero when the kernel ends.
+__device__ __forceinline__ bool reduce_two_level(const FgDev& f, int m, double* out, double* addto = nullptr) {
+    const int G = f.G, ng = (G + kRedGroup - 1) / kRedGroup, g = blockIdx.x / kRedGroup;
+    const int c0 = g * kRedGroup, cn = min(G, c0 + kRedGroup) - c0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ bool last_s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_s = (atomicAdd(&f.gcount[g], 1u) == (uint32_t)cn - 1);
+    __syncthreads();
+    if (!last_s) return false;
+    __threadfence();
+    for (int i = warp; i < m; i += nw) {
+        double v = lane < cn ? __ldcg(f.part + (size_t)i * G + c0 + lane) : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) f.gpart[(size_t)i * ng + g] = v;
+    }
+    if (threadIdx.x == 0) f.gcount[g] = 0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_s = (atomicAdd(&f.ctl->counter, 1u) == (uint32_t)ng - 1);
+    __syncthreads();
+    if (!last_s) return false;
+    __threadfence();
+    for (int i = warp; i < m; i += nw) {
+        double v = 0.0;
+        for (int q = lane; q < ng; q += 32) v += __ldcg(f.gpart + (size_t)i * ng + q);
+        v = warp_sum(v);
+        if (lane == 0) {
+            out[i] = v;
+            if (addto) addto[i] += v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) f.ctl->counter = 0;
+    return true;
+}
+
 // ---------------------------------------------------------------------------------------
 template <int VL>
 __global__ void k_spmv(CsrDev A, const double* __restrict__ x, double* __restrict__ y) {
@@ -455,9 +500,7 @@ __global__ void __launch_bounds__(256) k_fg_spmv_dot(CsrDev A, FgDev f, int j) {
     else
         cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
     cta_partials(spart, j, f.part, f.G);
-    if (!last_cta(&f.ctl->counter)) return;
-    reduce_partials(f.part, f.G, j + 1, f.H + (size_t)j * (f.m + 1));
-    if (threadIdx.x == 0) f.ctl->counter = 0;
+    reduce_two_level(f, j + 1, f.H + (size_t)j * (f.m + 1));
 }
 
 // w -= V h1 (h1 = column j of H) and the reorthogonalisation dots V^T w; the last CTA
@@ -476,9 +519,7 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
     __syncthreads();
     cta_dots(f.V, f.ld, f.w, r0, r1, j, spart, stask);
     cta_partials(spart, j, f.part, f.G);
-    if (!last_cta(&f.ctl->counter)) return;
-    reduce_partials(f.part, f.G, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
-    if (threadIdx.x == 0) f.ctl->counter = 0;
+    reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
 }
 
 // k_fg_cgs in double-float arithmetic from the split basis V32 + Vlo (gs_precision 3):
@@ -489,8 +530,8 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
 //  * update: thread t takes row t of the sub-slice, sums h1_i (V32 + Vlo)_ir over i = 0..j
 //    in double-float (renormalised every 8 terms; 32 loads in flight per thread), subtracts
 //    the sum from w_r in FP64, and leaves w_r split in shared memory;
-//  * dots: vector i goes to warp i % (NT / 32); lane l adds the rows l, l + 32, ... of the
-//    sub-slice into its own double-float accumulator for i (shared memory), renormalised
+//  * dots: vector i goes to warp i % (NT / 32); lane l adds the row pairs l, l + 32, ... of
+//    the sub-slice into its own double-float accumulator for i (shared memory), renormalised
 //    after each sub-slice; a warp takes two vectors per pass. The sub-slice's basis entries
 //    are read again here, from L1/L2.
 // At the end the 32 lane accumulators of a vector are added in FP64 by its warp, and the
@@ -502,20 +543,25 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int j) {
     extern __shared__ float2 sacc[];
-    __shared__ float hh[kMaxJ + 1], hl[kMaxJ + 1];
-    __shared__ float wh[NT], wl[NT];
+    __shared__ __align__(16) float2 hcf[kMaxJ + 2];   // h1_i split: (hi, lo)
+    __shared__ __align__(16) float4 wpk[NT / 2];     // w of row pair q: (hi 2q, hi 2q+1, lo 2q, lo 2q+1)
     if (f.ctl->cycle_done) return;
     int r0, r1;
     cta_rows(n, r0, r1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NT / 32;
+    constexpr int NW = NT / 32, RP = NT / 64;  // row pairs per lane in the dots
     const double* Hj = f.H + (size_t)j * (f.m + 1);
-    for (int u = threadIdx.x; u <= j; u += NT) df_split(__ldcg(Hj + u), hh[u], hl[u]);
+    for (int u = threadIdx.x; u <= j + 1; u += NT) {
+        float a = 0.f, b = 0.f;
+        if (u <= j) df_split(__ldcg(Hj + u), a, b);
+        hcf[u] = make_float2(a, b);
+    }
     for (int u = threadIdx.x; u < (j + 1) * 32; u += NT) sacc[u] = make_float2(0.f, 0.f);
     __syncthreads();
     const float* __restrict__ Vh = f.V32;
     const float* __restrict__ Vl = f.Vlo;
     const int64_t ld = f.ld;
+    float* wflat = reinterpret_cast<float*>(wpk);
     for (int base = r0; base < r1; base += NT) {
         const int r = base + threadIdx.x;
         float whi = 0.f, wlo = 0.f;
@@ -530,9 +576,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
                     vl[u] = Vl[(size_t)(i + u) * ld + r];
                 }
 #pragma unroll
-                for (int u = 0; u < 16; u++) {
-                    df_mac(sh, sl, hh[i + u], hl[i + u], vh[u], vl[u]);
-                    if (u == 7) df_renorm(sh, sl);
+                for (int u = 0; u < 16; u += 2) {
+                    const float4 c = *reinterpret_cast<const float4*>(&hcf[i + u]);  // two coefficients
+                    df_mac(sh, sl, c.x, c.y, vh[u], vl[u]);
+                    df_mac(sh, sl, c.z, c.w, vh[u + 1], vl[u + 1]);
+                    if (u == 6) df_renorm(sh, sl);
                 }
                 df_renorm(sh, sl);
             }
@@ -544,49 +592,78 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
                     vl[u] = Vl[(size_t)(i + u) * ld + r];
                 }
 #pragma unroll
-                for (int u = 0; u < 8; u++) df_mac(sh, sl, hh[i + u], hl[i + u], vh[u], vl[u]);
+                for (int u = 0; u < 8; u += 2) {
+                    const float4 c = *reinterpret_cast<const float4*>(&hcf[i + u]);
+                    df_mac(sh, sl, c.x, c.y, vh[u], vl[u]);
+                    df_mac(sh, sl, c.z, c.w, vh[u + 1], vl[u + 1]);
+                }
                 df_renorm(sh, sl);
                 i += 8;
             }
-            for (; i <= j; i++) df_mac(sh, sl, hh[i], hl[i], Vh[(size_t)i * ld + r], Vl[(size_t)i * ld + r]);
+            for (; i <= j; i++) {
+                const float2 c = hcf[i];
+                df_mac(sh, sl, c.x, c.y, Vh[(size_t)i * ld + r], Vl[(size_t)i * ld + r]);
+            }
             const double w1 = __dsub_rn(f.w[r], __dadd_rn((double)sh, (double)sl));
             f.w[r] = w1;
             df_split(w1, whi, wlo);
         }
-        wh[threadIdx.x] = whi;
-        wl[threadIdx.x] = wlo;
+        {
+            const int t = threadIdx.x;
+            wflat[(t >> 1) * 4 + (t & 1)] = whi;
+            wflat[(t >> 1) * 4 + 2 + (t & 1)] = wlo;
+        }
         __syncthreads();
-        // rows past the slice's end (the last sub-slice) read as zero: their w parts are zero
-        // and their basis entries are not loaded
+        // dots: lane l takes the row pairs l, l + 32, ... of the sub-slice (64-bit loads of
+        // two rows' parts); two vectors (i and i + NW) per pass so that twice the loads are in
+        // flight. Rows past the slice's end (the last sub-slice) are neither loaded nor used.
         const int cnt = min(NT, r1 - base);
+        float4 wq[RP];
+#pragma unroll
+        for (int k = 0; k < RP; k++) wq[k] = wpk[lane + 32 * k];
         for (int i = warp; i <= j; i += 2 * NW) {
-            // two vectors per pass (i and i + NW) so that twice the loads are in flight
             const int i2 = i + NW;
             const bool two = i2 <= j;
             const float* __restrict__ ph = Vh + (size_t)i * ld + base;
             const float* __restrict__ pl = Vl + (size_t)i * ld + base;
             const float* __restrict__ qh = Vh + (size_t)(two ? i2 : i) * ld + base;
             const float* __restrict__ ql = Vl + (size_t)(two ? i2 : i) * ld + base;
-            float xh[NT / 32], xl[NT / 32], yh[NT / 32], yl[NT / 32];
+            float2 xh[RP], xl[RP], yh[RP], yl[RP];
+            if (cnt == NT) {
 #pragma unroll
-            for (int k = 0; k < NT / 32; k++) {
-                const int q = lane + 32 * k;
-                const bool in = q < cnt;
-                xh[k] = in ? ph[q] : 0.f;
-                xl[k] = in ? pl[q] : 0.f;
-                yh[k] = in ? qh[q] : 0.f;
-                yl[k] = in ? ql[q] : 0.f;
+                for (int k = 0; k < RP; k++) {
+                    const int q = 2 * (lane + 32 * k);
+                    xh[k] = *reinterpret_cast<const float2*>(ph + q);
+                    xl[k] = *reinterpret_cast<const float2*>(pl + q);
+                    yh[k] = *reinterpret_cast<const float2*>(qh + q);
+                    yl[k] = *reinterpret_cast<const float2*>(ql + q);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < RP; k++) {
+                    const int q = 2 * (lane + 32 * k);
+                    const bool a0 = q < cnt, a1 = q + 1 < cnt;
+                    xh[k] = make_float2(a0 ? ph[q] : 0.f, a1 ? ph[q + 1] : 0.f);
+                    xl[k] = make_float2(a0 ? pl[q] : 0.f, a1 ? pl[q + 1] : 0.f);
+                    yh[k] = make_float2(a0 ? qh[q] : 0.f, a1 ? qh[q + 1] : 0.f);
+                    yl[k] = make_float2(a0 ? ql[q] : 0.f, a1 ? ql[q + 1] : 0.f);
+                }
             }
             float2 a = sacc[i * 32 + lane];
 #pragma unroll
-            for (int k = 0; k < NT / 32; k++) df_mac(a.x, a.y, xh[k], xl[k], wh[lane + 32 * k], wl[lane + 32 * k]);
+            for (int k = 0; k < RP; k++) {
+                df_mac(a.x, a.y, xh[k].x, xl[k].x, wq[k].x, wq[k].z);
+                df_mac(a.x, a.y, xh[k].y, xl[k].y, wq[k].y, wq[k].w);
+            }
             df_renorm(a.x, a.y);
             sacc[i * 32 + lane] = a;
             if (two) {
                 float2 c = sacc[i2 * 32 + lane];
 #pragma unroll
-                for (int k = 0; k < NT / 32; k++)
-                    df_mac(c.x, c.y, yh[k], yl[k], wh[lane + 32 * k], wl[lane + 32 * k]);
+                for (int k = 0; k < RP; k++) {
+                    df_mac(c.x, c.y, yh[k].x, yl[k].x, wq[k].x, wq[k].z);
+                    df_mac(c.x, c.y, yh[k].y, yl[k].y, wq[k].y, wq[k].w);
+                }
                 df_renorm(c.x, c.y);
                 sacc[i2 * 32 + lane] = c;
             }
@@ -598,9 +675,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
         const double t = warp_sum(__dadd_rn((double)a.x, (double)a.y));
         if (lane == 0) f.part[(size_t)i * f.G + blockIdx.x] = t;
     }
-    if (!last_cta(&f.ctl->counter)) return;
-    reduce_partials(f.part, f.G, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
-    if (threadIdx.x == 0) f.ctl->counter = 0;
+    reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
 }
 
 constexpr int kCgsDfThreads = 256;
