@@ -101,6 +101,10 @@ __device__ __forceinline__ double seq_sum_ldcg(const double* a, int m) {
     return s;
 }
 
+// fused multiply-add rounded once, never re-associated by the compiler
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class T>
 __device__ __forceinline__ T to_t(double v) {
     return (T)v;

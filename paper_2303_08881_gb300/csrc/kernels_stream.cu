@@ -679,22 +679,57 @@ __device__ bool grid_sync(InnerCtl* ctl, uint32_t nblocks, uint32_t& epoch, uint
     return ok_s != 0;
 }
 
+// terms of the deferred second Gram-Schmidt update w2 = w1 - V h2 that the next step forms
+// where it needs an entry (later steps store w2 and pass a third barrier)
+constexpr int kLazyMax = 3;
+
+// w - sum_t h[t] V_t, t < nt <= kLazyMax, at entry gi of the interface: the loads issued
+// together, then one explicitly rounded fused multiply-add per term, so every CTA that
+// evaluates it (the owner of the row and the CTAs that gather it through C_off) obtains the
+// same bits
+template <class T>
+__device__ __forceinline__ T lazy_sub(T w, const T* __restrict__ V, const T* hv, int nt, int n2, int gi) {
+    T vv[kLazyMax];
+#pragma unroll
+    for (int t = 0; t < kLazyMax; t++) vv[t] = t < nt ? __ldcg(V + (size_t)t * n2 + gi) : (T)0;
+#pragma unroll
+    for (int t = 0; t < kLazyMax; t++)
+        if (t < nt) w = fma_rn(-hv[t], vv[t], w);
+    return w;
+}
+
 // All k steps of the inner GMRES on the preconditioned Schur system (Eq. preSS) in one
 // cooperative launch, one CTA per subdomain, W0 = c = S~^{-1} g' and its norm partials
-// left by the forward kernel. Step j, with three grid barriers:
-//   A: v_j = W_in / ||W_in||; t = C_off v_j on the CTA's interface rows (other CTAs' W_in
-//      read through L2); x = S~_s^{-1} t (the streamed local Schur program); w = v_j + x;
-//      partial dots V_i . w (i <= j)
-//   B: h1 = sum of the partials (every CTA, fixed order); w -= V h1; partial dots again
-//   C: h2 likewise; w -= V h2; partial ||w||^2; w stored for the next step's C_off.
-// The Hessenberg entries go to ctl (CTA 0); k_bwd_s solves the least squares. Every CTA
-// forms each norm from the same partials in the same order, so the stopping decisions
-// (c = 0, breakdown) are uniform and no CTA leaves the barriers early.
+// left by the forward kernel. Step j, with two grid barriers:
+//   A: v_j = w2 / ||w2|| of the previous step (or W0 / ||W0||); t = C_off v_j on the CTA's
+//      interface rows, the entries of other CTAs formed from what they stored; x = S~_s^{-1}
+//      t (the streamed local Schur program); w = v_j + x; partial dots V_i . w (i <= j)
+//   B: h1 = sum of the partials (every CTA, fixed order); w1 = w - V h1, stored for the
+//      other CTAs; partial dots V_i . w1 and partial ||w1||^2
+//   C: h2 likewise; ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 = w2 + V h2 with V h2 orthogonal to
+//      w2), the same in every CTA. The next step forms v_{j+1} = (w1 - V h2) / ||w2||
+//      wherever it needs an entry, so no barrier closes C. If the subtraction cancels
+//      (||w2||^2 <= 1e-2 ||w1||^2, near a breakdown), or from step kLazyMax on, the step
+//      falls back to w2 stored explicitly, its norm partials and a third barrier. The last step stores w2 and its
+//      norm partials for the least squares of k_bwd_s, which starts after this launch.
+// The Hessenberg entries go to ctl (CTA 0). Every CTA forms each norm from the same partials
+// in the same order, so the stopping decisions (c = 0, breakdown) are uniform and no CTA
+// leaves the barriers early.
 template <class T, int RW, bool XS, class V = T>
 __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, RingCfg cfg, InnerDev<T> in, T* xg,
                                                     const int32_t* done) {
     __shared__ double red[32 * 8];
     __shared__ double hh[kMaxInner + 1];
+    __shared__ T hT[kMaxInner + 1];   // the current coefficients in T
+    __shared__ T hlz[kMaxInner + 1];  // h2 of the previous step, for w2 = w1 - V h2
+    // per-step scalars, formed by thread 0 only (GB300 issues FP64 at 1/64 of its FP32 rate,
+    // so a square root or a division in every warp costs thousands of cycles), in the
+    // preconditioner type T: the inner GMRES is part of the preconditioner, and with T =
+    // float its vectors and partial sums carry FP32 accuracy anyway
+    using ST = T;
+    __shared__ double nrm_s, beta_s, a_s;
+    __shared__ T inv_s;
+    __shared__ int stop_s, lazy_s;
     if (done && *done) return;
     InnerCtl* ctl = in.ctl;
     const int s = blockIdx.x, p = sd.p, n2 = sd.n2, tid = threadIdx.x;
@@ -702,27 +737,44 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
     const int g0 = sd.if_ptr[s];
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     T* x = xvec<T, XS>(sm, xg + ni, q0);
-    const double* nbank = in.part + ((size_t)2 * (kMaxInner + 1)) * p;
-    double beta = 0.0;
+    double* const nbank = in.part + ((size_t)2 * (kMaxInner + 1)) * p;  // ||w||^2 partials
+    double* const nbank2 = nbank + p;                                     // fallback ||w2||^2
     uint32_t gepoch = 0;  // grid barriers passed (thread 0)
-    for (int j = 0; j < in.k; j++) {
-        // ---- A
-        const double nrm = sqrt(warp_allsum_ldcg(nbank, p));
+    // thread 0: the norm of v_j's numerator is nrm; stopping tests, 1 / nrm
+    auto set_norm = [&](int j, ST nrm_t) {
+        const double nrm = (double)nrm_t;
+        nrm_s = nrm;
+        int stop = 0;
         if (j == 0) {
-            beta = nrm;
-            if (s == 0 && tid == 0) ctl->beta = nrm;
+            beta_s = nrm;
+            if (s == 0) ctl->beta = nrm;
             if (nrm == 0.0) {
-                if (s == 0 && tid == 0) ctl->zero = 1;
-                break;
+                if (s == 0) ctl->zero = 1;
+                stop = 1;
             }
         } else {
-            if (s == 0 && tid == 0) ctl->H[(j - 1) * (kMaxInner + 1) + j] = nrm;
-            if (nrm <= 1e-14 * beta) {  // lucky breakdown: the Krylov space is exhausted
-                if (s == 0 && tid == 0) ctl->steps = j;
-                break;
+            if (s == 0) ctl->H[(j - 1) * (kMaxInner + 1) + j] = nrm;
+            if (nrm <= 1e-14 * beta_s) {  // lucky breakdown: the Krylov space is exhausted
+                if (s == 0) ctl->steps = j;
+                stop = 1;
             }
         }
-        const T inv = (T)(1.0 / nrm);
+        stop_s = stop;
+        inv_s = stop ? (T)0 : (T)1 / nrm_t;
+    };
+    if (tid < 32) {
+        const double a = warp_allsum_ldcg(nbank, p);
+        if (tid == 0) {
+            set_norm(0, (ST)sqrt((ST)a));
+            lazy_s = 0;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < in.k; j++) {
+        // ---- A
+        if (stop_s) break;
+        const T inv = inv_s;
+        const int nlz = lazy_s ? j : 0;  // terms of the correction w1 - V h2
         const T* __restrict__ Win = (j & 1) ? in.W1 : in.W0;
         T* __restrict__ Wout = (j & 1) ? in.W0 : in.W1;
         // copies start only past the stopping tests: every copy issued is consumed (and
@@ -737,11 +789,32 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
             T acc = (T)0;
             for (int q0 = qa; q0 < qb; q0 += 4) {  // four gathers in flight, summed in order
                 T cv[4], wv[4];
+                int c[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const bool ok = q0 + u < qb;
+                    c[u] = ok ? in.coff_ci[q0 + u] : 0;
                     cv[u] = ok ? in.coff_v[q0 + u] : (T)0;
-                    wv[u] = ok ? __ldcg(Win + in.coff_ci[q0 + u]) : (T)0;
+                }
+                if (nlz) {
+                    // the gathers and their correction terms issued together
+                    T vv[4][kLazyMax];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const bool ok = q0 + u < qb;
+                        wv[u] = ok ? __ldcg(Win + c[u]) : (T)0;
+#pragma unroll
+                        for (int t = 0; t < kLazyMax; t++)
+                            vv[u][t] = (ok && t < nlz) ? __ldcg(in.V + (size_t)t * n2 + c[u]) : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+#pragma unroll
+                        for (int t = 0; t < kLazyMax; t++)
+                            if (t < nlz) wv[u] = fma_rn(-hlz[t], vv[u][t], wv[u]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) wv[u] = (q0 + u < qb) ? __ldcg(Win + c[u]) : (T)0;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++) acc += cv[u] * wv[u];
@@ -754,11 +827,14 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
         T* Vj = in.V + (size_t)j * n2;
         for (int i = tid; i < nf; i += blockDim.x) {
             const int gi = g0 + i;
-            const T v = __ldcg(Win + gi) * inv;
+            T wv = __ldcg(Win + gi);
+            if (nlz) wv = lazy_sub<T>(wv, in.V, hlz, nlz, n2, gi);
+            const T v = wv * inv;
             Vj[gi] = v;
             x[i] = v + x[i];
         }
         __syncthreads();
+        const bool last = j + 1 == in.k;
         for (int bank = 0; bank < 2; bank++) {
             // partial dots V_i . w, i <= j, into bank 0 (A) or 1 (B)
             for (int i0 = 0; i0 <= j; i0 += 8) {
@@ -776,13 +852,28 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
                     for (int u = 0; u < 8 && i0 + u <= j; u++)
                         in.part[((size_t)(bank * (kMaxInner + 1) + i0 + u)) * p + s] = (double)acc[u];
             }
+            if (bank == 1 && !last) {
+                // ||w1||^2 beside the second dots
+                T n1 = (T)0;
+                for (int i = tid; i < nf; i += blockDim.x) n1 += x[i] * x[i];
+                n1 = block_sum_t<T>(n1, reinterpret_cast<T*>(red));
+                if (tid == 0) nbank[s] = (double)n1;
+            }
             if (!grid_sync(ctl, (uint32_t)p, gepoch, cfg.spin, cfg.err)) return;
             // ---- B (bank 0) / C (bank 1): coefficients, Hessenberg column, update
             {
                 const int lane = tid & 31, nw = blockDim.x >> 5;
                 for (int i = tid >> 5; i <= j; i += nw) {
                     const double h = warp_allsum_ldcg(in.part + ((size_t)(bank * (kMaxInner + 1) + i)) * p, p);
-                    if (lane == 0) hh[i] = h;
+                    if (lane == 0) {
+                        hh[i] = h;
+                        hT[i] = (T)h;
+                    }
+                }
+                // the last warp sums the ||w1||^2 partials (its coefficients, if any, are done)
+                if (bank == 1 && !last && (tid >> 5) == nw - 1) {
+                    const double a = warp_allsum_ldcg(nbank, p);
+                    if (lane == 0) a_s = a;
                 }
             }
             __syncthreads();
@@ -791,21 +882,56 @@ __global__ void __launch_bounds__(256) k_inner_coop(SubDev sd, StreamDev<T> S, R
                     double& H = ctl->H[j * (kMaxInner + 1) + i];
                     H = bank ? H + hh[i] : hh[i];
                 }
-            T nacc = (T)0;
-            for (int i = tid; i < nf; i += blockDim.x) {
-                T w = x[i];
-                for (int t = 0; t <= j; t++) w -= (T)hh[t] * in.V[(size_t)t * n2 + g0 + i];
-                x[i] = w;
-                if (bank) {
+            if (bank == 0) {
+                for (int i = tid; i < nf; i += blockDim.x) {
+                    T w = x[i];
+                    for (int t = 0; t <= j; t++) w -= hT[t] * in.V[(size_t)t * n2 + g0 + i];
+                    x[i] = w;
+                    Wout[g0 + i] = w;  // w1, read by the other CTAs in the next step
+                }
+                __syncthreads();
+                continue;
+            }
+            // C: ||w2||^2 = ||w1||^2 - ||h2||^2, the same in every CTA (thread 0 forms it)
+            if (tid == 0) {
+                int lz = 0;
+                if (!last && j + 1 <= kLazyMax) {
+                    const ST a = (ST)a_s;
+                    ST hs = (ST)0;
+                    for (int i = 0; i <= j; i++) hs += (ST)hh[i] * (ST)hh[i];
+                    const ST d = a - hs;
+                    if (d > (ST)1e-2 * a) {
+                        lz = 1;
+                        set_norm(j + 1, (ST)sqrt(d));
+                    }
+                }
+                lazy_s = lz;
+            }
+            for (int i = tid; i <= j; i += blockDim.x) hlz[i] = hT[i];
+            __syncthreads();
+            if (!lazy_s) {
+                // the last step, or cancellation: w2 explicitly, its norm partials
+                T nacc = (T)0;
+                for (int i = tid; i < nf; i += blockDim.x) {
+                    T w = x[i];
+                    for (int t = 0; t <= j; t++) w -= hT[t] * in.V[(size_t)t * n2 + g0 + i];
+                    x[i] = w;
                     Wout[g0 + i] = w;
                     nacc += w * w;
                 }
-            }
-            __syncthreads();
-            if (bank) {
+                __syncthreads();
                 nacc = block_sum_t<T>(nacc, reinterpret_cast<T*>(red));
-                if (tid == 0) in.part[((size_t)2 * (kMaxInner + 1)) * p + s] = (double)nacc;
-                if (!grid_sync(ctl, (uint32_t)p, gepoch, cfg.spin, cfg.err)) return;
+                if (last) {
+                    if (tid == 0) nbank[s] = (double)nacc;  // for the least squares
+                } else {
+                    if (tid == 0) nbank2[s] = (double)nacc;
+                    if (!grid_sync(ctl, (uint32_t)p, gepoch, cfg.spin, cfg.err)) return;
+                    if (tid < 32) {
+                        const double a = warp_allsum_ldcg(nbank2, p);
+                        if (tid == 0) set_norm(j + 1, (ST)sqrt((ST)a));
+                    }
+                    __syncthreads();
+                }
             }
         }
     }
