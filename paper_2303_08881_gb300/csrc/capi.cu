@@ -293,7 +293,7 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.sn = h.alloc<double>((size_t)m + 1, &e);
     f.g = h.alloc<double>((size_t)m + 1, &e);
     f.h2 = h.alloc<double>((size_t)m + 1, &e);
-    f.hnext = h.alloc<double>(1, &e);
+    f.hnext = h.alloc<double>(2, &e);
     f.y = h.alloc<double>((size_t)m + 1, &e);
     const int ng = (h.fg_G + kRedGroup - 1) / kRedGroup;
     f.gpart = h.alloc<double>((size_t)(m + 2) * ng, &e);

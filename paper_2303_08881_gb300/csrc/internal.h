@@ -135,7 +135,7 @@ struct FgDev {
     double* sn;
     double* g;      // m+1
     double* h2;     // m+1: reorthogonalisation coefficients of the current step
-    double* hnext;  // 1: norm of the next basis vector
+    double* hnext;  // 2: norm of the next basis vector and its inverse (of beta after k_fg_resid)
     double* y;      // m: the least-squares solution R y = g of the cycle, written when it ends
     double* gpart;  // (m+2) x ng: partial sums of the groups of kRedGroup CTAs
     uint32_t* gcount;  // ng: arrival counters of the groups (zero between launches)

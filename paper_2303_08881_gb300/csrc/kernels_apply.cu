@@ -254,7 +254,7 @@ __global__ void k_bwd(SubDev sd, ProgDev<T> PB, InnerDev<T> in, const double* __
     if (done && *done) return;
     const int s = blockIdx.x;
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
-    const int steps = (sd.n2 > 0) ? inner_lsq(in.ctl, in.part, sd.p, in.k, t) : 0;
+    const int steps = (sd.n2 > 0) ? inner_lsq<T>(in.ctl, in.part, sd.p, in.k, t) : 0;
     T* x = work_vec<T>(sd, xg, q0, ns);
     if (ef) {
         for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)r[sd.q_orig[q0 + l]];
@@ -278,7 +278,7 @@ __global__ void k_inner_finish(SubDev sd, InnerDev<T> in, double* __restrict__ y
     __shared__ double t[kMaxInner];
     const int s = blockIdx.x;
     const int ns = sd.qoff[s + 1] - sd.qoff[s], ni = sd.nint[s], nf = ns - ni;
-    const int steps = inner_lsq(in.ctl, in.part, sd.p, in.k, t);
+    const int steps = inner_lsq<T>(in.ctl, in.part, sd.p, in.k, t);
     const int g0 = sd.if_ptr[s];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         T acc = (T)0;

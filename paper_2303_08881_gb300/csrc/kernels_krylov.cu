@@ -189,6 +189,7 @@ __global__ void k_fg_resid(CsrDev A, FgDev f, const double* __restrict__ b, cons
         }
         const double beta = sqrt(tot[0]);
         c->beta = beta;
+        f.hnext[1] = beta > 0.0 ? 1.0 / beta : 0.0;  // for k_fg_scale0 (one FP64 division)
         c->res_true = beta;
         c->steps = 0;
         c->est = beta;
@@ -262,7 +263,7 @@ __device__ __forceinline__ void store_basis32(const FgDev& f, size_t i, double v
 
 __global__ void k_fg_scale0(FgDev f, int n) {
     if (f.ctl->cycle_done) return;
-    const double inv = 1.0 / f.ctl->beta;
+    const double inv = __ldcg(f.hnext + 1);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double v = f.V[r] * inv;
         f.V[r] = v;
@@ -769,7 +770,8 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
         c->total += 1;
         c->steps = j + 1;
         c->est = fabs(sg[j + 1]);
-        *f.hnext = hn;  // norm of the new basis vector, for k_fg_next
+        f.hnext[0] = hn;  // norm of the new basis vector and its inverse, for k_fg_next
+        f.hnext[1] = hn > 0.0 ? 1.0 / hn : 0.0;
         int done = 0;
         if (c->est <= c->target || hn == 0.0 || c->total >= c->maxit || j + 1 == f.m) {
             c->cycle_done = 1;
@@ -789,7 +791,7 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
 
 __global__ void k_fg_next(FgDev f, int n, int j) {
     if (f.ctl->cycle_done) return;
-    const double inv = 1.0 / __ldcg(f.hnext);
+    const double inv = __ldcg(f.hnext + 1);
     const size_t off = (size_t)(j + 1) * f.ld;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double v = f.w[r] * inv;

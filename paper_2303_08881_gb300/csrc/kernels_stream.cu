@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(256) k_rap_fin_s(SubDev sd, StreamDev<T> S, Ri
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     ring_start(S, s, sm, cfg.nst);
-    const int steps = inner_lsq(in.ctl, in.part, sd.p, in.k, tt);
+    const int steps = inner_lsq<T>(in.ctl, in.part, sd.p, in.k, tt);
     T* x = xvec<T, XS>(sm, xg, q0);
     const int g0 = sd.if_ptr[s];
     for (int l = threadIdx.x; l < ni; l += blockDim.x) x[l] = (T)0;
@@ -1064,7 +1064,7 @@ __global__ void __launch_bounds__(256) k_bwd_s(SubDev sd, StreamDev<T> S, RingCf
     const int q0 = sd.qoff[s], ns = sd.qoff[s + 1] - q0, ni = sd.nint[s], nf = ns - ni;
     const Smem sm = smem_parts(cfg.nst, S.chunk);
     ring_start(S, s, sm, cfg.nst);
-    const int steps = (sd.n2 > 0) ? inner_lsq(in.ctl, in.part, sd.p, in.k, tt) : 0;
+    const int steps = (sd.n2 > 0) ? inner_lsq<T>(in.ctl, in.part, sd.p, in.k, tt) : 0;
     T* x = xvec<T, XS>(sm, xg, q0);
     if (ef)
         gather(x, r, sd.q_orig + q0, ni);
