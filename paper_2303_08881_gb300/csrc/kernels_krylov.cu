@@ -248,6 +248,24 @@ __device__ __forceinline__ void df_renorm(float& sh, float& sl) {
     sl = e;
 }
 
+// (ah, al) += (bh, bl), both double-float
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    two_sum(s, e, ah, al);
+}
+
+// sum of a double-float value over the 32 lanes of a warp (butterfly: every lane ends with
+// the same bits, TwoSum being exact whatever the order of its operands)
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(kFull, h, o), bl = __shfl_xor_sync(kFull, l, o);
+        df_add(h, l, bh, bl);
+    }
+}
+
 // basis entry i (offset into V) in its FP32 forms: the rounded copy V32 and, with the
 // double-float second pass, the remainder Vlo
 __device__ __forceinline__ void store_basis32(const FgDev& f, size_t i, double v) {
@@ -671,10 +689,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
         }
         __syncthreads();
     }
+    // the lanes' accumulators of a vector summed in double-float by its warp (FP32 shuffles
+    // and adds; an FP64 warp sum per vector kept GB300's FP64 pipe a third busy), then one
+    // conversion to the FP64 partial
     for (int i = warp; i <= j; i += NW) {
-        const float2 a = sacc[i * 32 + lane];
-        const double t = warp_sum(__dadd_rn((double)a.x, (double)a.y));
-        if (lane == 0) f.part[(size_t)i * f.G + blockIdx.x] = t;
+        float2 a = sacc[i * 32 + lane];
+        df_warp_sum(a.x, a.y);
+        if (lane == 0) f.part[(size_t)i * f.G + blockIdx.x] = __dadd_rn((double)a.x, (double)a.y);
     }
     reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
 }
