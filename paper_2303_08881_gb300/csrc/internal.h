@@ -122,6 +122,7 @@ struct FgCtl {
     int32_t breakdown;
     int32_t m;
     uint32_t counter;   // last-CTA-done counter
+    int32_t fuse;       // k_fg_cgs_df ended the current step (||w2|| from ||w1||^2 - ||h2||^2)
     double res_true;
     int32_t err;        // host mirror of the device error word (filled by the host copy)
 };

@@ -541,6 +541,8 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
     reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
 }
 
+__device__ __forceinline__ void fg_step_tail(const FgDev& f, int j, double hn);
+
 // k_fg_cgs in double-float arithmetic from the split basis V32 + Vlo (gs_precision 3):
 // w -= V h1 and the reorthogonalisation dots V^T w without FP64 operations per basis entry
 // (GB300 issues FP32 at 64 times its FP64 rate, so the kernel is bound by reading the basis
@@ -553,12 +555,15 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
 //    the sub-slice into its own double-float accumulator for i (shared memory), renormalised
 //    after each sub-slice; a warp takes two vectors per pass. The sub-slice's basis entries
 //    are read again here, from L1/L2.
-// At the end the 32 lane accumulators of a vector are added in FP64 by its warp, and the
-// CTA partials are combined in a fixed order by the last CTA, as in k_fg_cgs. Error: every
+// The dots also accumulate ||w1||^2 (w1 against itself, as coefficient j + 1). At the end
+// the 32 lane accumulators of each are added by its warp, and the CTA partials are combined
+// in a fixed order (reduce_two_level). The last CTA adds h2 to H and, unless the subtraction
+// cancels, takes ||w2||^2 = ||w1||^2 - ||h2||^2 and ends the Arnoldi step (fg_step_tail):
+// k_fg_norm is then skipped and k_fg_next forms w2 = w1 - V h2 as it normalises. Error: every
 // operation rounds at 2^-48 instead of FP64's 2^-53, so the update and the dots carry
 // errors ~(terms) * 2^-48 of the magnitudes summed: ~1e-13 ||w|| for 50 basis vectors,
 // far below the ~6e-8 ||w|| the second pass removes.
-// Dynamic shared memory: (j + 1) * 32 float2 accumulators.
+// Dynamic shared memory: (j + 2) * 32 float2 accumulators (the last for ||w1||^2).
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int j) {
     extern __shared__ float2 sacc[];
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
         if (u <= j) df_split(__ldcg(Hj + u), a, b);
         hcf[u] = make_float2(a, b);
     }
-    for (int u = threadIdx.x; u < (j + 1) * 32; u += NT) sacc[u] = make_float2(0.f, 0.f);
+    for (int u = threadIdx.x; u < (j + 2) * 32; u += NT) sacc[u] = make_float2(0.f, 0.f);
     __syncthreads();
     const float* __restrict__ Vh = f.V32;
     const float* __restrict__ Vl = f.Vlo;
@@ -687,17 +692,52 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
                 sacc[i2 * 32 + lane] = c;
             }
         }
+        if (warp == (j + 1) % NW) {  // ||w1||^2 as accumulator j + 1 (rows past the slice are zero)
+            float2 a = sacc[(j + 1) * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < RP; k++) {
+                df_mac(a.x, a.y, wq[k].x, wq[k].z, wq[k].x, wq[k].z);
+                df_mac(a.x, a.y, wq[k].y, wq[k].w, wq[k].y, wq[k].w);
+            }
+            df_renorm(a.x, a.y);
+            sacc[(j + 1) * 32 + lane] = a;
+        }
         __syncthreads();
     }
     // the lanes' accumulators of a vector summed in double-float by its warp (FP32 shuffles
     // and adds; an FP64 warp sum per vector kept GB300's FP64 pipe a third busy), then one
     // conversion to the FP64 partial
-    for (int i = warp; i <= j; i += NW) {
+    // (coefficient j + 1: the CTA's ||w1||^2)
+    for (int i = warp; i <= j + 1; i += NW) {
         float2 a = sacc[i * 32 + lane];
         df_warp_sum(a.x, a.y);
         if (lane == 0) f.part[(size_t)i * f.G + blockIdx.x] = __dadd_rn((double)a.x, (double)a.y);
     }
-    reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
+    if (!reduce_two_level(f, j + 2, f.h2)) return;
+    // the last CTA: h2 into column j of H, and ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 = w2 + V h2,
+    // V h2 orthogonal to w2). Without cancellation this ends the step here and k_fg_next forms
+    // w2; otherwise k_fg_norm forms w2 and its norm explicitly.
+    __shared__ int fuse_s;
+    __shared__ double hn_s;
+    double* col = f.H + (size_t)j * (f.m + 1);
+    for (int i = threadIdx.x; i <= j; i += NT) col[i] += __ldcg(f.h2 + i);
+    if (warp == 0) {
+        double hs = 0.0;
+        for (int i = lane; i <= j; i += 32) {
+            const double h = __ldcg(f.h2 + i);
+            hs += h * h;
+        }
+        hs = warp_sum(hs);
+        if (lane == 0) {
+            const double a = __ldcg(f.h2 + j + 1), d = a - hs;
+            const int fu = d > 1e-2 * a;
+            fuse_s = fu;
+            hn_s = fu ? sqrt(d) : 0.0;
+            f.ctl->fuse = fu;
+        }
+    }
+    __syncthreads();
+    if (fuse_s) fg_step_tail(f, j, hn_s);
 }
 
 constexpr int kCgsDfThreads = 256;
@@ -722,34 +762,15 @@ __device__ __forceinline__ void solve_upper(const FgDev& f, int steps, const dou
     __syncthreads();
 }
 
-// w -= V h2; ||w||; Givens; estimate; stop decision. The last CTA loads the new Hessenberg
-// column, the earlier rotations and g into shared memory in parallel, thread 0 applies the
-// rotations there, and the results go back in parallel; when the cycle ends, the CTA also
-// solves R y = g for k_fg_update.
-__global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
-    __shared__ double red[32];
-    __shared__ double hh[kMaxJ + 1];
-    __shared__ float hf[kMaxJ + 1];
-    __shared__ double tot[1];
+// The end of Arnoldi step j, by the whole last CTA of a kernel, given hn = ||w2|| = h_{j+1,j}:
+// the new Hessenberg column, the earlier rotations and g go to shared memory in parallel,
+// thread 0 applies the rotations there, the results go back in parallel; then the estimate,
+// the stop decision, the norm and its inverse for k_fg_next and, when the cycle ends, R y = g
+// for k_fg_update.
+__device__ __forceinline__ void fg_step_tail(const FgDev& f, int j, double hn) {
     __shared__ double scol[kMaxJ + 2], scs[kMaxJ + 1], ssn[kMaxJ + 1], sg[kMaxJ + 2];
+    __shared__ double ys[kMaxJ + 1];
     __shared__ int done_s;
-    if (f.ctl->cycle_done) return;
-    int r0, r1;
-    cta_rows(n, r0, r1);
-    for (int u = threadIdx.x; u <= j; u += blockDim.x) {
-        hh[u] = __ldcg(f.h2 + u);
-        hf[u] = (float)hh[u];
-    }
-    __syncthreads();
-    double acc = 0.0;
-    if (f.upd32)
-        cta_update32(f.V32, f.ld, f.w, hf, r0, r1, j, &acc);
-    else
-        cta_update(f.V, f.ld, f.w, hh, r0, r1, j, &acc);
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
-    if (!last_cta(&f.ctl->counter)) return;
-    reduce_partials(f.part, f.G, 1, tot);
     const int m1 = f.m + 1;
     double* col = f.H + (size_t)j * m1;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
@@ -763,8 +784,6 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     __syncthreads();
     if (threadIdx.x == 0) {
         FgCtl* c = f.ctl;
-        c->counter = 0;
-        const double hn = sqrt(tot[0]);
         scol[j + 1] = hn;
         for (int i = 0; i < j; i++) {
             const double a = scs[i] * scol[i] + ssn[i] * scol[i + 1];
@@ -804,20 +823,96 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     __syncthreads();
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = scol[i];
     if (done_s) {
-        __shared__ double ys[kMaxJ + 1];
         solve_upper(f, j + 1, scol, sg, ys);
         for (int i = threadIdx.x; i <= j; i += blockDim.x) f.y[i] = ys[i];
     }
 }
 
-__global__ void k_fg_next(FgDev f, int n, int j) {
+// w -= V h2; ||w||; then the step's end (fg_step_tail). With the double-float Gram-Schmidt
+// this kernel runs only when k_fg_cgs_df could not take ||w2|| from the Pythagorean relation
+// (FgCtl::fuse = 0); otherwise that kernel has ended the step and k_fg_next forms w2 itself.
+__global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
+    __shared__ double red[32];
+    __shared__ double hh[kMaxJ + 1];
+    __shared__ float hf[kMaxJ + 1];
+    __shared__ double tot[1];
+    if (f.ctl->cycle_done || f.ctl->fuse) return;
+    int r0, r1;
+    cta_rows(n, r0, r1);
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) {
+        hh[u] = __ldcg(f.h2 + u);
+        hf[u] = (float)hh[u];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    if (f.upd32)
+        cta_update32(f.V32, f.ld, f.w, hf, r0, r1, j, &acc);
+    else
+        cta_update(f.V, f.ld, f.w, hh, r0, r1, j, &acc);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) f.part[blockIdx.x] = acc;
+    if (!last_cta(&f.ctl->counter)) return;
+    reduce_partials(f.part, f.G, 1, tot);
+    if (threadIdx.x == 0) f.ctl->counter = 0;
+    fg_step_tail(f, j, sqrt(tot[0]));
+}
+
+// v_{j+1} = w2 / ||w2||. When k_fg_cgs_df ended the step (FgCtl::fuse), w holds w1 and this
+// kernel forms w2 = w1 - V h2 itself, as k_fg_norm would have (FP32 products of the FP32
+// basis copy summed in FP32, the sum subtracted in FP64), four rows per thread.
+__global__ void __launch_bounds__(256) k_fg_next(FgDev f, int n, int j) {
+    __shared__ float hf[kMaxJ + 1];
     if (f.ctl->cycle_done) return;
     const double inv = __ldcg(f.hnext + 1);
     const size_t off = (size_t)(j + 1) * f.ld;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const double v = f.w[r] * inv;
-        f.V[off + r] = v;
-        if (f.V32) store_basis32(f, off + r, v);
+    if (!f.ctl->fuse) {
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+            const double v = f.w[r] * inv;
+            f.V[off + r] = v;
+            if (f.V32) store_basis32(f, off + r, v);
+        }
+        return;
+    }
+    for (int u = threadIdx.x; u <= j; u += blockDim.x) hf[u] = (float)__ldcg(f.h2 + u);
+    __syncthreads();
+    const float* __restrict__ V32 = f.V32;
+    const int64_t ld = f.ld;
+    const int nth = gridDim.x * blockDim.x;
+    // r is a multiple of 4 below n <= ld (a multiple of 64): the four rows' loads stay inside
+    // the basis vectors; rows at or past n are not stored
+    for (int r = 4 * (blockIdx.x * blockDim.x + threadIdx.x); r < n; r += 4 * nth) {
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        int i = 0;
+        for (; i + 8 <= j + 1; i += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = ld4f(V32 + (size_t)(i + u) * ld + r);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const float hv = hf[i + u];
+                c.x += hv * v[u].x;
+                c.y += hv * v[u].y;
+                c.z += hv * v[u].z;
+                c.w += hv * v[u].w;
+            }
+        }
+        for (; i <= j; i++) {
+            const float4 v = ld4f(V32 + (size_t)i * ld + r);
+            const float hv = hf[i];
+            c.x += hv * v.x;
+            c.y += hv * v.y;
+            c.z += hv * v.z;
+            c.w += hv * v.w;
+        }
+        const float cq[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (r + q < n) {
+                const double v = (f.w[r + q] - (double)cq[q]) * inv;
+                f.V[off + r + q] = v;
+                store_basis32(f, off + r + q, v);
+            }
+        }
     }
 }
 
@@ -935,7 +1030,7 @@ cudaError_t launch_fg_scale0(const Handle& h, cudaStream_t st) {
 // (set on the current device whenever a handle sizes its FGMRES workspace)
 cudaError_t configure_krylov() {
     return cudaFuncSetAttribute(k_fg_cgs_df<kCgsDfThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (kMaxJ + 1) * 32 * (int)sizeof(float2));
+                                (kMaxJ + 2) * 32 * (int)sizeof(float2));
 }
 
 cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
@@ -946,7 +1041,7 @@ cudaError_t launch_fg_spmv_dot(const Handle& h, int j, cudaStream_t st) {
 
 cudaError_t launch_fg_cgs(const Handle& h, int j, cudaStream_t st) {
     if (h.fg.Vlo)
-        k_fg_cgs_df<kCgsDfThreads><<<h.fg_G, kCgsDfThreads, (size_t)(j + 1) * 32 * sizeof(float2), st>>>(h.fg, h.n, j);
+        k_fg_cgs_df<kCgsDfThreads><<<h.fg_G, kCgsDfThreads, (size_t)(j + 2) * 32 * sizeof(float2), st>>>(h.fg, h.n, j);
     else
         k_fg_cgs<<<h.fg_G, h.fg_threads, 0, st>>>(h.fg, h.n, j);
     return cudaGetLastError();
