@@ -104,10 +104,18 @@ def class_bytes(sz, prec, iters, m, k, gs="mixed3"):
     w32 = 8 * n if mixed else 0                     # the FP32 copy of w written and read
     vlo = 4 * n if gs == "mixed3" else 0            # the low FP32 part of each new basis vector
     b["fg_spmv_dot"] = sum(spmv + 16 * n + w32 + v1 * (j + 1) * n for j in js)
-    # the first update and the second pass's dots: FP64 basis, or its two FP32 parts (8 bytes either way)
-    b["fg_cgs"] = sum(8 * (j + 1) * n + 16 * n for j in js)
-    b["fg_norm"] = sum(v2 * (j + 1) * n + 16 * n for j in js)
-    b["fg_next"] = sum((16 + (4 if w32 else 0)) * n + vlo for j in js if j + 1 < m)
+    if gs == "mixed3":
+        # k_fg_cgs_df: both FP32 parts of the basis, w read and written, w1 split written; it
+        # ends the step, k_fg_norm exits at once, and k_fg_next forms w2 from the FP32 copy
+        # (w1's two parts read; V, V32 and Vlo written)
+        b["fg_cgs"] = sum(8 * (j + 1) * n + 24 * n for j in js)
+        b["fg_norm"] = 0
+        b["fg_next"] = sum(4 * (j + 1) * n + 24 * n for j in js if j + 1 < m)
+    else:
+        # the first update and the second pass's dots from the FP64 basis
+        b["fg_cgs"] = sum(8 * (j + 1) * n + 16 * n for j in js)
+        b["fg_norm"] = sum(v2 * (j + 1) * n + 16 * n for j in js)
+        b["fg_next"] = sum((16 + (4 if w32 else 0)) * n + vlo for j in js if j + 1 < m)
     b["fg_update"] = sum(8 * s * n + 16 * n for s in steps)
     b["fg_resid"] = (cycles + 1) * (spmv + 24 * n)
     b["fg_scale0"] = (cycles + 1) * 16 * n
@@ -146,9 +154,13 @@ def class_flops64(sz, iters, m, gs="mixed3"):
     f = {}
     mixed = gs in ("mixed1", "mixed2", "mixed3")
     f["fg_spmv_dot"] = sum(2 * nnz + (0 if mixed else 2 * (j + 1) * n) for j in js)
-    # mixed3: the update and the dots in double-float (FP32) arithmetic, one FP64 subtraction per row
+    # mixed3: the update and the dots in double-float (FP32) arithmetic, one FP64 subtraction per
+    # row; the second update and the normalisation in k_fg_next, one FP64 addition per row
     f["fg_cgs"] = sum((n if gs == "mixed3" else 4 * (j + 1) * n) for j in js)
-    f["fg_norm"] = sum((3 * n if gs in ("mixed2", "mixed3") else 2 * (j + 1) * n + 2 * n) for j in js)
+    if gs == "mixed3":
+        f["fg_norm"] = 0
+    else:
+        f["fg_norm"] = sum((3 * n if gs == "mixed2" else 2 * (j + 1) * n + 2 * n) for j in js)
     f["fg_next"] = sum(n for j in js if j + 1 < m)
     f["fg_update"] = sum(2 * s * n for s in steps)
     f["fg_resid"] = (cycles + 1) * (2 * nnz + 3 * n)

@@ -301,8 +301,10 @@ ilu_status ilu_get_ilut_factor(void* h, int32_t s, int32_t* rowptr, int32_t* col
 /* The Krylov basis of the handle's last gmres_solve (its last cycle): which = 0 the
    orthonormal vectors v_0..v_{k-1} (k <= restart + 1), which = 1 the preconditioned
    vectors z_0..z_{k-1} (k <= restart); out: HOST double[k * n], vector i at out + i * n, in
-   the original ordering. Vectors past the cycle's last step hold stale values. Synchronises
-   the stream. Errors: ILU_ERR_ARG (null pointers, which or k out of range, no solve yet). */
+   the original ordering. Vectors past the cycle's last step hold stale values. With
+   gs_precision = 3 the basis is kept as two FP32 parts and v = hi + lo is returned.
+   Synchronises the stream. Errors: ILU_ERR_ARG (null pointers, which or k out of range, no
+   solve yet). */
 ilu_status ilu_get_krylov(void* h, int32_t which, int32_t k, double* out);
 
 /* What ilu_setup chose for the streamed programs (0 block Jacobi, 1 forward, 2 local Schur,

@@ -2,6 +2,7 @@
 // device factorisation, apply dispatch and the FGMRES driver (one CUDA graph per cycle,
 // one host read of the device control block per cycle).
 #include <algorithm>
+#include <vector>
 #include <chrono>
 #include <cstring>
 #include <mutex>
@@ -307,6 +308,7 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     f.V32 = nullptr;
     f.w32 = nullptr;
     f.Vlo = nullptr;
+    f.wlo = nullptr;
     f.upd32 = h.o.gs_precision >= 2 ? 1 : 0;
     if (h.o.gs_precision > 0) {
         f.V32 = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
@@ -315,7 +317,8 @@ ilu_status ensure_fgmres(Handle& h, int m) {
     }
     if (h.o.gs_precision == 3) {
         f.Vlo = h.alloc<float>((size_t)(m + 1) * (size_t)f.ld, &e);
-        if (!f.Vlo) return map_err(e);
+        f.wlo = h.alloc<float>((size_t)f.ld, &e);
+        if (!f.Vlo || !f.wlo) return map_err(e);
     }
     CK(cudaMemsetAsync(f.ctl, 0, sizeof(FgCtl), h.st));
     f.m = m;
@@ -1010,6 +1013,19 @@ ilu_status ilu_get_krylov(void* hp, int32_t which, int32_t k, double* out) {
     if (!hp || !out || which < 0 || which > 1 || k < 1) return ILU_ERR_ARG;
     Handle* h = (Handle*)hp;
     if (h->o.analysis_only || !h->fg.V || k > (which == 0 ? h->fg_m + 1 : h->fg_m)) return ILU_ERR_ARG;
+    if (which == 0 && h->fg.Vlo) {
+        // the double-float Gram-Schmidt keeps the basis as two FP32 parts: v = hi + lo (the
+        // FP64 array holds their sum, rounded)
+        const size_t nk = (size_t)h->n * (size_t)k;
+        std::vector<float> hi(nk), lo(nk);
+        CK(cudaMemcpy2DAsync(hi.data(), (size_t)h->n * sizeof(float), h->fg.V32, (size_t)h->fg.ld * sizeof(float),
+                             (size_t)h->n * sizeof(float), (size_t)k, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpy2DAsync(lo.data(), (size_t)h->n * sizeof(float), h->fg.Vlo, (size_t)h->fg.ld * sizeof(float),
+                             (size_t)h->n * sizeof(float), (size_t)k, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (size_t i = 0; i < nk; i++) out[i] = (double)hi[i] + (double)lo[i];
+        return ILU_OK;
+    }
     const double* src = which == 0 ? h->fg.V : h->fg.Z;
     CK(cudaMemcpy2DAsync(out, (size_t)h->n * sizeof(double), src, (size_t)h->fg.ld * sizeof(double),
                          (size_t)h->n * sizeof(double), (size_t)k, cudaMemcpyDeviceToHost, h->st));

@@ -143,7 +143,8 @@ struct FgDev {
     double* part;   // G x (m+1) partial sums
     FgCtl* ctl;
     float* V32;     // (m+1) x ld: FP32 copy of V for the first Gram-Schmidt pass (null: FP64 pass)
-    float* w32;     // n: FP32 copy of w = A z_j for that pass
+    float* w32;     // n: FP32 copy of w = A z_j for that pass (with Vlo: then hi part of w1)
+    float* wlo;     // n: with Vlo, the lo part of w1 (w1 = w32 + wlo to ~48 bits)
     int32_t upd32;  // the second pass's update w -= V h2 from V32 with FP32 products
     float* Vlo;     // (m+1) x ld: V - V32 rounded to FP32, so V32 + Vlo carries ~48 bits of V;
                     // non-null: w -= V h1 and the second pass's dots in double-float arithmetic

@@ -631,6 +631,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
             const double w1 = __dsub_rn(f.w[r], __dadd_rn((double)sh, (double)sl));
             f.w[r] = w1;
             df_split(w1, whi, wlo);
+            f.w32[r] = whi;  // w1 split, for k_fg_next
+            f.wlo[r] = wlo;
         }
         {
             const int t = threadIdx.x;
@@ -857,9 +859,22 @@ __global__ void __launch_bounds__(256) k_fg_norm(FgDev f, int n, int j) {
     fg_step_tail(f, j, sqrt(tot[0]));
 }
 
-// v_{j+1} = w2 / ||w2||. When k_fg_cgs_df ended the step (FgCtl::fuse), w holds w1 and this
-// kernel forms w2 = w1 - V h2 itself, as k_fg_norm would have (FP32 products of the FP32
-// basis copy summed in FP32, the sum subtracted in FP64), four rows per thread.
+// (ah, al) * (bh, bl), both double-float: TwoProduct of the high parts by FMA, the cross
+// terms in FP32, renormalised by TwoSum
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    two_sum(p, e, h, l);
+}
+
+// v_{j+1} = w2 / ||w2||. When k_fg_cgs_df ended the step (FgCtl::fuse), this kernel forms
+// w2 = w1 - V h2 itself, as k_fg_norm would have (FP32 products of the FP32 basis copy summed
+// in FP32), four rows per thread, and the rest in double-float arithmetic: w1 arrives split
+// (w32 + wlo), w2 and v = w2 * (1 / ||w2||) are pairs of FP32 numbers, stored as the two FP32
+// parts of the basis; the FP64 basis vector, the input of the next preconditioner apply, is
+// their sum (one FP64 addition per row instead of the subtraction, product and split).
 __global__ void __launch_bounds__(256) k_fg_next(FgDev f, int n, int j) {
     __shared__ float hf[kMaxJ + 1];
     if (f.ctl->cycle_done) return;
@@ -875,6 +890,8 @@ __global__ void __launch_bounds__(256) k_fg_next(FgDev f, int n, int j) {
     }
     for (int u = threadIdx.x; u <= j; u += blockDim.x) hf[u] = (float)__ldcg(f.h2 + u);
     __syncthreads();
+    float ih, il;  // 1 / ||w2|| split
+    df_split(inv, ih, il);
     const float* __restrict__ V32 = f.V32;
     const int64_t ld = f.ld;
     const int nth = gridDim.x * blockDim.x;
@@ -908,9 +925,12 @@ __global__ void __launch_bounds__(256) k_fg_next(FgDev f, int n, int j) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (r + q < n) {
-                const double v = (f.w[r + q] - (double)cq[q]) * inv;
-                f.V[off + r + q] = v;
-                store_basis32(f, off + r + q, v);
+                float sh = f.w32[r + q], sl = f.wlo[r + q], vh, vl;
+                df_add(sh, sl, -cq[q], 0.f);
+                df_mul(sh, sl, ih, il, vh, vl);
+                f.V32[off + r + q] = vh;
+                f.Vlo[off + r + q] = vl;
+                f.V[off + r + q] = __dadd_rn((double)vh, (double)vl);  // the preconditioner's input
             }
         }
     }
@@ -1053,7 +1073,9 @@ cudaError_t launch_fg_norm(const Handle& h, int j, cudaStream_t st) {
 }
 
 cudaError_t launch_fg_next(const Handle& h, int j, cudaStream_t st) {
-    k_fg_next<<<h.sm_count * 4, 256, 0, st>>>(h.fg, h.n, j);
+    // the double-float form takes four rows per thread: one pass over n
+    const int blocks = std::max(h.sm_count * 4, (h.n + 1023) / 1024);
+    k_fg_next<<<blocks, 256, 0, st>>>(h.fg, h.n, j);
     return cudaGetLastError();
 }
 
