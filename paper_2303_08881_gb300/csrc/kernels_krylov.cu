@@ -541,8 +541,6 @@ __global__ void __launch_bounds__(256) k_fg_cgs(FgDev f, int n, int j) {
     reduce_two_level(f, j + 1, f.h2, f.H + (size_t)j * (f.m + 1));
 }
 
-__device__ __forceinline__ void fg_step_tail(const FgDev& f, int j, double hn);
-
 // k_fg_cgs in double-float arithmetic from the split basis V32 + Vlo (gs_precision 3):
 // w -= V h1 and the reorthogonalisation dots V^T w without FP64 operations per basis entry
 // (GB300 issues FP32 at 64 times its FP64 rate, so the kernel is bound by reading the basis
@@ -558,8 +556,8 @@ __device__ __forceinline__ void fg_step_tail(const FgDev& f, int j, double hn);
 // The dots also accumulate ||w1||^2 (w1 against itself, as coefficient j + 1). At the end
 // the 32 lane accumulators of each are added by its warp, and the CTA partials are combined
 // in a fixed order (reduce_two_level). The last CTA adds h2 to H and, unless the subtraction
-// cancels, takes ||w2||^2 = ||w1||^2 - ||h2||^2 and ends the Arnoldi step (fg_step_tail):
-// k_fg_norm is then skipped and k_fg_next forms w2 = w1 - V h2 as it normalises. Error: every
+// cancels, takes ||w2||^2 = ||w1||^2 - ||h2||^2: k_fg_norm is then skipped, and k_fg_next
+// ends the Arnoldi step (fg_step_tail) and forms w2 = w1 - V h2 as it normalises. Error: every
 // operation rounds at 2^-48 instead of FP64's 2^-53, so the update and the dots carry
 // errors ~(terms) * 2^-48 of the magnitudes summed: ~1e-13 ||w|| for 50 basis vectors,
 // far below the ~6e-8 ||w|| the second pass removes.
@@ -719,8 +717,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
     // the last CTA: h2 into column j of H, and ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 = w2 + V h2,
     // V h2 orthogonal to w2). Without cancellation this ends the step here and k_fg_next forms
     // w2; otherwise k_fg_norm forms w2 and its norm explicitly.
-    __shared__ int fuse_s;
-    __shared__ double hn_s;
     double* col = f.H + (size_t)j * (f.m + 1);
     for (int i = threadIdx.x; i <= j; i += NT) col[i] += __ldcg(f.h2 + i);
     if (warp == 0) {
@@ -733,13 +729,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fg_cgs_df(FgDev f, int n, int
         if (lane == 0) {
             const double a = __ldcg(f.h2 + j + 1), d = a - hs;
             const int fu = d > 1e-2 * a;
-            fuse_s = fu;
-            hn_s = fu ? sqrt(d) : 0.0;
             f.ctl->fuse = fu;
+            if (fu) {  // the norm and its inverse for k_fg_next, whose CTA 0 ends the step
+                const double hn = sqrt(d);
+                f.hnext[0] = hn;
+                f.hnext[1] = 1.0 / hn;
+            }
         }
     }
-    __syncthreads();
-    if (fuse_s) fg_step_tail(f, j, hn_s);
 }
 
 constexpr int kCgsDfThreads = 256;
@@ -888,6 +885,10 @@ __global__ void __launch_bounds__(256) k_fg_next(FgDev f, int n, int j) {
         }
         return;
     }
+    // CTA 0 first ends the Arnoldi step (Givens rotations, estimate, stop decision): a chain
+    // of dependent FP64 operations on one thread, hidden behind the other CTAs' rows. If it
+    // ends the cycle, CTAs starting later skip their rows; v_{j+1} is then not needed.
+    if (blockIdx.x == 0) fg_step_tail(f, j, __ldcg(f.hnext));
     for (int u = threadIdx.x; u <= j; u += blockDim.x) hf[u] = (float)__ldcg(f.h2 + u);
     __syncthreads();
     float ih, il;  // 1 / ||w2|| split
