@@ -134,8 +134,12 @@ typedef struct {
                              ~48 significant bits, error-free products and sums) from a two-term
                              FP32 split of every basis vector kept beside V (4 more bytes per
                              basis entry): no FP64 operation per basis entry, one FP64
-                             subtraction per row. All FP32 forms need the entries of w within
-                             the FP32 range. The
+                             subtraction per row. In this mode ||w2|| is taken as
+                             (||w1||^2 - ||h2||^2)^(1/2), ||w1||^2 summed in double-float beside
+                             the dots (w1 = w2 + V h2, V h2 orthogonal to w2), and w2 / ||w2|| is
+                             formed in double-float; when the subtraction cancels
+                             (||w2||^2 <= 1e-2 ||w1||^2) ||w2|| is formed explicitly.
+                             All FP32 forms need the entries of w within the FP32 range. The
                              coefficients H = h1 + h2, w itself, ||w||, the Givens rotations,
                              the solution update and the true residual are FP64 in every mode. */
     int32_t autotune;     /* streamed path: 1 = ilu_setup measures, for each streamed program, the

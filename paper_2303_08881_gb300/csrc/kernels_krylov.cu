@@ -2,19 +2,22 @@
 // outer Krylov method is FGMRES because the inner Schur GMRES makes M^{-1} vary).
 //
 // Every kernel partitions the n rows into G contiguous CTA ranges. Reductions write one
-// partial per CTA; the last CTA to finish (atomic ticket after a fence) combines the
-// partials in a fixed order, so every result is independent of timing. The Arnoldi
-// state (Hessenberg, Givens rotations, residual estimate, the cycle flag) lives on the
-// device: the host reads it once per cycle.
+// partial per CTA, combined in a fixed order (by the last CTA to finish, or in two levels
+// through groups of CTAs), so every result is independent of timing. The Arnoldi state
+// (Hessenberg, Givens rotations, residual estimate, the cycle flag) lives on the device: the
+// host reads it once per cycle.
 //
 // One Arnoldi step j (after z_j = M^{-1} v_j):
 //   k_fg_spmv_dot  w = A z_j and the first Gram-Schmidt dots V_{0..j}^T w (FP32 copies
 //                  of V and w by default: the second pass corrects their error)
-//   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w (FP64, or double-float
-//                  from a two-term FP32 split of V: k_fg_cgs_df)
+//   k_fg_cgs       w -= V h1 and the reorthogonalisation dots V^T w (FP64), or
+//   k_fg_cgs_df    the same in double-float from a two-term FP32 split of V (the default),
+//                  with ||w1||^2 and, from ||w1||^2 - ||h2||^2, the new norm
 //   k_fg_norm      w -= V h2 (from the FP32 copy of V by default: h2 is then small), ||w||,
-//                  Givens rotation, residual estimate, stop decision
-//   k_fg_next      v_{j+1} = w / ||w||
+//                  Givens rotation, residual estimate, stop decision; with k_fg_cgs_df only
+//                  when its norm cancels
+//   k_fg_next      v_{j+1} = w / ||w||; after k_fg_cgs_df it forms w = w1 - V h2 itself, and
+//                  its CTA 0 takes the Givens rotation, estimate and stop decision
 #include <algorithm>
 
 #include "devutil.cuh"
