@@ -1078,10 +1078,11 @@ def test_paper_iteration_counts(case):
 @pytest.mark.parametrize("case", _golden_cases(True),
                          ids=lambda c: f'{c["problem"]}-p{c["p"]}-{c.get("variant", "bj")}-{c.get("local_order", "natural")}')
 def test_paper_iteration_counts_slow(case):
-    """Larger printed counts: 3D Poisson 128^3 at Np=1 (~65 s); block Jacobi on 2D grids
-    split into 2 and 4 blocks of whole grid rows (~25 s, ~80 s); ILU(2) on 3D
-    convection-diffusion 128^3 with FGMRES(100) (~75 s); RAP-MILU(0) on 1024 x 2048 in 32
-    blocks (~7 min); block Jacobi on 3D 128 x 128 x 256 in 2 blocks (~6 min)."""
+    """Larger printed counts (opt-in): block Jacobi on 2D grids split into 4 and 8 blocks of
+    whole grid rows (~80 s, ~3 min); ILU(2) on 3D convection-diffusion 128^3 with
+    FGMRES(100) (~75 s); RAP-MILU(0) on 1024 x 2048 in 32 blocks (~7 min); block Jacobi on
+    3D 128 x 128 x 256 in 2 blocks (~6 min). The 3D Poisson 128^3 count at Np=1 and the 2D
+    block Jacobi count in 2 blocks run by default (about 100 s together)."""
     assert _run_paper_case(case) == case["iters"]
 
 
