@@ -188,6 +188,23 @@ void prog_push_row(ProgHost& P, const FPat& F, int32_t q0, int32_t r, int32_t cl
     P.pdsrc.push_back(upper ? (int32_t)(F.base + F.dpos[q0 + r]) : -1);
 }
 
+// Levels [l0, l1) of program S (rows with their entries) appended to program D as levels
+// of its own.
+void prog_copy_levels(ProgHost& D, const ProgHost& S, int32_t l0, int32_t l1) {
+    for (int32_t l = l0; l < l1; l++) {
+        for (int32_t k = S.lvl_ptr[l]; k < S.lvl_ptr[l + 1]; k++) {
+            D.prow.push_back(S.prow[k]);
+            for (int32_t e = S.pptr[k]; e < S.pptr[k + 1]; e++) {
+                D.pcol.push_back(S.pcol[e]);
+                D.psrc.push_back(S.psrc[e]);
+            }
+            D.pptr.push_back((int32_t)D.pcol.size());
+            D.pdsrc.push_back(S.pdsrc[k]);
+        }
+        prog_close_level(D);
+    }
+}
+
 int32_t row_count(const FPat& F, int32_t q0, int32_t r, int32_t clo, int32_t chi, bool upper) {
     int32_t cnt = 0;
     for (int32_t k = F.rp[q0 + r]; k < F.rp[q0 + r + 1]; k++) {
@@ -1604,22 +1621,10 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                 // the B parts (L_B, U_B, W, Z): factor_B's factorisation for SCHUR; for RAP the
                 // factorisation that defines R and P (Eq. wzinmilu), factor_S's
                 const FPat& fb = rap ? h.f2 : h.f1;
-                {   // forward: f' = L_B^{-1} f then g' = g - W f'   (W/Z)
-                    //          t = U_B^{-1} L_B^{-1} f then g' = g - E t   (E/F)
-                    ProgHost& P = G[PR_FWD];
-                    int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
-                    if (wz) {
-                        a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
-                    } else {
-                        a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
-                        a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
-                    }
-                    P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
-                    P.max_levels = std::max(P.max_levels, a);
-                }
                 {   // forward and the first local Schur solve in one program (base 0); the
                     // chain section starts at the interface rows (the W or E product)
                     ProgHost& P = G[PR_FWDS];
+                    const int32_t l0 = (int32_t)P.lvl_ptr.size() - 1;
                     int a = prog_add_tri(P, fb, q0, 0, ni, 0, ni, false, 0, lev);
                     if (!wz) a += prog_add_tri(P, fb, q0, 0, ni, 0, ni, true, 0, lev);
                     P.scan_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
@@ -1627,10 +1632,18 @@ ilu_status host_setup(Handle& h, const ilu_csr* A, const int32_t* part, int32_t 
                         a += prog_add_single(P, fb, q0, ni, ns, 0, ni, 0);
                     else
                         a += prog_add_single(P, apat, q0, ni, ns, 0, ni, 0);
+                    const int32_t l1 = (int32_t)P.lvl_ptr.size() - 1;
                     a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, false, 0, lev);
                     a += prog_add_tri(P, h.f2, q0, ni, ns, ni, ns, true, 0, lev);
                     P.sub_lvl.push_back((int32_t)P.lvl_ptr.size() - 1);
                     P.max_levels = std::max(P.max_levels, a);
+                    // forward alone: f' = L_B^{-1} f then g' = g - W f' (W/Z), or
+                    // t = U_B^{-1} L_B^{-1} f then g' = g - E t (E/F) -- the levels before
+                    // the local Schur solve above, copied rather than built again
+                    ProgHost& F = G[PR_FWD];
+                    prog_copy_levels(F, P, l0, l1);
+                    F.sub_lvl.push_back((int32_t)F.lvl_ptr.size() - 1);
+                    F.max_levels = std::max(F.max_levels, l1 - l0);
                 }
                 {   // local Schur solve U_S^{-1} L_S^{-1} on the interface part (base ni), one
                     // chain section
